@@ -1,0 +1,104 @@
+"""Seeded synthetic inputs shaped like the paper's test problems.
+
+This module holds no arithmetic of the method: it only builds matrices (and,
+for tests, explicit Gaussian sketches) from seeds.  Both the CUDA path and the
+CPU oracle consume what it produces.
+
+Workloads (Sec. 5 of arXiv 2509.21963 uses SuiteSparse and Gaussian-product
+matrices; these synthetic stand-ins keep their sizes and spectra):
+  * ``svd_matrix``        A = U diag(s) V^T, U, V Haar-orthogonal (QR of a Gaussian
+                          with the sign fix of Mezzadri 2007), any spectrum s.
+  * ``exact_rank``        A = X Y^T with Gaussian X, Y (rank r exactly).
+  * ``low_rank_gaussian`` the paper's Low-Rank matrix G1 G2^T (Sec. 5.1).
+  * ``lehmer``            A_ij = min(i,j)/max(i,j) (Sec. 5.3).
+  * ``decay_matrix_torch`` large matrices built on the GPU with torch (thin
+                          orthonormal factors of a capped rank plus i.i.d. noise).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def haar_orthogonal(n: int, k: int, rng: np.random.Generator) -> np.ndarray:
+    """n x k matrix with orthonormal columns, Haar distributed (k <= n)."""
+    Z = rng.standard_normal((n, k))
+    Q, R = np.linalg.qr(Z)
+    d = np.sign(np.diag(R))
+    d[d == 0] = 1.0
+    return Q * d
+
+
+def svd_matrix(m: int, n: int, s: np.ndarray, seed: int) -> np.ndarray:
+    """A = U diag(s) V^T with Haar U (m x k), V (n x k), k = len(s)."""
+    rng = np.random.default_rng(seed)
+    k = len(s)
+    U = haar_orthogonal(m, k, rng)
+    V = haar_orthogonal(n, k, rng)
+    return (U * np.asarray(s, dtype=np.float64)) @ V.T
+
+
+def cfg_small(seed: int = 0) -> np.ndarray:
+    """1000 x 800, s_i = 10^(-i/50), i = 1..800 (the small parity workload)."""
+    s = 10.0 ** (-np.arange(1, 801) / 50.0)
+    return svd_matrix(1000, 800, s, seed)
+
+
+def exact_rank(m: int, n: int, r: int, seed: int) -> np.ndarray:
+    rng = np.random.default_rng(seed)
+    return rng.standard_normal((m, r)) @ rng.standard_normal((n, r)).T
+
+
+def low_rank_gaussian(m: int, n: int, r: int, seed: int) -> np.ndarray:
+    """The Low-Rank test matrix of Sec. 5.1: G1 G2^T with standard Gaussians."""
+    return exact_rank(m, n, r, seed)
+
+
+def lehmer(n: int) -> np.ndarray:
+    i = np.arange(1, n + 1, dtype=np.float64)
+    return np.minimum.outer(i, i) / np.maximum.outer(i, i)
+
+
+def explicit_sketch(c: int, m: int, seed: int) -> np.ndarray:
+    """An explicit Gaussian sketch (c x m), for tests that pass G as an input."""
+    return np.random.default_rng(seed + 7919).standard_normal((c, m))
+
+
+def decay_matrix_torch(m: int, n: int, spectrum: str, seed: int, noise: float = 0.0,
+                       rank_cap: int = 2000, dtype=None, device="cuda"):
+    """Large A = U_k diag(s_1..s_k) V_k^T + noise * N(0,1), built with torch.
+
+    U_k, V_k: thin Q factors of seeded Gaussians (k = rank_cap columns).  The
+    factor product runs in FP32 (its rounding, ~1e-7 relative to |A|, sits far
+    below the noise term of the workloads that use this); the noise is drawn and
+    added in FP64 before the final cast to ``dtype``.
+    spectrum: "poly2" (i^-2), "exp200" (exp(-i/200)), "exp20" (exp(-i/20)),
+              "poly1.5" (i^-1.5).
+    """
+    import torch
+    dtype = dtype or torch.float64
+    k = min(rank_cap, m, n)
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    i = torch.arange(1, k + 1, device=device, dtype=torch.float64)
+    if spectrum == "poly2":
+        s = i ** -2.0
+    elif spectrum == "poly1.5":
+        s = i ** -1.5
+    elif spectrum == "exp200":
+        s = torch.exp(-i / 200.0)
+    elif spectrum == "exp20":
+        s = torch.exp(-i / 20.0)
+    else:
+        raise ValueError(spectrum)
+    U = torch.linalg.qr(torch.randn(m, k, device=device, generator=g, dtype=torch.float32))[0]
+    V = torch.linalg.qr(torch.randn(n, k, device=device, generator=g, dtype=torch.float32))[0]
+    A = torch.empty(m, n, device=device, dtype=dtype)
+    rows = max(1, (1 << 27) // max(n, 1))
+    for r0 in range(0, m, rows):
+        r1 = min(m, r0 + rows)
+        blk = ((U[r0:r1] * s.to(torch.float32)) @ V.T).to(torch.float64)
+        if noise > 0.0:
+            blk += noise * torch.randn(r1 - r0, n, device=device, generator=g, dtype=torch.float64)
+        A[r0:r1] = blk.to(dtype)
+    del U, V
+    return A
