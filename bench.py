@@ -1,0 +1,299 @@
+#!/usr/bin/env python3
+"""Time-to-tolerance of IterativeCUR (arXiv 2509.21963, Algorithm 1) on GB300.
+
+Default workload (one "step" = one complete cur_run to tolerance):
+  A = U diag(i^-2) V^T + noise, 20000 x 20000 FP64 (U, V thin orthonormal factors
+  of rank 2000 from QR of seeded Gaussians; i.i.d. N(0, (1e-8)^2) noise),
+  tol 1e-3, block size b = 50, sketch rows c = floor(1.1 b) = 55, seed 0.
+A (3.2 GB) is resident in HBM and larger than L2, so no L2 flush is needed.
+
+Prints ONE JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
+instead (the reference arm: a bounded column-slab sample, scaled to the full
+matrix).  Under torchrun every rank runs an independent replica (the method
+has no data-parallel exchange): value = max-over-ranks time / (ranks x steps).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+# dram bytes (read + write) of one sketch launch, from the committed ncu capture
+# summarised in profiles/; valid only while the kernel source is unchanged.
+TRAFFIC = {"gemm.cu": {"sha1": None, "bytes_per_launch_full": None}}
+FP64_PEAK_TFLOPS = 1.25  # GB300 nominal FP64 rate (no FP64 entry in the measured peaks)
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--m", type=int, default=20000)
+    p.add_argument("--n", type=int, default=20000)
+    p.add_argument("--dtype", choices=["f64", "f32"], default="f64")
+    p.add_argument("--tol", type=float, default=1e-3)
+    p.add_argument("--block", type=int, default=50)
+    p.add_argument("--sketch", type=int, default=55)
+    p.add_argument("--noise", type=float, default=1e-8)
+    p.add_argument("--seed", type=int, default=0)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--e2e-steps", type=int, default=3)
+    return p.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload_name(a):
+    dt = "FP64" if a.dtype == "f64" else "FP32"
+    return (f"{a.m}x{a.n} {dt} A=U diag(i^-2) V^T + N(0,({a.noise:g})^2) noise, tol {a.tol:g}, "
+            f"b={a.block}, c={a.sketch}")
+
+
+def make_matrix(a, device, dtype):
+    from paper_2509_21963_gb300 import inputs
+    return inputs.decay_matrix_torch(a.m, a.n, "poly2", seed=11, noise=a.noise, rank_cap=2000,
+                                     dtype=dtype, device=device)
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="clocks", suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = max(mx, float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def traffic_for_sketch():
+    src = os.path.join(ROOT, "paper_2509_21963_gb300", "csrc", "gemm.cu")
+    h = hashlib.sha1(open(src, "rb").read()).hexdigest()
+    rec = TRAFFIC["gemm.cu"]
+    if rec["sha1"] == h and rec["bytes_per_launch_full"] is not None:
+        return rec["bytes_per_launch_full"]
+    return None
+
+
+def oracle_sample(a, A_host_cols, frac_cols):
+    """Time the FP64 oracle (Algorithm 1, Lemma 1 form) on a column slab and scale
+    to the full matrix by n / n_slab (the sketch pass, the column selection and
+    the column residual all scale linearly in n)."""
+    import oracle
+    t0 = time.perf_counter()
+    oracle.run(A_host_cols, a.tol, a.block, a.sketch, seed=a.seed, mode=1)
+    dt = time.perf_counter() - t0
+    return dt * 1000.0 * (a.n / A_host_cols.shape[1]), dt
+
+
+def run_reference(a, ws, rank):
+    if rank != 0:
+        return 0
+    import numpy as np
+    import torch
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    dtype = torch.float64 if a.dtype == "f64" else torch.float32
+    ns = max(a.sketch + 1, a.n // 16)
+    A = make_matrix(a, dev, dtype)
+    slab = np.ascontiguousarray(A[:, :ns].to(torch.float64).cpu().numpy())
+    del A
+    for _ in range(a.warmup):
+        oracle_sample(a, slab, ns)
+    vals = []
+    t_all = 0.0
+    for _ in range(a.steps):
+        v, dt = oracle_sample(a, slab, ns)
+        vals.append(v)
+        t_all += dt
+    value = sum(vals) / len(vals)
+    sample = (f"oracle on the column slab A[:, :{ns}] of the same matrix (same m, tol, b, c), "
+              f"wall time x n/{ns}")
+    line = {"impl": "reference", "metric": "time-to-tolerance per CUR", "value": value, "unit": "ms",
+            "n_gpus": ws, "steps": a.steps, "warmup": a.warmup, "ms_per_step": value,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": workload_name(a)},
+            "cpu_baseline": {"value": value, "unit": "ms", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    a = parse()
+    ws, rank, local = dist_env()
+    if a.impl == "reference":
+        return run_reference(a, ws, rank)
+
+    import numpy as np
+    import torch
+    import paper_2509_21963_gb300 as cur
+
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dtype = torch.float64 if a.dtype == "f64" else torch.float32
+    A = make_matrix(a, f"cuda:{local}", dtype)
+    torch.cuda.synchronize()
+    ctx = cur.Context(local)
+    L = cur.lib()
+    stream = torch.cuda.current_stream()
+
+    def one_step(timing):
+        st, out = ctx.run_raw(A, a.tol, a.block, a.sketch, a.seed, timing=timing)
+        if st not in (cur.CUR_OK, cur.CUR_TOL_UNREACHED):
+            raise cur.CurError(st, ctx.last_error())
+        info = (int(L.cur_result_rank(out)), int(L.cur_result_iterations(out)),
+                float(L.cur_result_err(out)), float(L.cur_result_phase_ms(out, 1)),
+                int(L.cur_result_kernel_launches(out)), int(st))
+        L.cur_result_free(out)
+        return info
+
+    for _ in range(max(a.warmup, 3)):
+        one_step(True)
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.4)
+    barrier()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    infos = [one_step(True) for _ in range(a.steps)]
+    t1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    elapsed_ms = t0.elapsed_time(t1)
+    if ws > 1:
+        tt = torch.tensor([elapsed_ms], device=f"cuda:{local}", dtype=torch.float64)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        elapsed_ms = float(tt.item())
+    rank_r, iters, rho, _, launches, status = infos[-1]
+    sketch_ms = sum(i[3] for i in infos) / len(infos)
+    ms_per_step = elapsed_ms / a.steps
+    value = elapsed_ms / (a.steps * ws)
+
+    # end-to-end: the host-buffer C ABI call, H2D of A and D2H of I, J, U inside
+    e2e = None
+    if not a.no_e2e:
+        Ah = A.cpu().pin_memory()
+        An = Ah.numpy()
+        ctx.run_host(An, a.tol, a.block, a.sketch, a.seed)  # warm (grows the device copy)
+        torch.cuda.synchronize()
+        w0 = time.perf_counter()
+        for _ in range(a.e2e_steps):
+            r = ctx.run_host(An, a.tol, a.block, a.sketch, a.seed)
+        torch.cuda.synchronize()
+        e2e_ms = (time.perf_counter() - w0) * 1000.0 / a.e2e_steps
+        es = An.itemsize
+        e2e = {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": a.m * a.n * es,
+               "d2h_bytes_per_step": 16 * r.rank + 8 * r.rank * r.rank + 8 * (r.iterations + 8)}
+        del Ah, An
+
+    # roofline of the dominant kernel: the sketch Y = G A (FP64 arithmetic)
+    flops = 2.0 * a.sketch * a.m * a.n
+    achieved = flops / (sketch_ms * 1e-3) / 1e12
+    traffic = traffic_for_sketch()
+    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
+                "kernel": "gemm_kernel<FP64 A> (sketch Y = G A)",
+                "kernel_ms": sketch_ms,
+                "hbm_frac_of_measured": (a.m * a.n * A.element_size() / (sketch_ms * 1e-3)) / 6685.5e9}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not a.no_cpu_baseline:
+        ns = max(a.sketch + 1, a.n // 4)
+        slab = np.ascontiguousarray(A[:, :ns].to(torch.float64).cpu().numpy())
+        v, dt = oracle_sample(a, slab, ns)
+        cpu = {"value": v, "unit": "ms", "cores": 1, "kind": "oracle",
+               "sample": f"one oracle run on the column slab A[:, :{ns}] ({dt:.1f} s), scaled by n/{ns}"}
+
+    if rank == 0:
+        line = {
+            "metric": "time-to-tolerance per CUR", "value": value, "unit": "ms", "n_gpus": ws,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(a), "m": a.m, "n": a.n, "tol": a.tol,
+                       "block_size": a.block, "sketch_size": a.sketch, "a_dtype": a.dtype,
+                       "rank": rank_r, "iterations": iters, "rho": rho, "status": status,
+                       "l2": "inputs larger than L2 (A is resident in HBM)",
+                       "parallelism": f"replicas x{ws}"},
+            "gpu_launches": launches * a.steps,
+            "clocks": clk, "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

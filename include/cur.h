@@ -1,0 +1,148 @@
+/*
+ * cur.h -- C ABI of the GB300 (sm_103a) IterativeCUR library.
+ *
+ * IterativeCUR (Pritchard, Park, Nakatsukasa, Martinsson, arXiv 2509.21963,
+ * Algorithm 1): given A (m x n) and a relative Frobenius tolerance eps, find
+ * row indices I, column indices J and a core U = A(I,J)^+ such that
+ * ||A - A(:,J) U A(I,:)||_F / ||A||_F is estimated below eps (Sec. 1.1, Sec. 3.1).
+ * One Gaussian sketch Y = G A (c x n) is formed once; every iteration picks b
+ * columns by LU with partial pivoting (LUPP) on the sketched residual, b rows by
+ * LUPP on the residual at those columns, updates the residuals through Lemma 1
+ * (Sec. 4.2) and stops when rho = ||S^col||_F / ||G A||_F <= eps (Sec. 3.3).
+ *
+ * Conventions for every entry point:
+ *   - Matrices are row-major.  A has row stride lda >= n (elements).
+ *   - "device" pointers live in the memory of the context's GPU; "host"
+ *     pointers in ordinary (pageable or pinned) host memory.
+ *   - Indices are 0-based (the paper is 1-based), int64.
+ *   - Every call returns a cur_status; nothing aborts or throws across the
+ *     ABI.  cur_last_error() holds a one-line description of the last failure.
+ *   - A context is bound to one device and one CUDA stream; it is not
+ *     thread-safe (use one context per host thread).  All work of a call is
+ *     enqueued on that stream; calls that return results to the host
+ *     synchronise it.
+ */
+#ifndef CUR_H
+#define CUR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cur_ctx cur_ctx;       /* device, stream, workspace arena      */
+typedef struct cur_result cur_result; /* outputs of one run (device + host)   */
+
+typedef enum {
+  CUR_OK = 0,
+  CUR_EINVAL = 1,        /* invalid argument                                    */
+  CUR_ENONFINITE = 2,    /* A contains Inf/NaN (found by the sketch pass)       */
+  CUR_ENOMEM = 3,        /* device or host allocation failed                    */
+  CUR_EBUDGET = 4,       /* workspace would exceed the context's HBM budget     */
+  CUR_ECUDA = 5,         /* a CUDA call failed (code kept in cur_last_error)    */
+  CUR_ETIMEOUT = 6,      /* a device-side wait ran out of its iteration limit   */
+  CUR_TOL_UNREACHED = 7  /* stopped at max_rank with rho > eps (result valid)   */
+} cur_status;
+
+typedef enum { CUR_F64 = 0, CUR_F32 = 1 } cur_dtype;
+
+/* Arithmetic of the sketch pass Y = G A (all later steps are FP64). */
+typedef enum {
+  CUR_SKETCH_F64 = 0 /* FP64 products and sums (the plain method)             */
+} cur_sketch_mode;
+
+typedef struct cur_opts {
+  int64_t max_rank;        /* 0: min(m, n).  The last block is clamped to it.   */
+  const double *omega;     /* optional device G (c x m, row-major FP64), used
+                              instead of the seeded Gaussian; NULL: generated.  */
+  int sketch_mode;         /* cur_sketch_mode                                   */
+  double alpha;            /* risk-aware stopping (Sec. 3.3): 0 = off; else the
+                              loop stops at eps (1+delta) sqrt(1-2 sqrt(-ln(alpha)/c))
+                              and needs c > -4 ln(alpha) (CUR_EINVAL otherwise) */
+  double delta;            /* see alpha                                         */
+  int timing;              /* non-zero: record CUDA events around each phase
+                              (cur_result_phase_ms); adds ~2 events per phase   */
+} cur_opts;
+
+/* Phases of one run, for cur_result_phase_ms (device time, milliseconds). */
+typedef enum {
+  CUR_PHASE_GAUSSIAN = 0,  /* G from the seed (Algorithm 1 line 1)              */
+  CUR_PHASE_SKETCH = 1,    /* Y = G A and ||Y||_F (line 3): the pass over A     */
+  CUR_PHASE_LUPP_COL = 2,  /* J_k (line 7)                                      */
+  CUR_PHASE_ROW_RES = 3,   /* S^row (line 8)                                    */
+  CUR_PHASE_LUPP_ROW = 4,  /* I_k (line 10)                                     */
+  CUR_PHASE_FACTORS = 5,   /* Rt_k, N_k^+, L_k (Lemma 1 factors)                */
+  CUR_PHASE_COL_RES = 6,   /* S^col update and ||S^col||_F (lines 13-15)        */
+  CUR_PHASE_CORE = 7,      /* U = A(I,J)^+ at exit (line 12)                    */
+  CUR_PHASE_COUNT = 8
+} cur_phase;
+
+/* Create a context on `device` that enqueues on `cuda_stream` (a cudaStream_t;
+ * NULL = the legacy default stream).  hbm_budget_bytes caps the workspace the
+ * context may hold (0 = no cap).  *out receives the context. */
+int cur_create(cur_ctx **out, int device, void *cuda_stream, size_t hbm_budget_bytes);
+
+/* Release the context and its workspace.  NULL is a no-op. */
+void cur_free(cur_ctx *ctx);
+
+/* Text of the last failure on this context ("" if none); owned by the ctx. */
+const char *cur_last_error(const cur_ctx *ctx);
+
+/* Run Algorithm 1 on a device matrix.
+ *   A           device, m x n, row stride lda, FP64 or FP32 (dtype); borrowed:
+ *               read only, must stay valid and unchanged until the call returns.
+ *   tol         eps > 0 (NaN or <= 0: CUR_EINVAL).  eps >= 1 returns rank 0.
+ *   block_size  b >= 1 indices per iteration (Algorithm 1 input b).
+ *   sketch_size c rows of G; 0 selects floor(1.1 b) (Sec. 1.1); c < b: EINVAL.
+ *   seed        key of the Gaussian sketch (see cur_step_gaussian).
+ *   *out        a new result owned by the caller (free with cur_result_free);
+ *               set on CUR_OK and on CUR_TOL_UNREACHED, NULL otherwise.
+ * A = 0 (G A = 0) returns rank 0 with rho = 0. */
+int cur_run(cur_ctx *ctx, const void *A, int64_t m, int64_t n, int64_t lda,
+            int dtype, double tol, int block_size, int sketch_size,
+            uint64_t seed, cur_result **out);
+
+/* cur_run with options (opts may be NULL = defaults). */
+int cur_run_opts(cur_ctx *ctx, const void *A, int64_t m, int64_t n,
+                 int64_t lda, int dtype, double tol, int block_size,
+                 int sketch_size, uint64_t seed, const cur_opts *opts,
+                 cur_result **out);
+
+/* End-to-end form: A is a HOST buffer (m x n, stride lda).  The call copies A
+ * to the device (a context-owned buffer, grown as needed), runs, and copies
+ * I, J, U and rho back into the result's host mirrors before returning. */
+int cur_run_host(cur_ctx *ctx, const void *A_host, int64_t m, int64_t n,
+                 int64_t lda, int dtype, double tol, int block_size,
+                 int sketch_size, uint64_t seed, const cur_opts *opts,
+                 cur_result **out);
+
+/* Accessors.  Device arrays stay valid until cur_result_free. */
+int64_t cur_result_rank(const cur_result *r);          /* |I| = |J|            */
+int64_t cur_result_iterations(const cur_result *r);   /* loop iterations      */
+int cur_result_status(const cur_result *r);            /* CUR_OK / TOL_UNREACHED */
+double cur_result_err(const cur_result *r);            /* final rho            */
+double cur_result_sketch_norm(const cur_result *r);    /* ||G A||_F            */
+const int64_t *cur_result_I(const cur_result *r);      /* device, rank entries */
+const int64_t *cur_result_J(const cur_result *r);      /* device, rank entries */
+const double *cur_result_U(const cur_result *r);       /* device, rank x rank,
+                                                          rows follow J, columns I */
+/* Device milliseconds spent in `phase` (0 unless the run had opts->timing). */
+double cur_result_phase_ms(const cur_result *r, int phase);
+/* Number of kernel launches the run issued (all of them this library's). */
+int64_t cur_result_kernel_launches(const cur_result *r);
+/* rho after each iteration; host array of cur_result_iterations() entries. */
+const double *cur_result_rho_history(const cur_result *r);
+
+/* Copy I, J (rank entries each) and U (rank*rank) to host buffers; any of them
+ * may be NULL.  Synchronises the context's stream. */
+int cur_result_copy_to_host(const cur_result *r, int64_t *I, int64_t *J, double *U);
+
+/* Release a result (device and host buffers).  NULL is a no-op. */
+void cur_result_free(cur_result *r);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CUR_H */

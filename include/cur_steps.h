@@ -1,0 +1,60 @@
+/*
+ * cur_steps.h -- the individual steps of IterativeCUR (arXiv 2509.21963,
+ * Algorithm 1) as C-ABI entry points on device buffers.  cur_run() chains the
+ * same kernels; these calls exist so that each step can be checked and timed
+ * on its own.  Same conventions as cur.h: row-major, 0-based int64 indices,
+ * cur_status return codes, work enqueued on the context's stream.  All
+ * pointers are device pointers unless named *_host.  Buffers are
+ * caller-owned; the library keeps scratch inside the context.
+ */
+#ifndef CUR_STEPS_H
+#define CUR_STEPS_H
+
+#include "cur.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Gaussian sketching matrix G (c x m, FP64), Algorithm 1 "Generate a sketch
+ * matrix" with N(0,1) entries (Sec. 3.2.1).  Definition (shared with nothing
+ * but this comment):
+ *   x = Philox4x64-10(counter = {q, i, 0, 0}, key = {seed, 0x43555200})
+ *   u_t = ((x_t >> 11) + 0.5) 2^-53,  t = 0..3
+ *   G[i,4q+0..1] = sqrt(-2 ln u_0) (cos, sin)(2 pi u_1)
+ *   G[i,4q+2..3] = sqrt(-2 ln u_2) (cos, sin)(2 pi u_3)
+ * G has row stride m.  Errors: CUR_EINVAL if c < 1 or m < 1. */
+int cur_step_gaussian(cur_ctx *ctx, uint64_t seed, int64_t c, int64_t m, double *G);
+
+/* Initial sketch S_0^col = Y = G A (Algorithm 1 line 3) in FP64 arithmetic.
+ *   G  c x m FP64 (stride m); A m x n (stride lda, dtype FP64 or FP32);
+ *   Y  c x n FP64 output (stride n);
+ *   sumsq_host (may be NULL) receives ||Y||_F^2 (synchronises the stream). */
+int cur_step_sketch(cur_ctx *ctx, const double *G, int64_t c, const void *A,
+                    int64_t m, int64_t n, int64_t lda, int dtype, double *Y,
+                    double *sumsq_host);
+
+/* LUPP index selection (Sec. 3.2.1, 3.2.2): the candidates are the ncand
+ * columns of X (nr x ncand, stride ldx, FP64; read only).  Step t picks the
+ * eligible candidate with the largest |W[t, i]| of the running Schur
+ * complement (ties: smallest index; an all-zero row picks the smallest eligible
+ * index and eliminates nothing) and eliminates every other eligible candidate
+ * against it.  mask (ncand bytes, non-zero = not eligible) is updated with the
+ * picks.  piv receives `steps` indices.  Requires steps <= nr and at least
+ * `steps` eligible candidates (else CUR_EINVAL). */
+int cur_step_lupp(cur_ctx *ctx, const double *X, int64_t ldx, int64_t nr,
+                  int64_t ncand, int64_t steps, uint8_t *mask, int64_t *piv);
+
+/* Generalised inverse X = M^+ (q x p, stride p) of M (p x q, stride ldm) by
+ * Householder QR with column pivoting (Businger-Golub): M P = Q R,
+ * k = #{|R_ii| > thr}, X = P [R_11^{-1} Q_1^T; 0].  This is the core solve
+ * "U = A(I,J)^+, default QR" of Algorithm 1.  thr < 0 selects
+ * thr = max(p,q) 2^-52 |R_00|.  rank_host (may be NULL) receives k
+ * (synchronises the stream). */
+int cur_step_pinv(cur_ctx *ctx, const double *M, int64_t p, int64_t q,
+                  int64_t ldm, double thr, double *X, int64_t *rank_host);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CUR_STEPS_H */

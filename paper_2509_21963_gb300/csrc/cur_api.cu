@@ -1,0 +1,695 @@
+// cur_api.cu -- C ABI and host orchestration of IterativeCUR (arXiv
+// 2509.21963, Algorithm 1) on one GPU.
+//
+// Per run:  G (seeded Gaussian, c x m)  ->  S = Y = G A, ||Y||_F   (one pass of A)
+// Per iteration k (Algorithm 1 lines 7-15, residuals through Lemma 1):
+//   J_k  = LUPP(S^col)                       cooperative selection kernel
+//   S^row = A(:,J_k) - L Rt(:,J_k)           gather + FP64 GEMM   (m x b)
+//   I_k  = LUPP(S^row)
+//   Rt_k = A(I_k,:) - L(I_k,:) Rt            gather + FP64 GEMM   (b x n)
+//   N^+  = pinv(S^row(I_k,:))                pivoted QR, one CTA
+//   L_k  = S^row N^+                         FP64 GEMM            (m x b)
+//   S^col -= (S^col(:,J_k) N^+) Rt_k, ||S^col||_F   fused GEMM + sum of squares
+//   rho = ||S^col||_F / ||Y||_F              8-byte read-back, host decides
+// At exit U = A(I,J)^+ by pivoted QR (line 12, "default QR").
+// Lemma 1 gives S_k = A - sum_l L_l Rt_l with L_l = S_{l-1}(:,J_l) N_l^+ and
+// Rt_l = S_{l-1}(I_l,:): the same residuals as lines 8 and 13-14, without an
+// explicit U inside the loop.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/cur.h"
+#include "../../include/cur_steps.h"
+#include "cur_internal.cuh"
+
+using namespace cur;
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+enum BufId {
+  B_OMEGA, B_S, B_LUPPW, B_SROWT, B_G1, B_G2, B_N, B_NP, B_SJK, B_T1, B_PARTS, B_SPLITK,
+  B_LT, B_RT, B_I, B_J, B_MASKC, B_MASKR, B_QRSMALL, B_QRBIG, B_CORE, B_STATUS, B_AHOST,
+  B_STEP_QR, B_STEP_LUPP, B_STEP_PARTS, B_COUNT
+};
+
+struct cur_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  size_t budget = 0;
+  size_t held = 0;
+  int num_sms = 0;
+  std::string err;
+  DevBuf buf[B_COUNT];
+  DevStatus* st_host = nullptr;  // pinned mirror of the device status block
+  // phase timing (opts->timing): events recorded at phase boundaries
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<int> ev_phase;      // phase that starts at event i (-1: none)
+  bool timing = false;
+  int64_t launches = 0;           // kernel launches of the current run
+};
+
+struct cur_result {
+  cur_ctx* ctx = nullptr;
+  int64_t rank = 0, iters = 0;
+  int status = CUR_OK;
+  double rho = 1.0, normY = 0.0;
+  int64_t* I = nullptr;
+  int64_t* J = nullptr;
+  double* U = nullptr;
+  std::vector<double> rho_hist;
+  double phase_ms[CUR_PHASE_COUNT] = {0};
+  int64_t launches = 0;
+  bool host_valid = false;
+  std::vector<int64_t> I_host, J_host;
+  std::vector<double> U_host;
+};
+
+namespace {
+
+// Largest r for which the core solve U = A(I,J)^+ runs (its reflector lives
+// in shared memory); runs of larger matrices stop there (CUR_TOL_UNREACHED).
+constexpr int64_t kMaxCoreRank = 16384;
+
+int fail(cur_ctx* ctx, int code, const char* fmt, ...) {
+  char msg[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(msg, sizeof(msg), fmt, ap);
+  va_end(ap);
+  if (ctx) ctx->err = msg;
+  return code;
+}
+
+#define CK(expr)                                                                          \
+  do {                                                                                    \
+    cudaError_t e_ = (expr);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      return fail(ctx, CUR_ECUDA, "%s failed: %s (%d)", #expr, cudaGetErrorString(e_),    \
+                  (int)e_);                                                               \
+  } while (0)
+
+#define TRY(expr)                   \
+  do {                              \
+    int s_ = (expr);                \
+    if (s_ != CUR_OK) return s_;    \
+  } while (0)
+
+// Grow-only named workspace; contents are not preserved unless keep > 0.
+int ensure(cur_ctx* ctx, BufId id, size_t bytes, size_t keep = 0) {
+  DevBuf& b = ctx->buf[id];
+  if (bytes == 0) bytes = 1;
+  bytes = (bytes + 255) / 256 * 256;
+  if (b.bytes >= bytes) return CUR_OK;
+  size_t grow = b.bytes + b.bytes / 2;
+  if (keep == 0 && grow > bytes) bytes = (grow + 255) / 256 * 256;
+  if (ctx->budget && ctx->held - b.bytes + bytes > ctx->budget)
+    return fail(ctx, CUR_EBUDGET, "workspace of %zu bytes exceeds the HBM budget of %zu bytes",
+                ctx->held - b.bytes + bytes, ctx->budget);
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, CUR_ENOMEM, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+  }
+  if (keep && b.p) {
+    e = cudaMemcpyAsync(p, b.p, keep < b.bytes ? keep : b.bytes, cudaMemcpyDeviceToDevice,
+                        ctx->stream);
+    if (e != cudaSuccess) { cudaFree(p); return fail(ctx, CUR_ECUDA, "workspace copy failed"); }
+  }
+  if (b.p) { cudaStreamSynchronize(ctx->stream); cudaFree(b.p); }
+  ctx->held = ctx->held - b.bytes + bytes;
+  b.p = p;
+  b.bytes = bytes;
+  return CUR_OK;
+}
+
+template <typename T>
+T* bp(cur_ctx* ctx, BufId id) { return static_cast<T*>(ctx->buf[id].p); }
+
+LaunchEnv env_of(cur_ctx* ctx) { return LaunchEnv{ctx->stream, ctx->num_sms, ctx->device}; }
+
+// Record a phase boundary: the interval from this event to the next one is
+// charged to `phase` (-1 closes the previous interval).
+void tick(cur_ctx* ctx, int phase) {
+  if (!ctx->timing) return;
+  size_t i = ctx->ev_phase.size();
+  if (i >= ctx->ev_pool.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) { cudaGetLastError(); ctx->timing = false; return; }
+    ctx->ev_pool.push_back(e);
+  }
+  cudaEventRecord(ctx->ev_pool[i], ctx->stream);
+  ctx->ev_phase.push_back(phase);
+}
+
+void collect_phases(cur_ctx* ctx, cur_result* res) {
+  if (!ctx->timing) return;
+  cudaStreamSynchronize(ctx->stream);
+  for (size_t i = 0; i + 1 < ctx->ev_phase.size(); ++i) {
+    int ph = ctx->ev_phase[i];
+    if (ph < 0 || ph >= CUR_PHASE_COUNT) continue;
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, ctx->ev_pool[i], ctx->ev_pool[i + 1]) == cudaSuccess)
+      res->phase_ms[ph] += ms;
+    else
+      cudaGetLastError();
+  }
+  ctx->ev_phase.clear();
+}
+
+// Read the device status block; translate a device error.
+int read_status(cur_ctx* ctx) {
+  CK(cudaMemcpyAsync(ctx->st_host, ctx->buf[B_STATUS].p, sizeof(DevStatus),
+                     cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (ctx->st_host->err == kDevTimeout)
+    return fail(ctx, CUR_ETIMEOUT, "a device-side grid barrier exceeded its cycle budget");
+  if (ctx->st_host->err == kDevNoCandidate)
+    return fail(ctx, CUR_EINVAL, "LUPP ran out of eligible candidates");
+  if (ctx->st_host->err != 0) return fail(ctx, CUR_ECUDA, "device status %d", ctx->st_host->err);
+  return CUR_OK;
+}
+
+DevStatus* dstat(cur_ctx* ctx) { return bp<DevStatus>(ctx, B_STATUS); }
+
+int lupp_call(cur_ctx* ctx, BufId wid, const double* X, int64_t ldx, int64_t nr, int64_t ncand,
+              int64_t steps, uint8_t* mask, int64_t* piv) {
+  LaunchEnv env = env_of(ctx);
+  int grid = lupp_grid(env, nr, ncand);
+  TRY(ensure(ctx, wid, sizeof(double) * lupp_work_doubles(nr, ncand, grid) + 256));
+  LuppWork w;
+  w.W = bp<double>(ctx, wid);
+  w.slot_val = w.W + (size_t)nr * ncand;
+  w.bar = reinterpret_cast<GridBar*>(w.slot_val + 2 * (size_t)grid * (nr + 2));
+  w.max_grid = grid;
+  CK(launch_lupp(env, X, ldx, nr, ncand, steps, mask, piv, w, grid, dstat(ctx)));
+  ctx->launches += 1;
+  return CUR_OK;
+}
+
+int pinv_call(cur_ctx* ctx, BufId wid, const double* M, int64_t p, int64_t q, int64_t ldm,
+              int thr_mode, double thr, double* scale_dev, double* X, int64_t ldx) {
+  LaunchEnv env = env_of(ctx);
+  int grid = qrcp_grid(env, p, q);
+  TRY(ensure(ctx, wid, qrcp_work_bytes(p, q, grid)));
+  QrcpWork w;
+  qrcp_carve(ctx->buf[wid].p, p, q, grid, &w);
+  CK(launch_qrcp_pinv(env, M, p, q, ldm, thr_mode, thr, scale_dev, X, ldx, w, grid, dstat(ctx)));
+  ctx->launches += 2;
+  return CUR_OK;
+}
+
+int gemm(cur_ctx* ctx, GemmArgs g) {
+  if (g.M <= 0 || g.N <= 0) return CUR_OK;
+  CK(launch_gemm(env_of(ctx), g));
+  ctx->launches += g.ksplit > 1 ? 2 : 1;
+  return CUR_OK;
+}
+
+// (rlim, clim): extent of the source in its (r, c) index space.
+int gather(cur_ctx* ctx, const void* X, bool f32, int64_t ldx, bool trans, const int64_t* ridx,
+           const int64_t* cidx, int64_t rows, int64_t cols, int64_t rlim, int64_t clim,
+           double* out, int64_t ldo) {
+  if (rows <= 0 || cols <= 0) return CUR_OK;
+  CK(launch_gather2d(env_of(ctx), X, f32, ldx, trans, ridx, cidx, rows, cols, rlim, clim, out, ldo));
+  ctx->launches += 1;
+  return CUR_OK;
+}
+
+int sum_parts(cur_ctx* ctx, const double* parts, int64_t n, double* out) {
+  CK(launch_sum_parts(env_of(ctx), parts, n, out));
+  ctx->launches += 1;
+  return CUR_OK;
+}
+
+GemmArgs gargs(int64_t M, int64_t N, int64_t K, double alpha, const double* A, int64_t lda,
+               bool tA, const void* B, int64_t ldb, bool tB, bool bf32, double beta,
+               const double* Cin, int64_t ldcin, double* D, int64_t ldd) {
+  GemmArgs g{};
+  g.M = M; g.N = N; g.K = K; g.alpha = alpha; g.A = A; g.lda = lda; g.transA = tA;
+  g.B = B; g.ldb = ldb; g.transB = tB; g.b_is_f32 = bf32; g.beta = beta; g.Cin = Cin;
+  g.ldcin = ldcin; g.D = D; g.ldd = ldd; g.sumsq_part = nullptr; g.partial = nullptr;
+  g.ksplit = 1;
+  return g;
+}
+
+// Y = G A with FP64 arithmetic into Y, ||Y||^2 into status scalar[slot].
+int sketch_f64(cur_ctx* ctx, const double* G, int64_t c, const void* A, bool a_f32, int64_t m,
+               int64_t n, int64_t lda, double* Y, int slot, BufId parts_id) {
+  GemmArgs g = gargs(c, n, m, 1.0, G, m, false, A, lda, false, a_f32, 0.0, nullptr, 0, Y, n);
+  int64_t tiles = ((c + 63) / 64) * ((n + 63) / 64);
+  int64_t ks = (2 * ctx->num_sms + tiles - 1) / tiles;
+  int64_t kmax_split = (m + 255) / 256;
+  if (ks > kmax_split) ks = kmax_split;
+  if (ks < 1) ks = 1;
+  g.ksplit = (int)ks;
+  if (ks > 1) {
+    TRY(ensure(ctx, B_SPLITK, sizeof(double) * (size_t)(ks * c * n)));
+    g.partial = bp<double>(ctx, B_SPLITK);
+  }
+  int64_t nparts = gemm_num_sumsq_parts(g);
+  TRY(ensure(ctx, parts_id, sizeof(double) * (size_t)nparts));
+  g.sumsq_part = bp<double>(ctx, parts_id);
+  TRY(gemm(ctx, g));
+  TRY(sum_parts(ctx, g.sumsq_part, nparts, &dstat(ctx)->scalar[slot]));
+  return CUR_OK;
+}
+
+int validate(cur_ctx* ctx, const void* A, int64_t m, int64_t n, int64_t lda, int dtype,
+             double tol, int b, int* c, const cur_opts* o, int64_t* max_rank, double* tol_eff) {
+  if (!ctx) return CUR_EINVAL;
+  if (!A) return fail(ctx, CUR_EINVAL, "A is NULL");
+  if (m < 1 || n < 1) return fail(ctx, CUR_EINVAL, "m and n must be >= 1");
+  if (lda < n) return fail(ctx, CUR_EINVAL, "lda (%lld) < n (%lld)", (long long)lda, (long long)n);
+  if (dtype != CUR_F64 && dtype != CUR_F32) return fail(ctx, CUR_EINVAL, "unknown dtype %d", dtype);
+  if (!(tol > 0.0)) return fail(ctx, CUR_EINVAL, "tol must be > 0 (got %g)", tol);
+  if (b < 1) return fail(ctx, CUR_EINVAL, "block_size must be >= 1");
+  if (*c == 0) *c = (11 * b) / 10;
+  if (*c < b) return fail(ctx, CUR_EINVAL, "sketch_size (%d) < block_size (%d)", *c, b);
+  int64_t mn = m < n ? m : n;
+  if (mn > kMaxCoreRank) mn = kMaxCoreRank;
+  *max_rank = mn;
+  *tol_eff = tol;
+  if (o) {
+    if (o->max_rank < 0) return fail(ctx, CUR_EINVAL, "max_rank < 0");
+    if (o->max_rank > 0 && o->max_rank < mn) *max_rank = o->max_rank;
+    if (o->sketch_mode != CUR_SKETCH_F64)
+      return fail(ctx, CUR_EINVAL, "unknown sketch_mode %d", o->sketch_mode);
+    if (o->alpha != 0.0) {
+      if (!(o->alpha > 0.0 && o->alpha < 1.0) || !(o->delta >= 0.0))
+        return fail(ctx, CUR_EINVAL, "alpha must be in (0,1) and delta >= 0");
+      double la = -std::log(o->alpha);
+      if (!((double)*c > 4.0 * la))
+        return fail(ctx, CUR_EINVAL, "risk-aware stop needs c > -4 ln(alpha) = %g", 4.0 * la);
+      *tol_eff = tol * (1.0 + o->delta) * std::sqrt(1.0 - 2.0 * std::sqrt(la / (double)*c));
+    }
+  }
+  return CUR_OK;
+}
+
+int run_device(cur_ctx* ctx, const void* A, int64_t m, int64_t n, int64_t lda, int dtype,
+               double tol, int b, int c, uint64_t seed, const cur_opts* o, cur_result** out) {
+  int64_t max_rank;
+  double tol_eff;
+  TRY(validate(ctx, A, m, n, lda, dtype, tol, b, &c, o, &max_rank, &tol_eff));
+  CK(cudaSetDevice(ctx->device));
+  const bool f32 = dtype == CUR_F32;
+  cudaStream_t s = ctx->stream;
+  LaunchEnv env = env_of(ctx);
+  ctx->timing = o && o->timing;
+  ctx->ev_phase.clear();
+  ctx->launches = 0;
+
+  TRY(ensure(ctx, B_STATUS, sizeof(DevStatus)));
+  CK(cudaMemsetAsync(ctx->buf[B_STATUS].p, 0, sizeof(DevStatus), s));
+  double minus1 = -1.0;
+  CK(cudaMemcpyAsync(&dstat(ctx)->scalar[2], &minus1, sizeof(double), cudaMemcpyHostToDevice, s));
+
+  // line 1: G; line 3: S_0 = Y = G A and ||Y||_F (the one full pass over A)
+  const double* G = o ? o->omega : nullptr;
+  if (!G) {
+    TRY(ensure(ctx, B_OMEGA, sizeof(double) * (size_t)(c * m)));
+    tick(ctx, CUR_PHASE_GAUSSIAN);
+    CK(launch_gaussian(env, seed, c, m, bp<double>(ctx, B_OMEGA), m));
+    ctx->launches += 1;
+    G = bp<double>(ctx, B_OMEGA);
+  }
+  TRY(ensure(ctx, B_S, sizeof(double) * (size_t)(c * n)));
+  double* S = bp<double>(ctx, B_S);
+  TRY(ensure(ctx, B_PARTS, sizeof(double) * 4096));
+  tick(ctx, CUR_PHASE_SKETCH);
+  TRY(sketch_f64(ctx, G, c, A, f32, m, n, lda, S, 0, B_PARTS));
+  tick(ctx, -1);
+  TRY(read_status(ctx));
+  const double nY2 = ctx->st_host->scalar[0];
+  if (!std::isfinite(nY2)) return fail(ctx, CUR_ENONFINITE, "A contains Inf or NaN");
+  const double nY = std::sqrt(nY2);
+
+  cur_result* res = new cur_result();
+  res->ctx = ctx;
+  res->normY = nY;
+  if (nY == 0.0) {  // G A = 0: nothing to approximate
+    res->rho = 0.0;
+    collect_phases(ctx, res);
+    res->launches = ctx->launches;
+    *out = res;
+    return CUR_OK;
+  }
+
+  // index arrays and masks
+  int64_t rcap = max_rank < 256 ? max_rank : 256;
+  if (rcap < b) rcap = b < max_rank ? b : max_rank;
+  auto fail_res = [&](int code) { delete res; return code; };
+  int st;
+  if ((st = ensure(ctx, B_I, sizeof(int64_t) * (size_t)max_rank)) != CUR_OK) return fail_res(st);
+  if ((st = ensure(ctx, B_J, sizeof(int64_t) * (size_t)max_rank)) != CUR_OK) return fail_res(st);
+  if ((st = ensure(ctx, B_MASKC, (size_t)n)) != CUR_OK) return fail_res(st);
+  if ((st = ensure(ctx, B_MASKR, (size_t)m)) != CUR_OK) return fail_res(st);
+  if ((st = ensure(ctx, B_LT, sizeof(double) * (size_t)(rcap * m))) != CUR_OK) return fail_res(st);
+  if ((st = ensure(ctx, B_RT, sizeof(double) * (size_t)(rcap * n))) != CUR_OK) return fail_res(st);
+  const size_t bsz = (size_t)b;
+  if ((st = ensure(ctx, B_SROWT, sizeof(double) * bsz * m)) != CUR_OK) return fail_res(st);
+  if ((st = ensure(ctx, B_N, sizeof(double) * bsz * bsz)) != CUR_OK) return fail_res(st);
+  if ((st = ensure(ctx, B_NP, sizeof(double) * bsz * bsz)) != CUR_OK) return fail_res(st);
+  if ((st = ensure(ctx, B_SJK, sizeof(double) * (size_t)c * bsz)) != CUR_OK) return fail_res(st);
+  if ((st = ensure(ctx, B_T1, sizeof(double) * (size_t)c * bsz)) != CUR_OK) return fail_res(st);
+  {
+    cudaError_t e1 = cudaMemsetAsync(ctx->buf[B_MASKC].p, 0, (size_t)n, s);
+    cudaError_t e2 = cudaMemsetAsync(ctx->buf[B_MASKR].p, 0, (size_t)m, s);
+    cudaError_t e3 = cudaMemsetAsync(ctx->buf[B_I].p, 0, sizeof(int64_t) * (size_t)max_rank, s);
+    cudaError_t e4 = cudaMemsetAsync(ctx->buf[B_J].p, 0, sizeof(int64_t) * (size_t)max_rank, s);
+    if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess || e4 != cudaSuccess)
+      return fail_res(fail(ctx, CUR_ECUDA, "memset failed"));
+  }
+  int64_t* Id = bp<int64_t>(ctx, B_I);
+  int64_t* Jd = bp<int64_t>(ctx, B_J);
+  uint8_t* maskc = bp<uint8_t>(ctx, B_MASKC);
+  uint8_t* maskr = bp<uint8_t>(ctx, B_MASKR);
+
+  double rho = 1.0;
+  int64_t r = 0;
+  while (rho > tol_eff && r < max_rank) {  // Algorithm 1 line 6
+    const int64_t bk = (int64_t)b < max_rank - r ? (int64_t)b : max_rank - r;
+    if (r + bk > rcap) {  // grow the Lemma 1 factors, keeping their content
+      int64_t nc = rcap * 2 > r + bk ? rcap * 2 : r + bk;
+      if (nc > max_rank) nc = max_rank;
+      if ((st = ensure(ctx, B_LT, sizeof(double) * (size_t)(nc * m), sizeof(double) * (size_t)(r * m))) != CUR_OK) return fail_res(st);
+      if ((st = ensure(ctx, B_RT, sizeof(double) * (size_t)(nc * n), sizeof(double) * (size_t)(r * n))) != CUR_OK) return fail_res(st);
+      rcap = nc;
+    }
+    double* LT = bp<double>(ctx, B_LT);   // rows: L_l^T (L is m x r)
+    double* Rt = bp<double>(ctx, B_RT);   // rows: Rt_l  (r x n)
+    double* SrowT = bp<double>(ctx, B_SROWT);
+    int64_t* Jk = Jd + r;
+    int64_t* Ik = Id + r;
+
+    // line 7: J_k = LUPP on S^col (candidates: the n columns)
+    tick(ctx, CUR_PHASE_LUPP_COL);
+    if ((st = lupp_call(ctx, B_LUPPW, S, n, c, n, bk, maskc, Jk)) != CUR_OK) return fail_res(st);
+    // line 8: S^row^T = A(:,J_k)^T - Rt(:,J_k)^T L^T   (bk x m)
+    tick(ctx, CUR_PHASE_ROW_RES);
+    if ((st = gather(ctx, A, f32, lda, true, Jk, nullptr, bk, m, n, m, SrowT, m)) != CUR_OK)
+      return fail_res(st);
+    if (r > 0) {
+      if ((st = ensure(ctx, B_G1, sizeof(double) * (size_t)(rcap * bk))) != CUR_OK) return fail_res(st);
+      double* G1 = bp<double>(ctx, B_G1);
+      if ((st = gather(ctx, Rt, false, n, false, nullptr, Jk, r, bk, r, n, G1, bk)) != CUR_OK)
+        return fail_res(st);
+      if ((st = gemm(ctx, gargs(bk, m, r, -1.0, G1, bk, true, LT, m, false, false, 1.0, SrowT, m,
+                                SrowT, m))) != CUR_OK) return fail_res(st);
+    }
+    // line 10: I_k = LUPP on S^row (candidates: the m rows)
+    tick(ctx, CUR_PHASE_LUPP_ROW);
+    if ((st = lupp_call(ctx, B_LUPPW, SrowT, m, bk, m, bk, maskr, Ik)) != CUR_OK) return fail_res(st);
+    // N = S^row(I_k, :) = S_{k-1}(I_k, J_k)
+    tick(ctx, CUR_PHASE_FACTORS);
+    double* Nd = bp<double>(ctx, B_N);
+    double* Np = bp<double>(ctx, B_NP);
+    if ((st = gather(ctx, SrowT, false, m, true, Ik, nullptr, bk, bk, m, bk, Nd, bk)) != CUR_OK)
+      return fail_res(st);
+    // Rt_k = A(I_k,:) - L(I_k,:) Rt
+    double* Rk = Rt + (size_t)r * n;
+    if ((st = gather(ctx, A, f32, lda, false, Ik, nullptr, bk, n, m, n, Rk, n)) != CUR_OK)
+      return fail_res(st);
+    if (r > 0) {
+      if ((st = ensure(ctx, B_G2, sizeof(double) * (size_t)(rcap * bk))) != CUR_OK) return fail_res(st);
+      double* G2 = bp<double>(ctx, B_G2);
+      if ((st = gather(ctx, LT, false, m, false, nullptr, Ik, r, bk, r, m, G2, bk)) != CUR_OK)
+        return fail_res(st);
+      if ((st = gemm(ctx, gargs(bk, n, r, -1.0, G2, bk, true, Rt, n, false, false, 1.0, Rk, n,
+                                Rk, n))) != CUR_OK) return fail_res(st);
+    }
+    // N^+ by pivoted QR; rank threshold |I| 2^-52 |R_00(N_1)|
+    if ((st = pinv_call(ctx, B_QRSMALL, Nd, bk, bk, bk, 2, (double)(r + bk),
+                        &dstat(ctx)->scalar[2], Np, bk)) != CUR_OK) return fail_res(st);
+    // L_k^T = (S^row N^+)^T = N^+^T S^row^T   (bk x m)
+    if ((st = gemm(ctx, gargs(bk, m, bk, 1.0, Np, bk, true, SrowT, m, false, false, 0.0, nullptr, 0,
+                              LT + (size_t)r * m, m))) != CUR_OK) return fail_res(st);
+    // lines 13-14 (Lemma 1): S^col -= (S^col(:,J_k) N^+) Rt_k, fused ||S^col||^2
+    tick(ctx, CUR_PHASE_COL_RES);
+    double* SJk = bp<double>(ctx, B_SJK);
+    double* T1 = bp<double>(ctx, B_T1);
+    if ((st = gather(ctx, S, false, n, false, nullptr, Jk, c, bk, c, n, SJk, bk)) != CUR_OK)
+      return fail_res(st);
+    if ((st = gemm(ctx, gargs(c, bk, bk, 1.0, SJk, bk, false, Np, bk, false, false, 0.0, nullptr, 0,
+                              T1, bk))) != CUR_OK) return fail_res(st);
+    {
+      GemmArgs g = gargs(c, n, bk, -1.0, T1, bk, false, Rk, n, false, false, 1.0, S, n, S, n);
+      int64_t np = gemm_num_sumsq_parts(g);
+      if ((st = ensure(ctx, B_PARTS, sizeof(double) * (size_t)np)) != CUR_OK) return fail_res(st);
+      g.sumsq_part = bp<double>(ctx, B_PARTS);
+      if ((st = gemm(ctx, g)) != CUR_OK) return fail_res(st);
+      if ((st = sum_parts(ctx, g.sumsq_part, np, &dstat(ctx)->scalar[1])) != CUR_OK)
+        return fail_res(st);
+    }
+    // line 15: rho_k (the host needs it to decide line 6)
+    tick(ctx, -1);
+    if ((st = read_status(ctx)) != CUR_OK) return fail_res(st);
+    r += bk;
+    rho = std::sqrt(ctx->st_host->scalar[1]) / nY;
+    res->rho_hist.push_back(rho);
+  }
+
+  // line 12 for the returned CUR: U = A(I,J)^+ by pivoted QR
+  res->rank = r;
+  res->iters = (int64_t)res->rho_hist.size();
+  res->rho = rho;
+  res->status = rho > tol_eff ? CUR_TOL_UNREACHED : CUR_OK;
+  if (r > 0) {
+    int64_t *Ires = nullptr, *Jres = nullptr;
+    double* Ures = nullptr;
+    cudaError_t e = cudaMalloc((void**)&Ires, sizeof(int64_t) * (size_t)r);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&Jres, sizeof(int64_t) * (size_t)r);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&Ures, sizeof(double) * (size_t)(r * r));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      cudaFree(Ires); cudaFree(Jres); cudaFree(Ures);
+      return fail_res(fail(ctx, CUR_ENOMEM, "result allocation failed"));
+    }
+    res->I = Ires;
+    res->J = Jres;
+    res->U = Ures;
+    CK(cudaMemcpyAsync(res->I, Id, sizeof(int64_t) * (size_t)r, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(res->J, Jd, sizeof(int64_t) * (size_t)r, cudaMemcpyDeviceToDevice, s));
+    if ((st = ensure(ctx, B_CORE, sizeof(double) * (size_t)(r * r))) != CUR_OK) { cur_result_free(res); return st; }
+    double* Mc = bp<double>(ctx, B_CORE);
+    tick(ctx, CUR_PHASE_CORE);
+    if ((st = gather(ctx, A, f32, lda, false, res->I, res->J, r, r, m, n, Mc, r)) != CUR_OK) {
+      cur_result_free(res);
+      return st;
+    }
+    if ((st = pinv_call(ctx, B_QRBIG, Mc, r, r, r, 0, 0.0, nullptr, res->U, r)) != CUR_OK) {
+      cur_result_free(res);
+      return st;
+    }
+    tick(ctx, -1);
+    if ((st = read_status(ctx)) != CUR_OK) { cur_result_free(res); return st; }
+  }
+  collect_phases(ctx, res);
+  res->launches = ctx->launches;
+  *out = res;
+  return res->status;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+int cur_create(cur_ctx** out, int device, void* cuda_stream, size_t hbm_budget_bytes) {
+  if (!out) return CUR_EINVAL;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return CUR_EINVAL;
+  }
+  if (cudaSetDevice(device) != cudaSuccess) return CUR_ECUDA;
+  cur_ctx* ctx = new cur_ctx();
+  ctx->device = device;
+  ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+  ctx->budget = hbm_budget_bytes;
+  cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
+  if (cudaMallocHost((void**)&ctx->st_host, sizeof(DevStatus)) != cudaSuccess) {
+    delete ctx;
+    return CUR_ENOMEM;
+  }
+  *out = ctx;
+  return CUR_OK;
+}
+
+void cur_free(cur_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  for (auto& b : ctx->buf)
+    if (b.p) cudaFree(b.p);
+  for (auto e : ctx->ev_pool) cudaEventDestroy(e);
+  if (ctx->st_host) cudaFreeHost(ctx->st_host);
+  delete ctx;
+}
+
+const char* cur_last_error(const cur_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int cur_run(cur_ctx* ctx, const void* A, int64_t m, int64_t n, int64_t lda, int dtype, double tol,
+            int block_size, int sketch_size, uint64_t seed, cur_result** out) {
+  return cur_run_opts(ctx, A, m, n, lda, dtype, tol, block_size, sketch_size, seed, nullptr, out);
+}
+
+int cur_run_opts(cur_ctx* ctx, const void* A, int64_t m, int64_t n, int64_t lda, int dtype,
+                 double tol, int block_size, int sketch_size, uint64_t seed, const cur_opts* opts,
+                 cur_result** out) {
+  if (!out) return fail(ctx, CUR_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!ctx) return CUR_EINVAL;
+  if (sketch_size < 0) return fail(ctx, CUR_EINVAL, "sketch_size < 0");
+  return run_device(ctx, A, m, n, lda, dtype, tol, block_size, sketch_size, seed, opts, out);
+}
+
+int cur_run_host(cur_ctx* ctx, const void* A_host, int64_t m, int64_t n, int64_t lda, int dtype,
+                 double tol, int block_size, int sketch_size, uint64_t seed, const cur_opts* opts,
+                 cur_result** out) {
+  if (!out) return fail(ctx, CUR_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!ctx) return CUR_EINVAL;
+  if (!A_host) return fail(ctx, CUR_EINVAL, "A is NULL");
+  if (m < 1 || n < 1 || lda < n) return fail(ctx, CUR_EINVAL, "bad shape");
+  if (dtype != CUR_F64 && dtype != CUR_F32) return fail(ctx, CUR_EINVAL, "unknown dtype");
+  size_t es = dtype == CUR_F64 ? 8 : 4;
+  size_t bytes = es * (size_t)(m * n);
+  CK(cudaSetDevice(ctx->device));
+  TRY(ensure(ctx, B_AHOST, bytes));
+  CK(cudaMemcpy2DAsync(ctx->buf[B_AHOST].p, es * (size_t)n, A_host, es * (size_t)lda,
+                       es * (size_t)n, (size_t)m, cudaMemcpyHostToDevice, ctx->stream));
+  int st = run_device(ctx, ctx->buf[B_AHOST].p, m, n, n, dtype, tol, block_size, sketch_size, seed,
+                      opts, out);
+  if (*out) {
+    cur_result* r = *out;
+    r->I_host.resize((size_t)r->rank);
+    r->J_host.resize((size_t)r->rank);
+    r->U_host.resize((size_t)(r->rank * r->rank));
+    if (r->rank > 0) {
+      CK(cudaMemcpyAsync(r->I_host.data(), r->I, sizeof(int64_t) * (size_t)r->rank,
+                         cudaMemcpyDeviceToHost, ctx->stream));
+      CK(cudaMemcpyAsync(r->J_host.data(), r->J, sizeof(int64_t) * (size_t)r->rank,
+                         cudaMemcpyDeviceToHost, ctx->stream));
+      CK(cudaMemcpyAsync(r->U_host.data(), r->U, sizeof(double) * (size_t)(r->rank * r->rank),
+                         cudaMemcpyDeviceToHost, ctx->stream));
+    }
+    CK(cudaStreamSynchronize(ctx->stream));
+    r->host_valid = true;
+  }
+  return st;
+}
+
+int64_t cur_result_rank(const cur_result* r) { return r ? r->rank : 0; }
+int64_t cur_result_iterations(const cur_result* r) { return r ? r->iters : 0; }
+int cur_result_status(const cur_result* r) { return r ? r->status : CUR_EINVAL; }
+double cur_result_err(const cur_result* r) { return r ? r->rho : NAN; }
+double cur_result_sketch_norm(const cur_result* r) { return r ? r->normY : NAN; }
+const int64_t* cur_result_I(const cur_result* r) { return r ? r->I : nullptr; }
+const int64_t* cur_result_J(const cur_result* r) { return r ? r->J : nullptr; }
+const double* cur_result_U(const cur_result* r) { return r ? r->U : nullptr; }
+double cur_result_phase_ms(const cur_result* r, int phase) {
+  return (r && phase >= 0 && phase < CUR_PHASE_COUNT) ? r->phase_ms[phase] : 0.0;
+}
+int64_t cur_result_kernel_launches(const cur_result* r) { return r ? r->launches : 0; }
+const double* cur_result_rho_history(const cur_result* r) {
+  return r && !r->rho_hist.empty() ? r->rho_hist.data() : nullptr;
+}
+
+int cur_result_copy_to_host(const cur_result* r, int64_t* I, int64_t* J, double* U) {
+  if (!r) return CUR_EINVAL;
+  size_t k = (size_t)r->rank;
+  if (k == 0) return CUR_OK;
+  if (r->host_valid) {
+    if (I) memcpy(I, r->I_host.data(), sizeof(int64_t) * k);
+    if (J) memcpy(J, r->J_host.data(), sizeof(int64_t) * k);
+    if (U) memcpy(U, r->U_host.data(), sizeof(double) * k * k);
+    return CUR_OK;
+  }
+  cur_ctx* ctx = r->ctx;
+  if (I) CK(cudaMemcpyAsync(I, r->I, sizeof(int64_t) * k, cudaMemcpyDeviceToHost, ctx->stream));
+  if (J) CK(cudaMemcpyAsync(J, r->J, sizeof(int64_t) * k, cudaMemcpyDeviceToHost, ctx->stream));
+  if (U) CK(cudaMemcpyAsync(U, r->U, sizeof(double) * k * k, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return CUR_OK;
+}
+
+void cur_result_free(cur_result* r) {
+  if (!r) return;
+  if (r->ctx) cudaStreamSynchronize(r->ctx->stream);
+  cudaFree(r->I);
+  cudaFree(r->J);
+  cudaFree(r->U);
+  delete r;
+}
+
+// ---- step entry points (cur_steps.h) ---------------------------------------
+
+int cur_step_gaussian(cur_ctx* ctx, uint64_t seed, int64_t c, int64_t m, double* G) {
+  if (!ctx) return CUR_EINVAL;
+  if (c < 1 || m < 1 || !G) return fail(ctx, CUR_EINVAL, "bad arguments");
+  CK(cudaSetDevice(ctx->device));
+  CK(launch_gaussian(env_of(ctx), seed, c, m, G, m));
+  return CUR_OK;
+}
+
+int cur_step_sketch(cur_ctx* ctx, const double* G, int64_t c, const void* A, int64_t m, int64_t n,
+                    int64_t lda, int dtype, double* Y, double* sumsq_host) {
+  if (!ctx) return CUR_EINVAL;
+  if (!G || !A || !Y || c < 1 || m < 1 || n < 1 || lda < n || (dtype != CUR_F64 && dtype != CUR_F32))
+    return fail(ctx, CUR_EINVAL, "bad arguments");
+  CK(cudaSetDevice(ctx->device));
+  TRY(ensure(ctx, B_STATUS, sizeof(DevStatus)));
+  CK(cudaMemsetAsync(ctx->buf[B_STATUS].p, 0, sizeof(DevStatus), ctx->stream));
+  TRY(sketch_f64(ctx, G, c, A, dtype == CUR_F32, m, n, lda, Y, 0, B_STEP_PARTS));
+  if (sumsq_host) {
+    TRY(read_status(ctx));
+    *sumsq_host = ctx->st_host->scalar[0];
+  }
+  return CUR_OK;
+}
+
+int cur_step_lupp(cur_ctx* ctx, const double* X, int64_t ldx, int64_t nr, int64_t ncand,
+                  int64_t steps, uint8_t* mask, int64_t* piv) {
+  if (!ctx) return CUR_EINVAL;
+  if (!X || !mask || !piv || nr < 1 || ncand < 1 || ldx < ncand || steps < 0 || steps > nr ||
+      steps > ncand)
+    return fail(ctx, CUR_EINVAL, "bad arguments");
+  CK(cudaSetDevice(ctx->device));
+  TRY(ensure(ctx, B_STATUS, sizeof(DevStatus)));
+  CK(cudaMemsetAsync(ctx->buf[B_STATUS].p, 0, sizeof(DevStatus), ctx->stream));
+  TRY(lupp_call(ctx, B_STEP_LUPP, X, ldx, nr, ncand, steps, mask, piv));
+  return read_status(ctx);
+}
+
+int cur_step_pinv(cur_ctx* ctx, const double* M, int64_t p, int64_t q, int64_t ldm, double thr,
+                  double* X, int64_t* rank_host) {
+  if (!ctx) return CUR_EINVAL;
+  if (!M || !X || p < 1 || q < 1 || ldm < q) return fail(ctx, CUR_EINVAL, "bad arguments");
+  if (p > kMaxCoreRank) return fail(ctx, CUR_EINVAL, "p > 16384 is not supported by the core solve");
+  CK(cudaSetDevice(ctx->device));
+  TRY(ensure(ctx, B_STATUS, sizeof(DevStatus)));
+  CK(cudaMemsetAsync(ctx->buf[B_STATUS].p, 0, sizeof(DevStatus), ctx->stream));
+  TRY(pinv_call(ctx, B_STEP_QR, M, p, q, ldm, thr < 0 ? 0 : 1, thr, nullptr, X, p));
+  TRY(read_status(ctx));
+  if (rank_host) {
+    QrcpWork w;
+    LaunchEnv env = env_of(ctx);
+    qrcp_carve(ctx->buf[B_STEP_QR].p, p, q, qrcp_grid(env, p, q), &w);
+    CK(cudaMemcpy(rank_host, w.rank, sizeof(int64_t), cudaMemcpyDeviceToHost));
+  }
+  return CUR_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,118 @@
+// cur_internal.cuh -- declarations shared by the CUDA translation units of the
+// IterativeCUR library (arXiv 2509.21963).  Each kernel file exposes host-side
+// launch functions; the orchestrator (cur_api.cu) chains them on one stream.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace cur {
+
+// Error codes written by kernels into a device status word (never __trap()).
+enum DevErr : int {
+  kDevOk = 0,
+  kDevTimeout = 1,      // a grid barrier waited past its cycle budget
+  kDevNoCandidate = 2,  // LUPP ran out of eligible candidates
+};
+
+// Device-side status block: kernels set `err` with atomicCAS(0 -> code).
+struct DevStatus {
+  int err;
+  int pad;
+  double scalar[6];  // [0] sumsq of Y, [1] sumsq of S, [2] pinv rank-scale, ...
+};
+
+// Bounded software grid barrier for cooperative launches.
+struct GridBar {
+  unsigned count;
+  unsigned gen;
+};
+
+// Cycle budget of one barrier wait (~2 s at 2 GHz): far above any legitimate
+// wait, short enough that a lost block surfaces as CUR_ETIMEOUT.
+constexpr long long kBarrierBudget = 4000000000LL;
+
+struct LaunchEnv {
+  cudaStream_t stream;
+  int num_sms;
+  int device;
+};
+
+// ---- rng.cu ---------------------------------------------------------------
+cudaError_t launch_gaussian(const LaunchEnv& env, uint64_t seed, int64_t c, int64_t m,
+                            double* G, int64_t ldg);
+
+// ---- gemm.cu --------------------------------------------------------------
+// D = alpha * op(A) op(B) + beta * Cin (row-major; op(X) = X or X^T).
+// A is FP64; B is FP64 or FP32 (b_is_f32).  Cin may alias D.  If sumsq_part
+// is non-null, each CTA writes the sum of squares of its D tile into
+// sumsq_part[cta] and the number of CTAs into *nparts.  ksplit > 1 splits the
+// K range across gridDim.z, accumulating partial tiles in `partial`
+// (ksplit * M * N doubles) and finishing in a reduction kernel.
+struct GemmArgs {
+  int64_t M, N, K;
+  double alpha;
+  const double* A; int64_t lda; bool transA;
+  const void* B; int64_t ldb; bool transB; bool b_is_f32;
+  double beta;
+  const double* Cin; int64_t ldcin;
+  double* D; int64_t ldd;
+  double* sumsq_part;   // optional
+  double* partial;      // required when ksplit > 1
+  int ksplit;
+};
+// Returns the number of sum-of-squares partials written (0 if none).
+int64_t gemm_num_sumsq_parts(const GemmArgs& g);
+cudaError_t launch_gemm(const LaunchEnv& env, const GemmArgs& g);
+// out[0] = sum of parts[0..n) in a fixed order (one CTA).
+cudaError_t launch_sum_parts(const LaunchEnv& env, const double* parts, int64_t n, double* out);
+
+// ---- gather.cu ------------------------------------------------------------
+// out[a * ldo + t] = src(r(a), c(t)) for a < rows, t < cols, where
+// r(a) = ridx ? ridx[a] : a, c(t) = cidx ? cidx[t] : t and src(i, j) =
+// X[i * ldx + j] (or X[j * ldx + i] if trans).  X is FP64 or FP32.  Index
+// pairs outside [0, rlim) x [0, clim) are not read (out = 0).
+cudaError_t launch_gather2d(const LaunchEnv& env, const void* X, bool x_is_f32, int64_t ldx,
+                            bool trans, const int64_t* ridx, const int64_t* cidx,
+                            int64_t rows, int64_t cols, int64_t rlim, int64_t clim,
+                            double* out, int64_t ldo);
+
+// ---- lupp.cu --------------------------------------------------------------
+struct LuppWork {
+  double* W;          // nr * ncand working copy
+  double* slot_val;   // 2 * max_grid * (nr + 2)
+  GridBar* bar;
+  int max_grid;
+};
+size_t lupp_work_doubles(int64_t nr, int64_t ncand, int max_grid);
+int lupp_grid(const LaunchEnv& env, int64_t nr, int64_t ncand);
+cudaError_t launch_lupp(const LaunchEnv& env, const double* X, int64_t ldx, int64_t nr,
+                        int64_t ncand, int64_t steps, uint8_t* mask, int64_t* piv,
+                        const LuppWork& w, int grid, DevStatus* st);
+
+// ---- qrcp.cu --------------------------------------------------------------
+struct QrcpWork {
+  double* Rc;       // q * p   (column-major copy of M: Rc[col * p + i])
+  double* V;        // kmax * p Householder vectors
+  double* tau;      // kmax
+  double* rdiag;    // kmax
+  int64_t* perm;    // q
+  uint8_t* used;    // q
+  double* slots;    // 2 * max_grid * 2
+  GridBar* bar;
+  int64_t* rank;    // 1 (device)
+  double* Ysolve;   // p * p solve scratch
+  int max_grid;
+};
+size_t qrcp_work_bytes(int64_t p, int64_t q, int max_grid);
+void qrcp_carve(void* base, int64_t p, int64_t q, int max_grid, QrcpWork* w);
+int qrcp_grid(const LaunchEnv& env, int64_t p, int64_t q);
+// thr_mode: 0 relative (max(p,q) 2^-52 |R_00|); 1 absolute `thr`; 2 absolute
+// thr * (*scale_dev), where *scale_dev (if *scale_dev < 0) is first set to
+// 2^-52 |R_00| of this factorisation.
+cudaError_t launch_qrcp_pinv(const LaunchEnv& env, const double* M, int64_t p, int64_t q,
+                             int64_t ldm, int thr_mode, double thr, double* scale_dev,
+                             double* X, int64_t ldx, const QrcpWork& w, int grid,
+                             DevStatus* st);
+
+}  // namespace cur

@@ -1,0 +1,164 @@
+// lupp.cu -- LU with partial pivoting as the index selector of IterativeCUR
+// (arXiv 2509.21963, Sec. 3.2.1 column selection on the sketched residual
+// S^col, Sec. 3.2.2 row selection on S^row; Algorithm 1 lines 7 and 10).
+//
+// The candidates (columns of S^col, rows of A for S^row) are the ncand
+// columns of an nr x ncand matrix X.  One cooperative launch performs all
+// `steps` pivot steps: every CTA owns a contiguous slice of candidates in a
+// working copy W (L2-resident: at most a few tens of MB), finds its local
+// winner with warp-shuffle argmax on (|value| desc, index asc), publishes the
+// winner's whole current column, and after ONE bounded grid barrier per step
+// every CTA knows the global pivot and its column, and eliminates its own
+// candidates with it (rank-1 Schur update, FP64).  Publication slots are
+// double-buffered by step parity, which is what makes one barrier per step
+// sufficient.
+#include <climits>
+
+#include "gridbar.cuh"
+
+namespace cur {
+namespace {
+
+constexpr int kThreads = 256;
+
+struct Best {
+  double a;
+  long long i;  // LLONG_MAX = none
+};
+
+__device__ __forceinline__ bool better(double a, long long i, const Best& b) {
+  return a > b.a || (a == b.a && i < b.i);
+}
+
+__device__ __forceinline__ Best warp_best(Best b) {
+  for (int o = 16; o > 0; o >>= 1) {
+    double oa = __shfl_down_sync(0xffffffffu, b.a, o);
+    long long oi = __shfl_down_sync(0xffffffffu, b.i, o);
+    if (better(oa, oi, b)) { b.a = oa; b.i = oi; }
+  }
+  return b;
+}
+
+struct LuppParams {
+  const double* X; int64_t ldx; int nr; int64_t ncand; int steps;
+  uint8_t* mask; int64_t* piv;
+  double* W;
+  double* slots;  // [2][grid][nr + 2]: abs, index bits, column values
+  GridBar* bar; DevStatus* st;
+};
+
+__global__ void __launch_bounds__(kThreads) lupp_kernel(LuppParams p) {
+  extern __shared__ double pv[];  // pivot column, nr entries
+  __shared__ Best red[kThreads / 32];
+  __shared__ Best s_win;
+  __shared__ int s_wcta;
+  const int G = gridDim.x, cta = blockIdx.x, tid = threadIdx.x;
+  const int lane = tid & 31, wid = tid >> 5;
+  const int64_t per = (p.ncand + G - 1) / G;
+  const int64_t lo = (int64_t)cta * per, hi = min(p.ncand, lo + per);
+  const int64_t ldw = p.ncand;
+  const int stride = p.nr + 2;
+
+  for (int rr = 0; rr < p.nr; ++rr)
+    for (int64_t i = lo + tid; i < hi; i += kThreads) p.W[rr * ldw + i] = p.X[rr * p.ldx + i];
+
+  for (int t = 0; t < p.steps; ++t) {
+    double* slot = p.slots + ((size_t)(t & 1) * G) * stride;
+    // 1. local argmax over eligible owned candidates
+    Best b{-1.0, LLONG_MAX};
+    for (int64_t i = lo + tid; i < hi; i += kThreads) {
+      if (p.mask[i]) continue;
+      double a = fabs(p.W[(int64_t)t * ldw + i]);
+      if (better(a, i, b)) { b.a = a; b.i = i; }
+    }
+    b = warp_best(b);
+    if (lane == 0) red[wid] = b;
+    __syncthreads();
+    if (wid == 0) {
+      Best c = lane < kThreads / 32 ? red[lane] : Best{-1.0, LLONG_MAX};
+      c = warp_best(c);
+      if (lane == 0) s_win = c;
+    }
+    __syncthreads();
+    Best mine = s_win;
+    // 2. publish (|value|, index, current column) of the local winner
+    double* my = slot + (size_t)cta * stride;
+    if (tid == 0) { my[0] = mine.a; my[1] = __longlong_as_double(mine.i); }
+    if (mine.i != LLONG_MAX)
+      for (int rr = t + tid; rr < p.nr; rr += kThreads) my[2 + rr] = p.W[rr * ldw + mine.i];
+    __threadfence();
+    if (!grid_barrier(p.bar, p.st)) return;
+    // 3. global winner (every CTA computes the same answer)
+    if (wid == 0) {
+      Best c{-1.0, LLONG_MAX};
+      int ccta = -1;
+      for (int g = lane; g < G; g += 32) {
+        const double* s = slot + (size_t)g * stride;
+        double a = __ldcg(s);
+        long long i = __double_as_longlong(__ldcg(s + 1));
+        if (better(a, i, c)) { c.a = a; c.i = i; ccta = g; }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        double oa = __shfl_down_sync(0xffffffffu, c.a, o);
+        long long oi = __shfl_down_sync(0xffffffffu, c.i, o);
+        int oc = __shfl_down_sync(0xffffffffu, ccta, o);
+        if (better(oa, oi, c)) { c.a = oa; c.i = oi; ccta = oc; }
+      }
+      if (lane == 0) { s_win = c; s_wcta = ccta; }
+    }
+    __syncthreads();
+    Best w = s_win;
+    if (w.i == LLONG_MAX) {  // no eligible candidate left anywhere
+      if (tid == 0) dev_set_err(p.st, kDevNoCandidate);
+      return;
+    }
+    const double* wcol = slot + (size_t)s_wcta * stride + 2;
+    for (int rr = t + tid; rr < p.nr; rr += kThreads) pv[rr] = __ldcg(wcol + rr);
+    if (cta == 0 && tid == 0) p.piv[t] = w.i;
+    if (tid == 0 && w.i >= lo && w.i < hi) p.mask[w.i] = 1;
+    __syncthreads();
+    // 4. eliminate the owned eligible candidates against the pivot
+    if (w.a > 0.0) {
+      const double pt = pv[t];
+      for (int64_t i = lo + tid; i < hi; i += kThreads) {
+        if (p.mask[i]) continue;
+        double l = p.W[(int64_t)t * ldw + i] / pt;
+        for (int rr = t + 1; rr < p.nr; ++rr) {
+          double* wp = p.W + rr * ldw + i;
+          *wp = fma(-l, pv[rr], *wp);
+        }
+      }
+    }
+  }
+}
+
+}  // namespace
+
+size_t lupp_work_doubles(int64_t nr, int64_t ncand, int max_grid) {
+  return (size_t)nr * ncand + 2 * (size_t)max_grid * (nr + 2);
+}
+
+int lupp_grid(const LaunchEnv& env, int64_t nr, int64_t ncand) {
+  int64_t g = (nr * ncand + 16383) / 16384;
+  int64_t cap = env.num_sms;
+  if (g > cap) g = cap;
+  if (g > ncand) g = ncand;
+  return g < 1 ? 1 : (int)g;
+}
+
+cudaError_t launch_lupp(const LaunchEnv& env, const double* X, int64_t ldx, int64_t nr,
+                        int64_t ncand, int64_t steps, uint8_t* mask, int64_t* piv,
+                        const LuppWork& w, int grid, DevStatus* st) {
+  if (steps <= 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(w.bar, 0, sizeof(GridBar), env.stream);
+  if (e != cudaSuccess) return e;
+  LuppParams p;
+  p.X = X; p.ldx = ldx; p.nr = (int)nr; p.ncand = ncand; p.steps = (int)steps;
+  p.mask = mask; p.piv = piv; p.W = w.W; p.slots = w.slot_val; p.bar = w.bar; p.st = st;
+  void* args[] = {&p};
+  size_t smem = sizeof(double) * (size_t)(nr > 0 ? nr : 1);
+  return cudaLaunchCooperativeKernel((const void*)lupp_kernel, dim3(grid), dim3(kThreads), args,
+                                     smem, env.stream);
+}
+
+}  // namespace cur

@@ -1,0 +1,283 @@
+// qrcp.cu -- core solve of IterativeCUR (arXiv 2509.21963, Algorithm 1
+// line 12, "U = A(I,J)^+, default QR"): generalised inverse of a p x q matrix
+// by Householder QR with column pivoting (Businger & Golub 1965),
+//   M P = Q R,  k = #{|R_ii| > thr},  X = P [R_11^{-1} Q_1^T ; 0]   (q x p).
+// Also used for N_k^+ of Lemma 1, N_k = S(I_k, J_k).
+//
+// Factorisation: one cooperative launch.  M is copied column-major (columns
+// contiguous); CTA g owns the columns col = g (mod G) and a warp per column
+// computes norms and applies reflectors.  Pivoting is virtual: a permutation
+// array records which physical column is pivot j, so no column is ever moved.
+// One bounded grid barrier per step publishes the per-CTA norm maxima; every
+// CTA then rebuilds the reflector from the (untouched) pivot column in shared
+// memory.  Solve: an independent launch, one warp per column of the identity:
+// apply H_0..H_{k-1}, then column-oriented back substitution with R_11.
+#include <climits>
+
+#include "gridbar.cuh"
+
+namespace cur {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+
+struct QrcpParams {
+  const double* M; int64_t p, q, ldm;
+  int thr_mode; double thr; double* scale_dev;
+  QrcpWork w; DevStatus* st;
+};
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__global__ void __launch_bounds__(kThreads) qrcp_factor_kernel(QrcpParams P) {
+  extern __shared__ double v[];  // reflector, p entries (indices >= j used)
+  __shared__ double s_red_a[kWarps];
+  __shared__ long long s_red_i[kWarps];
+  __shared__ double s_nrm2;
+  __shared__ long long s_jp;
+  __shared__ double s_tau, s_alpha;
+  const int G = gridDim.x, cta = blockIdx.x, tid = threadIdx.x;
+  const int lane = tid & 31, wid = tid >> 5;
+  const int64_t p = P.p, q = P.q, kmax = p < q ? p : q;
+  double* Rc = P.w.Rc;
+
+  // column-major working copy of the owned columns
+  for (int64_t col = cta + (int64_t)G * wid; col < q; col += (int64_t)G * kWarps) {
+    for (int64_t i = lane; i < p; i += 32) Rc[col * p + i] = P.M[i * P.ldm + col];
+    if (lane == 0) P.w.used[col] = 0;
+  }
+  __syncthreads();
+
+  for (int64_t j = 0; j < kmax; ++j) {
+    double* slot = P.w.slots + (size_t)((j & 1) * G) * 2;
+    // A. squared norms of the owned, unused columns over rows j..p-1
+    double ba = -1.0;
+    long long bi = LLONG_MAX;
+    for (int64_t col = cta + (int64_t)G * wid; col < q; col += (int64_t)G * kWarps) {
+      if (P.w.used[col]) continue;
+      double s = 0.0;
+      for (int64_t i = j + lane; i < p; i += 32) { double x = __ldcg(Rc + col * p + i); s = fma(x, x, s); }
+      s = warp_sum(s);
+      if (s > ba || (s == ba && col < bi)) { ba = s; bi = col; }
+    }
+    if (lane == 0) { s_red_a[wid] = ba; s_red_i[wid] = bi; }
+    __syncthreads();
+    if (tid == 0) {
+      double a = -1.0; long long ii = LLONG_MAX;
+      for (int w = 0; w < kWarps; ++w)
+        if (s_red_a[w] > a || (s_red_a[w] == a && s_red_i[w] < ii)) { a = s_red_a[w]; ii = s_red_i[w]; }
+      slot[2 * cta] = a;
+      slot[2 * cta + 1] = __longlong_as_double(ii);
+    }
+    __threadfence();
+    if (!grid_barrier(P.w.bar, P.st)) return;
+    // B. global pivot (largest norm, smallest index) and its reflector
+    if (tid == 0) {
+      double a = -1.0; long long ii = LLONG_MAX;
+      for (int g = 0; g < G; ++g) {
+        double ga = __ldcg(slot + 2 * g);
+        long long gi = __double_as_longlong(__ldcg(slot + 2 * g + 1));
+        if (ga > a || (ga == a && gi < ii)) { a = ga; ii = gi; }
+      }
+      s_nrm2 = a; s_jp = ii;
+    }
+    __syncthreads();
+    const long long jp = s_jp;
+    if (jp == LLONG_MAX) { if (tid == 0) dev_set_err(P.st, kDevNoCandidate); return; }
+    for (int64_t i = j + tid; i < p; i += kThreads) v[i] = __ldcg(Rc + jp * p + i);
+    __syncthreads();
+    if (tid == 0) {
+      double normx = sqrt(s_nrm2);
+      double x0 = v[j];
+      if (normx == 0.0) {
+        s_tau = 0.0; s_alpha = 0.0;
+      } else {
+        double alpha = x0 >= 0.0 ? -normx : normx;
+        s_alpha = alpha;
+        v[j] = x0 - alpha;
+        s_tau = 0.0;  // set after the norm of v below
+      }
+    }
+    __syncthreads();
+    if (s_alpha != 0.0) {  // tau = 2 / ||v||^2
+      double s = 0.0;
+      for (int64_t i = j + tid; i < p; i += kThreads) s = fma(v[i], v[i], s);
+      s = warp_sum(s);
+      if (lane == 0) s_red_a[wid] = s;
+      __syncthreads();
+      if (tid == 0) {
+        double t = 0.0;
+        for (int w = 0; w < kWarps; ++w) t += s_red_a[w];
+        s_tau = 2.0 / t;
+      }
+      __syncthreads();
+    }
+    const double tau = s_tau;
+    if (cta == 0) {
+      if (tid == 0) { P.w.perm[j] = jp; P.w.rdiag[j] = s_alpha; P.w.tau[j] = tau; }
+      for (int64_t i = j + tid; i < p; i += kThreads) P.w.V[j * p + i] = v[i];
+    }
+    if (tid == 0 && (jp % G) == cta) P.w.used[jp] = 1;
+    __syncthreads();
+    // C. apply H_j = I - tau v v^T to the owned unused columns
+    if (tau != 0.0) {
+      for (int64_t col = cta + (int64_t)G * wid; col < q; col += (int64_t)G * kWarps) {
+        if (P.w.used[col]) continue;
+        double d = 0.0;
+        for (int64_t i = j + lane; i < p; i += 32) d = fma(v[i], __ldcg(Rc + col * p + i), d);
+        d = warp_sum(d) * tau;
+        for (int64_t i = j + lane; i < p; i += 32) {
+          double* r = Rc + col * p + i;
+          *r = fma(-d, v[i], __ldcg(r));
+        }
+      }
+    }
+    __syncthreads();
+  }
+  // numerical rank (CTA 0 wrote every rdiag itself)
+  if (cta == 0 && tid == 0) {
+    double thr;
+    double r0 = kmax > 0 ? fabs(P.w.rdiag[0]) : 0.0;
+    if (P.thr_mode == 0) {
+      thr = (double)(p > q ? p : q) * 0x1.0p-52 * r0;
+    } else if (P.thr_mode == 1) {
+      thr = P.thr;
+    } else {
+      double sc = *P.scale_dev;
+      if (sc < 0.0) { sc = 0x1.0p-52 * r0; *P.scale_dev = sc; }
+      thr = P.thr * sc;
+    }
+    int64_t k = 0;
+    while (k < kmax && fabs(P.w.rdiag[k]) > thr) ++k;
+    *P.w.rank = k;
+  }
+  // columns never pivoted (q > p): append in increasing order after kmax
+  if (cta == 0 && tid == 0 && q > kmax) {
+    int64_t pos = kmax;
+    for (int64_t col = 0; col < q; ++col) {
+      bool used = false;
+      for (int64_t jj = 0; jj < kmax; ++jj) used |= (P.w.perm[jj] == col);
+      if (!used) P.w.perm[pos++] = col;
+    }
+  }
+}
+
+struct SolveParams {
+  int64_t p, q;
+  const double* Rc; const double* V; const double* tau; const double* rdiag;
+  const int64_t* perm; const int64_t* rank;
+  double* Ywork;  // p * p: column l of Q^T then Z
+  double* X; int64_t ldx;
+};
+
+// One warp per column l of the identity.
+__global__ void __launch_bounds__(kThreads) qrcp_solve_kernel(SolveParams S) {
+  const int lane = threadIdx.x & 31;
+  const int64_t l = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
+  if (l >= S.p) return;
+  const int64_t p = S.p, k = *S.rank;
+  double* y = S.Ywork + l * p;
+  for (int64_t i = lane; i < p; i += 32) y[i] = (i == l) ? 1.0 : 0.0;
+  __syncwarp();
+  for (int64_t j = 0; j < k; ++j) {  // y = H_{k-1} ... H_0 e_l
+    double t = S.tau[j];
+    if (t == 0.0) continue;
+    const double* vj = S.V + j * p;
+    double d = 0.0;
+    for (int64_t i = j + lane; i < p; i += 32) d = fma(vj[i], y[i], d);
+    d = warp_sum(d) * t;
+    for (int64_t i = j + lane; i < p; i += 32) y[i] = fma(-d, vj[i], y[i]);
+    __syncwarp();
+  }
+  // back substitution R_11 z = y(0:k), column oriented
+  for (int64_t i = k - 1; i >= 0; --i) {
+    double zi = y[i] / S.rdiag[i];
+    __syncwarp();
+    const double* rcol = S.Rc + S.perm[i] * p;  // R(0:i, i) lives in pivot column i
+    for (int64_t a = lane; a < i; a += 32) y[a] = fma(-zi, rcol[a], y[a]);
+    if (lane == 0) y[i] = zi;
+    __syncwarp();
+  }
+  for (int64_t i = lane; i < S.q; i += 32) {
+    double val = (i < k) ? y[i] : 0.0;
+    S.X[S.perm[i] * S.ldx + l] = val;
+  }
+}
+
+}  // namespace
+
+size_t qrcp_work_bytes(int64_t p, int64_t q, int max_grid) {
+  int64_t kmax = p < q ? p : q;
+  size_t b = 0;
+  auto add = [&](size_t bytes) { b += (bytes + 255) / 256 * 256; };
+  add(sizeof(double) * (size_t)(q * p));        // Rc
+  add(sizeof(double) * (size_t)(kmax * p));     // V
+  add(sizeof(double) * (size_t)kmax);           // tau
+  add(sizeof(double) * (size_t)kmax);           // rdiag
+  add(sizeof(int64_t) * (size_t)q);             // perm
+  add((size_t)q);                               // used
+  add(sizeof(double) * 4 * (size_t)max_grid);   // slots
+  add(sizeof(GridBar));
+  add(sizeof(int64_t));                         // rank
+  add(sizeof(double) * (size_t)(p * p));        // solve work
+  return b;
+}
+
+void qrcp_carve(void* base, int64_t p, int64_t q, int max_grid, QrcpWork* w) {
+  int64_t kmax = p < q ? p : q;
+  char* c = static_cast<char*>(base);
+  auto take = [&](size_t bytes) { void* r = c; c += (bytes + 255) / 256 * 256; return r; };
+  w->Rc = (double*)take(sizeof(double) * (size_t)(q * p));
+  w->V = (double*)take(sizeof(double) * (size_t)(kmax * p));
+  w->tau = (double*)take(sizeof(double) * (size_t)kmax);
+  w->rdiag = (double*)take(sizeof(double) * (size_t)kmax);
+  w->perm = (int64_t*)take(sizeof(int64_t) * (size_t)q);
+  w->used = (uint8_t*)take((size_t)q);
+  w->slots = (double*)take(sizeof(double) * 4 * (size_t)max_grid);
+  w->bar = (GridBar*)take(sizeof(GridBar));
+  w->rank = (int64_t*)take(sizeof(int64_t));
+  w->Ysolve = (double*)take(sizeof(double) * (size_t)(p * p));
+  w->max_grid = max_grid;
+}
+
+int qrcp_grid(const LaunchEnv& env, int64_t p, int64_t q) {
+  (void)p;
+  if (q <= 128) return 1;
+  int64_t g = q / 16;
+  if (g > env.num_sms) g = env.num_sms;
+  return g < 1 ? 1 : (int)g;
+}
+
+cudaError_t launch_qrcp_pinv(const LaunchEnv& env, const double* M, int64_t p, int64_t q,
+                             int64_t ldm, int thr_mode, double thr, double* scale_dev,
+                             double* X, int64_t ldx, const QrcpWork& w, int grid,
+                             DevStatus* st) {
+  if (p <= 0 || q <= 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(w.bar, 0, sizeof(GridBar), env.stream);
+  if (e != cudaSuccess) return e;
+  QrcpParams P;
+  P.M = M; P.p = p; P.q = q; P.ldm = ldm; P.thr_mode = thr_mode; P.thr = thr;
+  P.scale_dev = scale_dev; P.w = w; P.st = st;
+  size_t smem = sizeof(double) * (size_t)p;
+  if (smem > 48 * 1024) {
+    e = cudaFuncSetAttribute((const void*)qrcp_factor_kernel,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  void* args[] = {&P};
+  e = cudaLaunchCooperativeKernel((const void*)qrcp_factor_kernel, dim3(grid), dim3(kThreads),
+                                  args, smem, env.stream);
+  if (e != cudaSuccess) return e;
+  SolveParams S;
+  S.p = p; S.q = q; S.Rc = w.Rc; S.V = w.V; S.tau = w.tau; S.rdiag = w.rdiag; S.perm = w.perm;
+  S.rank = w.rank; S.Ywork = w.Ysolve; S.X = X; S.ldx = ldx;
+  unsigned blocks = (unsigned)((p + kWarps - 1) / kWarps);
+  qrcp_solve_kernel<<<blocks, kThreads, 0, env.stream>>>(S);
+  return cudaGetLastError();
+}
+
+}  // namespace cur

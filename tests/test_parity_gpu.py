@@ -1,0 +1,291 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle.
+
+Tolerances (derived from the arithmetic, u = 2^-53):
+  * G (Box-Muller): both sides evaluate the same expression on identical Philox
+    words; CUDA's log/sin/cos (<= 1-2 ulp) and glibc's (< 1 ulp) differ by a
+    few ulp, so |dG| <= 8 ulp(G).
+  * Y = G A: any summation order obeys |Y_hat - Y| <= gamma_m |G||A|,
+    gamma_m = m u / (1 - m u); two such results differ by at most twice that.
+  * LUPP pivots, I, J: bit-exact.  Every comparison first checks that the
+    oracle's decisions are not at rounding level (gap >= 1e-9 of the scale).
+  * rho (Lemma 1 recurrence): each update S -= (S(:,J_k) N^+) Rt_k adds
+    rounding <= (b+1) u g ||S_{k-1}|| with interpolation growth g <= 10, so
+    |d rho| <= 1e-10 rho + 20 (b+1) u sum_{l<k} rho_l  (rho_0 = 1).
+  * U: forward error of any backward-stable inverse is ~kappa u; the CUR that
+    U defines is well conditioned: ||C dU R||_F / ||A||_F <= 1e-10.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2509_21963_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+U_RND = 2.0 ** -53
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2509_21963_gb300 as cur
+    c = cur.Context(0)
+    yield c
+    c.close()
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+# ---------------------------------------------------------------------------
+# single steps
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("c,m,seed", [(30, 1000, 0), (55, 20001, 7), (3, 5, 123)])
+def test_gaussian_matches_oracle(ctx, c, m, seed):
+    G = ctx.gaussian(seed, c, m).cpu().numpy()
+    R = oracle.gaussian_sketch(seed, c, m)
+    assert np.all(np.abs(G - R) <= 8 * np.spacing(np.abs(R)))
+
+
+@pytest.mark.parametrize("c,m,n,f32", [(30, 1000, 800, False), (55, 2048, 1999, False),
+                                       (7, 333, 65, True), (64, 4097, 129, False)])
+def test_sketch_within_summation_bound(ctx, c, m, n, f32):
+    rng = np.random.default_rng(m + n)
+    A = rng.standard_normal((m, n))
+    if f32:
+        A = A.astype(np.float32).astype(np.float64)
+    G = oracle.gaussian_sketch(3, c, m)
+    Ad = dev(A.astype(np.float32) if f32 else A)
+    Y, ss = ctx.sketch(dev(G), Ad)
+    Y = Y.cpu().numpy()
+    Yo = oracle.sketch(G, A)
+    gam = m * U_RND / (1 - m * U_RND)
+    bound = 2 * gam * (np.abs(G) @ np.abs(A))
+    assert np.all(np.abs(Y - Yo) <= bound)
+    assert abs(ss - (Yo ** 2).sum()) <= 1e-12 * (Yo ** 2).sum()
+
+
+@pytest.mark.parametrize("nr,ncand,steps", [(30, 800, 10), (55, 20000, 50), (7, 1001, 7),
+                                            (50, 20000, 50), (12, 40, 12)])
+def test_lupp_pivots_exact(ctx, nr, ncand, steps):
+    rng = np.random.default_rng(nr * ncand)
+    X = rng.standard_normal((nr, ncand))
+    mask = np.zeros(ncand, np.uint8)
+    mask[rng.choice(ncand, size=min(5, ncand - steps), replace=False)] = 1
+    piv_o, gap = oracle.lupp(X.T.copy(), steps, mask.copy())
+    assert gap > 1e-9 * np.abs(X).max()
+    piv_g, mask_g = ctx.lupp(dev(X), steps, dev(mask))
+    assert np.array_equal(piv_g.cpu().numpy(), piv_o)
+    m2 = mask.copy()
+    m2[piv_o] = 1
+    assert np.array_equal(mask_g.cpu().numpy(), m2)
+
+
+def test_lupp_zero_pivot_and_ties(ctx):
+    X = np.zeros((2, 5))
+    X[1, 3] = 1.0
+    piv, _ = ctx.lupp(dev(X), 2)
+    assert list(piv.cpu().numpy()) == [0, 3]
+    T = np.array([[1.0, -1.0, 1.0, 0.5]])
+    piv, _ = ctx.lupp(dev(T), 1)
+    assert list(piv.cpu().numpy()) == [0]
+
+
+@pytest.mark.parametrize("p,seed", [(30, 1), (50, 2), (129, 3), (370, 4)])
+def test_pinv_matches_oracle(ctx, p, seed):
+    rng = np.random.default_rng(seed)
+    M = rng.standard_normal((p, p))
+    Xo, ko, _, _ = oracle.qrcp_pinv(M)
+    Xg, kg = ctx.pinv(dev(M))
+    Xg = Xg.cpu().numpy()
+    assert kg == ko == p
+    kappa = np.linalg.cond(M)
+    assert np.linalg.norm(Xg - Xo) / np.linalg.norm(Xo) <= 10 * p * kappa * U_RND
+    assert np.linalg.norm(M @ Xg - np.eye(p)) <= 10 * p * kappa * U_RND
+
+
+def test_pinv_rank_deficient(ctx):
+    rng = np.random.default_rng(5)
+    M = rng.standard_normal((40, 10)) @ rng.standard_normal((10, 40))
+    Xg, kg = ctx.pinv(dev(M))
+    Xo, ko, _, _ = oracle.qrcp_pinv(M)
+    assert kg == ko == 10
+    Xg = Xg.cpu().numpy()
+    assert np.abs(M @ Xg @ M - M).max() < 1e-11 * np.abs(M).max()
+
+
+# ---------------------------------------------------------------------------
+# the whole method
+# ---------------------------------------------------------------------------
+def _decided_prefix(ref, b, col_scale, tau=1e-9):
+    """Number of leading selections whose LUPP decisions are not at rounding
+    level in the oracle (gap / scale >= tau)."""
+    k = 0
+    for it in range(ref.iters):
+        if ref.gap_col[it] < tau * col_scale or ref.gap_row[it] < tau * ref.scale_row[it]:
+            break
+        k += 1
+    return min(ref.rank, k * b)
+
+
+def _check_parity(A, got, ref, b, require_full=True):
+    n_dec = _decided_prefix(ref, b, ref.maxabsY)
+    if require_full:
+        assert n_dec == ref.rank, "oracle decisions at rounding level; choose another seed"
+    assert np.array_equal(got.I[:n_dec], ref.I[:n_dec])
+    assert np.array_equal(got.J[:n_dec], ref.J[:n_dec])
+    if n_dec < ref.rank:
+        return
+    assert got.rank == ref.rank and got.iterations == ref.iters and got.status == ref.status
+    hist_prev = np.concatenate([[1.0], ref.rho_hist[:-1]])
+    bound = 1e-10 * ref.rho_hist + 20 * (b + 1) * U_RND * np.cumsum(hist_prev)
+    assert np.all(np.abs(got.rho_history - ref.rho_hist) <= bound)
+    assert abs(got.rho - ref.rho) <= bound[-1]
+    if ref.rank:
+        C, R = A[:, ref.J], A[ref.I, :]
+        dU = np.linalg.norm(C @ (got.U - ref.U) @ R) / np.linalg.norm(A)
+        assert dU <= 1e-10
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_small_workload_parity(ctx, seed):
+    """1000 x 800, s_i = 10^(-i/50), tol 1e-6, b = 10, c = 2b + 10 = 30."""
+    A = inputs.cfg_small(seed)
+    ref = oracle.run(A, 1e-6, 10, 30, seed=seed, mode=1)
+    got = ctx.run(dev(A), 1e-6, 10, 30, seed)
+    _check_parity(A, got, ref, 10)
+    assert got.status == 0 and got.rho <= 1e-6
+    err_g = oracle.true_error(A, got.I, got.J, got.U)
+    err_o = oracle.true_error(A, ref.I, ref.J, ref.U)
+    assert abs(err_g - err_o) <= 1e-9 * err_o + 1e-12
+
+
+def test_small_workload_matches_literal_algorithm(ctx):
+    """Against the literal form of Algorithm 1 (explicit U every iteration):
+    the same indices; rho within the literal form's own rounding error
+    (kappa(A(I,J)) u relative, kappa ~ 1e9 here)."""
+    A = inputs.cfg_small(0)
+    lit = oracle.run(A, 1e-6, 10, 30, seed=0, mode=0)
+    got = ctx.run(dev(A), 1e-6, 10, 30, 0)
+    assert np.array_equal(got.I, lit.I) and np.array_equal(got.J, lit.J)
+    kappa = np.linalg.cond(A[np.ix_(lit.I, lit.J)])
+    assert abs(got.rho - lit.rho) <= 10 * kappa * U_RND * lit.rho + 1e-13
+
+
+@pytest.mark.parametrize("m,n,b,c,tol,f32", [
+    (777, 1234, 7, 9, 1e-8, False),     # ragged tiles, n > m
+    (3000, 50, 8, 8, 1e-10, False),     # tall, c = b
+    (40, 3000, 16, 17, 1e-9, False),    # wide; rank capped by m
+    (5, 300, 10, 11, 1e-12, False),     # m < b: last block clamped
+    (1000, 800, 10, 30, 1e-5, True),    # FP32 input, same values
+])
+def test_shapes_parity(ctx, m, n, b, c, tol, f32):
+    k = min(m, n)
+    A = inputs.svd_matrix(m, n, 0.8 ** np.arange(k), seed=m + n)
+    if f32:
+        A = A.astype(np.float32).astype(np.float64)
+    ref = oracle.run(A, tol, b, c, seed=9, mode=1)
+    Ad = dev(A.astype(np.float32)) if f32 else dev(A)
+    got = ctx.run(Ad, tol, b, c, 9)
+    _check_parity(A, got, ref, b, require_full=False)
+
+
+def test_explicit_sketch_parity(ctx):
+    A = inputs.cfg_small(3)
+    G = inputs.explicit_sketch(30, 1000, seed=3)
+    ref = oracle.run(A, 1e-6, 10, 30, G=G, mode=1)
+    got = ctx.run(dev(A), 1e-6, 10, 30, 0, omega=dev(G))
+    _check_parity(A, got, ref, 10)
+
+
+def test_exact_rank_recovery_gpu(ctx):
+    A = inputs.exact_rank(500, 400, 37, seed=4)
+    ref = oracle.run(A, 1e-10, 10, 30, seed=2, mode=1)
+    got = ctx.run(dev(A), 1e-10, 10, 30, 2)
+    # the first 30 selections are decided; the 4th block picks from noise
+    assert np.array_equal(got.I[:30], ref.I[:30]) and np.array_equal(got.J[:30], ref.J[:30])
+    assert got.status == 0 and got.rank == ref.rank == 40
+    assert oracle.true_error(A, got.I, got.J, got.U) < 1e-12
+    assert got.rho < 1e-12
+
+
+def test_edge_cases_gpu(ctx):
+    import paper_2509_21963_gb300 as cur
+    Z = torch.zeros(64, 48, dtype=torch.float64, device="cuda")
+    r = ctx.run(Z, 1e-6, 4, 5, 0)
+    assert r.rank == 0 and r.rho == 0.0 and r.status == 0
+    A = inputs.svd_matrix(64, 48, 0.5 ** np.arange(48), seed=1)
+    Ad = dev(A)
+    r = ctx.run(Ad, 1.0, 4, 5, 0)
+    assert r.rank == 0 and r.rho == 1.0
+    r = ctx.run(Ad, 1e-14, 4, 5, 0, max_rank=6)
+    assert r.rank == 6 and r.status == cur.CUR_TOL_UNREACHED
+    ref = oracle.run(A, 1e-14, 4, 5, seed=0, max_rank=6, mode=1)
+    assert np.array_equal(r.I, ref.I) and np.array_equal(r.J, ref.J)
+    bad = Ad.clone()
+    bad[3, 7] = float("nan")
+    with pytest.raises(cur.CurError) as e:
+        ctx.run(bad, 1e-6, 4, 5, 0)
+    assert e.value.status == cur.CUR_ENONFINITE
+    bad[3, 7] = float("inf")
+    with pytest.raises(cur.CurError) as e:
+        ctx.run(bad, 1e-6, 4, 5, 0)
+    assert e.value.status == cur.CUR_ENONFINITE
+    for args in [(0.0, 4, 5), (float("nan"), 4, 5), (1e-6, 4, 3), (1e-6, 0, 5)]:
+        with pytest.raises(cur.CurError) as e:
+            ctx.run(Ad, *args, 0)
+        assert e.value.status == cur.CUR_EINVAL
+    with pytest.raises(cur.CurError) as e:
+        ctx.run(Ad, 1e-6, 4, 5, 0, alpha=1e-10)  # c = 5 <= -4 ln(alpha)
+    assert e.value.status == cur.CUR_EINVAL
+    # the context stays usable after every error
+    r = ctx.run(Ad, 1e-6, 4, 5, 0)
+    assert r.status == 0
+
+
+def test_risk_aware_threshold_gpu(ctx):
+    A = inputs.cfg_small(0)
+    alpha, delta = 1e-3, 0.0
+    thr = oracle.risk_threshold(1e-4, delta, alpha, 30)
+    ref = oracle.run(A, thr, 10, 30, seed=0, mode=1)
+    got = ctx.run(dev(A), 1e-4, 10, 30, 0, alpha=alpha, delta=delta)
+    _check_parity(A, got, ref, 10)
+    assert got.rho <= thr
+
+
+def test_host_entry_point_matches_device(ctx):
+    A = inputs.cfg_small(1)
+    a = ctx.run(dev(A), 1e-6, 10, 30, 1)
+    h = ctx.run_host(A, 1e-6, 10, 30, 1)
+    assert np.array_equal(a.I, h.I) and np.array_equal(a.J, h.J)
+    assert a.rho == h.rho and np.array_equal(a.U, h.U)
+
+
+def test_deterministic_repeat(ctx):
+    A = dev(inputs.cfg_small(2))
+    a = ctx.run(A, 1e-6, 10, 30, 4)
+    b = ctx.run(A, 1e-6, 10, 30, 4)
+    assert np.array_equal(a.I, b.I) and a.rho == b.rho and np.array_equal(a.U, b.U)
+
+
+# ---------------------------------------------------------------------------
+# full size: 20000 x 20000, the configuration bench.py times
+# ---------------------------------------------------------------------------
+def test_full_size_parity_fp64(ctx):
+    """A = U diag(i^-2) V^T + N(0, (1e-8)^2), 20000^2 FP64, tol 1e-3, b = 50,
+    c = floor(1.1 b) = 55: the oracle runs the whole method on the same matrix
+    (one pass of A in plain C, ~half a minute) and must agree exactly on I, J."""
+    m = n = 20000
+    A = inputs.decay_matrix_torch(m, n, "poly2", seed=11, noise=1e-8, dtype=torch.float64)
+    got = ctx.run(A, 1e-3, 50, 55, 0)
+    Ah = A.cpu().numpy()
+    del A
+    torch.cuda.empty_cache()
+    ref = oracle.run(Ah, 1e-3, 50, 55, seed=0, mode=1)
+    _check_parity(Ah, got, ref, 50)
+    assert got.rho <= 1e-3
