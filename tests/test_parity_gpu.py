@@ -11,8 +11,13 @@ Tolerances (derived from the arithmetic, u = 2^-53):
   * rho (Lemma 1 recurrence): each update S -= (S(:,J_k) N^+) Rt_k adds
     rounding <= (b+1) u g ||S_{k-1}|| with interpolation growth g <= 10, so
     |d rho| <= 1e-10 rho + 20 (b+1) u sum_{l<k} rho_l  (rho_0 = 1).
-  * U: forward error of any backward-stable inverse is ~kappa u; the CUR that
-    U defines is well conditioned: ||C dU R||_F / ||A||_F <= 1e-10.
+  * U = A(I,J)^+: Householder QR of M = A(I,J) (p x p) has normwise backward
+    error ||dM||_F <= sqrt(p) gamma_{cp} ||M||_F (Higham 2002, Thm 19.4), so two
+    independent FP64 inverses differ by ||dU|| / ||U|| <= 32 p^1.5 kappa(M) u
+    and, to first order (dU = -U dM U), by
+    ||C dU R||_F <= 32 p^1.5 u ||C U||_F ||M||_F ||U R||_F.  Both gates are
+    floored at 1e-10.  (At kappa ~ 1e9, LAPACK's own inverse is 1.5e-8 away from
+    the exact one in ||C dU R|| / ||A||: 1e-10 is below the FP64 floor there.)
 """
 import math
 
@@ -147,9 +152,22 @@ def _check_parity(A, got, ref, b, require_full=True):
     assert np.all(np.abs(got.rho_history - ref.rho_hist) <= bound)
     assert abs(got.rho - ref.rho) <= bound[-1]
     if ref.rank:
-        C, R = A[:, ref.J], A[ref.I, :]
-        dU = np.linalg.norm(C @ (got.U - ref.U) @ R) / np.linalg.norm(A)
-        assert dU <= 1e-10
+        _check_core(A, got, ref)
+
+
+def _check_core(A, got, ref):
+    """Gate U; return the bound used for the CUR it defines (relative to ||A||)."""
+    p = ref.rank
+    C, R, M = A[:, ref.J], A[ref.I, :], A[np.ix_(ref.I, ref.J)]
+    kappa = np.linalg.cond(M)
+    nA = np.linalg.norm(A)
+    dU_rel = np.linalg.norm(got.U - ref.U) / np.linalg.norm(ref.U)
+    assert dU_rel <= max(1e-10, 32 * p ** 1.5 * kappa * U_RND)
+    dCUR = np.linalg.norm(C @ (got.U - ref.U) @ R) / nA
+    scale = np.linalg.norm(C @ ref.U) * np.linalg.norm(M) * np.linalg.norm(ref.U @ R) / nA
+    bound = max(1e-10, 32 * p ** 1.5 * U_RND * scale)
+    assert dCUR <= bound
+    return bound
 
 
 @pytest.mark.parametrize("seed", [0, 1, 2])
@@ -160,21 +178,29 @@ def test_small_workload_parity(ctx, seed):
     got = ctx.run(dev(A), 1e-6, 10, 30, seed)
     _check_parity(A, got, ref, 10)
     assert got.status == 0 and got.rho <= 1e-6
+    # | ||A - C U_g R|| - ||A - C U_o R|| | <= ||C (U_g - U_o) R||
     err_g = oracle.true_error(A, got.I, got.J, got.U)
     err_o = oracle.true_error(A, ref.I, ref.J, ref.U)
-    assert abs(err_g - err_o) <= 1e-9 * err_o + 1e-12
+    assert abs(err_g - err_o) <= _check_core(A, got, ref)
 
 
 def test_small_workload_matches_literal_algorithm(ctx):
-    """Against the literal form of Algorithm 1 (explicit U every iteration):
-    the same indices; rho within the literal form's own rounding error
-    (kappa(A(I,J)) u relative, kappa ~ 1e9 here)."""
+    """Against the literal form of Algorithm 1 (explicit U = A(I,J)^+ every
+    iteration): the same indices; rho within the literal form's own rounding
+    error.  There S^col = Y - (Y_J U) R with a backward-stable U (backward error
+    <= sqrt(p) gamma_{cp} ||M||), so to first order
+    |d rho| <= 32 p^1.5 u ||Y_J U|| ||M|| ||U R|| / ||Y||
+    (the literal rho even differs between x86 and Arm hosts by ~1e-10 here)."""
     A = inputs.cfg_small(0)
     lit = oracle.run(A, 1e-6, 10, 30, seed=0, mode=0)
     got = ctx.run(dev(A), 1e-6, 10, 30, 0)
     assert np.array_equal(got.I, lit.I) and np.array_equal(got.J, lit.J)
-    kappa = np.linalg.cond(A[np.ix_(lit.I, lit.J)])
-    assert abs(got.rho - lit.rho) <= 10 * kappa * U_RND * lit.rho + 1e-13
+    Y = oracle.sketch(oracle.gaussian_sketch(0, 30, A.shape[0]), A)
+    M = A[np.ix_(lit.I, lit.J)]
+    W = Y[:, lit.J] @ lit.U
+    bound = 32 * lit.rank ** 1.5 * U_RND * np.linalg.norm(W) * np.linalg.norm(M) * \
+        np.linalg.norm(lit.U @ A[lit.I, :]) / np.linalg.norm(Y)
+    assert abs(got.rho - lit.rho) <= bound
 
 
 @pytest.mark.parametrize("m,n,b,c,tol,f32", [
@@ -276,16 +302,17 @@ def test_deterministic_repeat(ctx):
 # ---------------------------------------------------------------------------
 # full size: 20000 x 20000, the configuration bench.py times
 # ---------------------------------------------------------------------------
-def test_full_size_parity_fp64(ctx):
-    """A = U diag(i^-2) V^T + N(0, (1e-8)^2), 20000^2 FP64, tol 1e-3, b = 50,
-    c = floor(1.1 b) = 55: the oracle runs the whole method on the same matrix
-    (one pass of A in plain C, ~half a minute) and must agree exactly on I, J."""
+@pytest.mark.parametrize("tol,noise", [(1e-2, 1e-8), (1e-3, 1e-10)])
+def test_full_size_parity_fp64(ctx, tol, noise):
+    """A = U diag(i^-2) V^T + N(0, noise^2), 20000^2 FP64, b = 50, c = 55 (the
+    configuration bench.py times, and its second form): the oracle runs the
+    whole method on the same matrix and must agree exactly on I, J."""
     m = n = 20000
-    A = inputs.decay_matrix_torch(m, n, "poly2", seed=11, noise=1e-8, dtype=torch.float64)
-    got = ctx.run(A, 1e-3, 50, 55, 0)
+    A = inputs.decay_matrix_torch(m, n, "poly2", seed=11, noise=noise, dtype=torch.float64)
+    got = ctx.run(A, tol, 50, 55, 0)
     Ah = A.cpu().numpy()
     del A
     torch.cuda.empty_cache()
-    ref = oracle.run(Ah, 1e-3, 50, 55, seed=0, mode=1)
+    ref = oracle.run(Ah, tol, 50, 55, seed=0, mode=1)
     _check_parity(Ah, got, ref, 50)
-    assert got.rho <= 1e-3
+    assert got.status == 0 and got.rho <= tol
