@@ -54,6 +54,30 @@ int cur_step_lupp(cur_ctx *ctx, const double *X, int64_t ldx, int64_t nr,
 int cur_step_pinv(cur_ctx *ctx, const double *M, int64_t p, int64_t q,
                   int64_t ldm, double thr, double *X, int64_t *rank_host);
 
+/* cur_step_lupp without any allocation.  The paper has no counterpart: this
+ * entry point exists for callers that cannot call cudaMalloc (code running
+ * inside another framework's memory pool, allocation-free real-time loops,
+ * allocators that must not be re-entered).  It needs no context: `device`
+ * selects the GPU (made current by the call) and `cuda_stream` the stream
+ * (NULL = legacy default stream).  X, mask and piv are as for cur_step_lupp
+ * and stay caller-owned.
+ *   Scratch: a fixed 16 MiB device array inside the library (held by every GPU
+ *   that loads the library until the process exits) that must hold
+ *   nr * ncand + 2 * G * (nr + 2) doubles plus 256 bytes, G <= the SM count
+ *   (e.g. 55 x 20000 fits); larger problems and nr > 6144 return CUR_EINVAL
+ *   with a message in err.  The call allocates nothing (no cudaMalloc,
+ *   cudaFree or allocating library routine).
+ *   Set-up: the first call on a device resolves the array's device address
+ *   (cudaGetSymbolAddress) with that device current; make that first call
+ *   before any stream capture.
+ *   Concurrency: all calls share the one array, so calls that overlap on the
+ *   GPU (different streams, threads or processes' streams on the same device)
+ *   race; serialise them.  The call synchronises `cuda_stream`.
+ *   err/err_len (may be NULL/0) receive a one-line message ("" on success). */
+int cur_step_lupp_noalloc(int device, void *cuda_stream, const double *X, int64_t ldx,
+                          int64_t nr, int64_t ncand, int64_t steps, uint8_t *mask,
+                          int64_t *piv, char *err, size_t err_len);
+
 #ifdef __cplusplus
 }
 #endif

@@ -75,6 +75,8 @@ _SIGNATURES = {
     "cur_step_sketch": (_int, [_vp, _vp, _i64, _vp, _i64, _i64, _i64, _int, _vp, _vp]),
     "cur_step_lupp": (_int, [_vp, _vp, _i64, _i64, _i64, _i64, _vp, _vp]),
     "cur_step_pinv": (_int, [_vp, _vp, _i64, _i64, _i64, _dbl, _vp, _vp]),
+    "cur_step_lupp_noalloc": (_int, [_int, _vp, _vp, _i64, _i64, _i64, _i64, _vp, _vp,
+                                     ctypes.c_char_p, _sz]),
 }
 
 EXPORTED = tuple(_SIGNATURES)
