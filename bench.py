@@ -32,7 +32,7 @@ sys.path.insert(0, ROOT)
 
 # dram bytes (read + write) of one sketch launch, from the committed ncu capture
 # summarised in profiles/; valid only while the kernel source is unchanged.
-TRAFFIC = {"gemm.cu": {"sha1": None, "bytes_per_launch_full": None}}
+TRAFFIC = {"sketch_simt.cu": {"sha1": None, "bytes_per_launch_full": None}}
 FP64_PEAK_TFLOPS = 1.25  # GB300 nominal FP64 rate (no FP64 entry in the measured peaks)
 
 
@@ -146,9 +146,9 @@ class ClockSampler:
 
 
 def traffic_for_sketch():
-    src = os.path.join(ROOT, "paper_2509_21963_gb300", "csrc", "gemm.cu")
+    src = os.path.join(ROOT, "paper_2509_21963_gb300", "csrc", "sketch_simt.cu")
     h = hashlib.sha1(open(src, "rb").read()).hexdigest()
-    rec = TRAFFIC["gemm.cu"]
+    rec = TRAFFIC["sketch_simt.cu"]
     if rec["sha1"] == h and rec["bytes_per_launch_full"] is not None:
         return rec["bytes_per_launch_full"]
     return None
@@ -296,7 +296,7 @@ def main():
     traffic = traffic_for_sketch()
     roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
-                "kernel": "gemm_kernel<FP64 A> (sketch Y = G A)",
+                "kernel": "sketch_kernel<FP64 A> (Y = G A, FP64 SIMT pipe)",
                 "kernel_ms": sketch_ms,
                 "hbm_frac_of_measured": (a.m * a.n * A.element_size() / (sketch_ms * 1e-3)) / 6685.5e9}
 

@@ -243,22 +243,18 @@ GemmArgs gargs(int64_t M, int64_t N, int64_t K, double alpha, const double* A, i
 // Y = G A with FP64 arithmetic into Y, ||Y||^2 into status scalar[slot].
 int sketch_f64(cur_ctx* ctx, const double* G, int64_t c, const void* A, bool a_f32, int64_t m,
                int64_t n, int64_t lda, double* Y, int slot, BufId parts_id) {
-  GemmArgs g = gargs(c, n, m, 1.0, G, m, false, A, lda, false, a_f32, 0.0, nullptr, 0, Y, n);
-  int64_t tiles = ((c + 63) / 64) * ((n + 63) / 64);
-  int64_t ks = (2 * ctx->num_sms + tiles - 1) / tiles;
-  int64_t kmax_split = (m + 255) / 256;
-  if (ks > kmax_split) ks = kmax_split;
-  if (ks < 1) ks = 1;
-  g.ksplit = (int)ks;
-  if (ks > 1) {
-    TRY(ensure(ctx, B_SPLITK, sizeof(double) * (size_t)(ks * c * n)));
-    g.partial = bp<double>(ctx, B_SPLITK);
+  LaunchEnv env = env_of(ctx);
+  SketchPlan plan = plan_sketch_simt(env, c, m, n);
+  double* partial = nullptr;
+  if (plan.partial_doubles) {
+    TRY(ensure(ctx, B_SPLITK, sizeof(double) * plan.partial_doubles));
+    partial = bp<double>(ctx, B_SPLITK);
   }
-  int64_t nparts = gemm_num_sumsq_parts(g);
-  TRY(ensure(ctx, parts_id, sizeof(double) * (size_t)nparts));
-  g.sumsq_part = bp<double>(ctx, parts_id);
-  TRY(gemm(ctx, g));
-  TRY(sum_parts(ctx, g.sumsq_part, nparts, &dstat(ctx)->scalar[slot]));
+  TRY(ensure(ctx, parts_id, sizeof(double) * (size_t)plan.sumsq_parts));
+  double* parts = bp<double>(ctx, parts_id);
+  CK(launch_sketch_simt(env, plan, G, m, c, A, a_f32, lda, m, n, Y, partial, parts));
+  ctx->launches += plan.ks > 1 ? 2 : 1;
+  TRY(sum_parts(ctx, parts, plan.sumsq_parts, &dstat(ctx)->scalar[slot]));
   return CUR_OK;
 }
 

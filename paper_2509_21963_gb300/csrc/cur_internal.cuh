@@ -67,6 +67,21 @@ cudaError_t launch_gemm(const LaunchEnv& env, const GemmArgs& g);
 // out[0] = sum of parts[0..n) in a fixed order (one CTA).
 cudaError_t launch_sum_parts(const LaunchEnv& env, const double* parts, int64_t n, double* out);
 
+// ---- sketch_simt.cu --------------------------------------------------------
+// Y = G A (c x n) in FP64 on the SIMT FP64 pipe, K split into ks balanced work
+// units (partial buffer of ks * c * n doubles when ks > 1), fixed-order reduce.
+struct SketchPlan {
+  int64_t kunit = 0;          // rows of A per work unit
+  int ks = 1;                 // number of work units along K
+  size_t partial_doubles = 0; // scratch for the K split
+  int64_t sumsq_parts = 0;    // number of sum-of-squares partials written
+};
+SketchPlan plan_sketch_simt(const LaunchEnv& env, int64_t c, int64_t m, int64_t n);
+cudaError_t launch_sketch_simt(const LaunchEnv& env, const SketchPlan& p, const double* G,
+                               int64_t ldg, int64_t c, const void* A, bool a_f32, int64_t lda,
+                               int64_t m, int64_t n, double* Y, double* partial,
+                               double* sumsq_part);
+
 // ---- gather.cu ------------------------------------------------------------
 // out[a * ldo + t] = src(r(a), c(t)) for a < rows, t < cols, where
 // r(a) = ridx ? ridx[a] : a, c(t) = cidx ? cidx[t] : t and src(i, j) =

@@ -75,6 +75,20 @@ def test_sketch_within_summation_bound(ctx, c, m, n, f32):
     assert abs(ss - (Yo ** 2).sum()) <= 1e-12 * (Yo ** 2).sum()
 
 
+def test_sketch_strided_unaligned(ctx):
+    """A with an odd row stride (scalar-load path) and 3 row blocks of Y."""
+    rng = np.random.default_rng(77)
+    m, n, c = 517, 333, 140
+    Afull = rng.standard_normal((m, n + 1))
+    Ad = dev(Afull)[:, 1:]          # row stride 334, base offset by one element
+    A = Afull[:, 1:]
+    G = oracle.gaussian_sketch(5, c, m)
+    Y, _ = ctx.sketch(dev(G), Ad)
+    Yo = oracle.sketch(G, np.ascontiguousarray(A))
+    gam = m * U_RND / (1 - m * U_RND)
+    assert np.all(np.abs(Y.cpu().numpy() - Yo) <= 2 * gam * (np.abs(G) @ np.abs(A)))
+
+
 @pytest.mark.parametrize("nr,ncand,steps", [(30, 800, 10), (55, 20000, 50), (7, 1001, 7),
                                             (50, 20000, 50), (12, 40, 12)])
 def test_lupp_pivots_exact(ctx, nr, ncand, steps):
