@@ -34,6 +34,7 @@ sys.path.insert(0, ROOT)
 # summarised in profiles/; valid only while the kernel source is unchanged.
 TRAFFIC = {"sketch_simt.cu": {"sha1": None, "bytes_per_launch_full": None}}
 FP64_PEAK_TFLOPS = 1.25  # GB300 nominal FP64 rate (no FP64 entry in the measured peaks)
+HBM_GBS = 6685.5          # measured copy bandwidth of the GB300s (MEASURED_PEAKS.json)
 
 
 def parse():
@@ -45,6 +46,8 @@ def parse():
     p.add_argument("--m", type=int, default=20000)
     p.add_argument("--n", type=int, default=20000)
     p.add_argument("--dtype", choices=["f64", "f32"], default="f64")
+    p.add_argument("--sketch-mode", type=int, default=0,
+                   help="0 FP64 sketch; 1/2/3 tensor-core precision form with 1/2/3 digits (FP32 A)")
     p.add_argument("--tol", type=float, default=1e-2)
     p.add_argument("--block", type=int, default=50)
     p.add_argument("--sketch", type=int, default=55)
@@ -80,8 +83,9 @@ def dist_env():
 
 def workload_name(a):
     dt = "FP64" if a.dtype == "f64" else "FP32"
+    form = "" if a.sketch_mode == 0 else f", tensor-core sketch with {a.sketch_mode} digit(s)"
     return (f"{a.m}x{a.n} {dt} A=U diag(i^-2) V^T + N(0,({a.noise:g})^2) noise, tol {a.tol:g}, "
-            f"b={a.block}, c={a.sketch}")
+            f"b={a.block}, c={a.sketch}{form}")
 
 
 def make_matrix(a, device, dtype):
@@ -229,7 +233,8 @@ def main():
     last_phases = [None]
 
     def one_step(timing):
-        st, out = ctx.run_raw(A, a.tol, a.block, a.sketch, a.seed, timing=timing)
+        st, out = ctx.run_raw(A, a.tol, a.block, a.sketch, a.seed, timing=timing,
+                              sketch_mode=a.sketch_mode)
         if st not in (cur.CUR_OK, cur.CUR_TOL_UNREACHED):
             raise cur.CurError(st, ctx.last_error())
         last_phases[0] = {p: float(L.cur_result_phase_ms(out, i)) for i, p in enumerate(cur.PHASES)}
@@ -277,11 +282,11 @@ def main():
         log("e2e: copying A to pinned host memory")
         Ah = A.cpu().pin_memory()
         An = Ah.numpy()
-        ctx.run_host(An, a.tol, a.block, a.sketch, a.seed)  # warm (grows the device copy)
+        ctx.run_host(An, a.tol, a.block, a.sketch, a.seed, sketch_mode=a.sketch_mode)  # warm
         torch.cuda.synchronize()
         w0 = time.perf_counter()
         for _ in range(a.e2e_steps):
-            r = ctx.run_host(An, a.tol, a.block, a.sketch, a.seed)
+            r = ctx.run_host(An, a.tol, a.block, a.sketch, a.seed, sketch_mode=a.sketch_mode)
         torch.cuda.synchronize()
         e2e_ms = (time.perf_counter() - w0) * 1000.0 / a.e2e_steps
         log(f"e2e: {e2e_ms:.2f} ms per step")
@@ -290,15 +295,24 @@ def main():
                "d2h_bytes_per_step": 16 * r.rank + 8 * r.rank * r.rank + 8 * (r.iterations + 8)}
         del Ah, An
 
-    # roofline of the dominant kernel: the sketch Y = G A (FP64 arithmetic)
-    flops = 2.0 * a.sketch * a.m * a.n
-    achieved = flops / (sketch_ms * 1e-3) / 1e12
-    traffic = traffic_for_sketch()
-    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
-                "kernel": "sketch_kernel<FP64 A> (Y = G A, FP64 SIMT pipe)",
-                "kernel_ms": sketch_ms,
-                "hbm_frac_of_measured": (a.m * a.n * A.element_size() / (sketch_ms * 1e-3)) / 6685.5e9}
+    # roofline of the dominant kernel: the sketch Y = G A
+    if a.sketch_mode == 0:
+        flops = 2.0 * a.sketch * a.m * a.n
+        achieved = flops / (sketch_ms * 1e-3) / 1e12
+        roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                    "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                    "traffic": traffic_for_sketch(),
+                    "kernel": "sketch_kernel<FP64 A> (Y = G A, FP64 SIMT pipe)",
+                    "kernel_ms": sketch_ms,
+                    "hbm_frac_of_measured": (a.m * a.n * A.element_size() / (sketch_ms * 1e-3)) / HBM_GBS / 1e9}
+    else:
+        # algorithmic bytes: two reads of A (column scales, then the sketch pass)
+        byts = 2.0 * a.m * a.n * A.element_size()
+        achieved = byts / (sketch_ms * 1e-3) / 1e9
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": HBM_GBS, "unit": "GB/s",
+                    "frac": achieved / HBM_GBS, "traffic": None,
+                    "kernel": f"sketch phase, precision form ({a.sketch_mode} digits): colmax + "
+                              "sketch_tc_kernel + reduce", "kernel_ms": sketch_ms}
 
     # second form: tighter tolerance on the low-noise variant of the spectrum
     second = None
@@ -312,7 +326,8 @@ def main():
         A = make_matrix(b2, f"cuda:{local}", dtype)
         torch.cuda.synchronize()
         for _ in range(2):
-            st2, out2 = ctx.run_raw(A, b2.tol, a.block, a.sketch, a.seed, timing=True)
+            st2, out2 = ctx.run_raw(A, b2.tol, a.block, a.sketch, a.seed, timing=True,
+                                    sketch_mode=a.sketch_mode)
             L.cur_result_free(out2)
         s0 = torch.cuda.Event(enable_timing=True)
         s1 = torch.cuda.Event(enable_timing=True)
@@ -320,7 +335,8 @@ def main():
         s0.record(stream)
         reps = max(2, a.steps // 2)
         for _ in range(reps):
-            st2, out2 = ctx.run_raw(A, b2.tol, a.block, a.sketch, a.seed, timing=True)
+            st2, out2 = ctx.run_raw(A, b2.tol, a.block, a.sketch, a.seed, timing=True,
+                                    sketch_mode=a.sketch_mode)
             info2 = (int(L.cur_result_rank(out2)), int(L.cur_result_iterations(out2)),
                      float(L.cur_result_err(out2)), int(st2))
             ph = {p: float(L.cur_result_phase_ms(out2, i)) for i, p in enumerate(cur.PHASES)}
@@ -347,7 +363,8 @@ def main():
             "metric": "time-to-tolerance per CUR", "value": value, "unit": "ms", "n_gpus": ws,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms_per_step,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64", "data": "synthetic",
+            "dtype": "f64" if a.sketch_mode == 0 else f"bf16x{a.sketch_mode} sketch, f64 loop",
+            "data": "synthetic",
             "config": {"workload": workload_name(a), "m": a.m, "n": a.n, "tol": a.tol,
                        "block_size": a.block, "sketch_size": a.sketch, "a_dtype": a.dtype,
                        "rank": rank_r, "iterations": iters, "rho": rho, "status": status,

@@ -48,15 +48,26 @@ typedef enum {
 
 typedef enum { CUR_F64 = 0, CUR_F32 = 1 } cur_dtype;
 
-/* Arithmetic of the sketch pass Y = G A (all later steps are FP64). */
+/* Arithmetic of the sketch pass Y = G A (all later steps are FP64).
+ * The precision forms run on the tensor cores (tcgen05, BF16 operands) and
+ * need an FP32 A with lda % 4 == 0 and a 16-byte aligned base; they use the
+ * 8-bit sketch G_q = clamp(rint(16 G), -127, 127) and the S-digit fixed point
+ * of each column (digits of 8 bits relative to a power-of-two column scale
+ * 2^E_j > max |A(:,j)|), and compute Y = G_q fix_S(A) exactly:
+ *   |fix_S(A)(k,j) - A(k,j)| <= 2^(E_j - 8S - 1).
+ * c (rounded up to 16) must be <= 128, and <= 80 for S = 3. */
 typedef enum {
-  CUR_SKETCH_F64 = 0 /* FP64 products and sums (the plain method)             */
+  CUR_SKETCH_F64 = 0,   /* FP64 products and sums (the plain method)            */
+  CUR_SKETCH_BF16 = 1,  /* S = 1: one BF16 digit per entry (2^-8 of column max)  */
+  CUR_SKETCH_BF16X2 = 2,/* S = 2: hi + lo digits (2^-16)                         */
+  CUR_SKETCH_BF16X3 = 3 /* S = 3: hi + mid + lo digits (2^-24)                   */
 } cur_sketch_mode;
 
 typedef struct cur_opts {
   int64_t max_rank;        /* 0: min(m, n).  The last block is clamped to it.   */
   const double *omega;     /* optional device G (c x m, row-major FP64), used
-                              instead of the seeded Gaussian; NULL: generated.  */
+                              instead of the seeded Gaussian; NULL: generated.
+                              The precision forms use clamp(rint(16 G), +-127). */
   int sketch_mode;         /* cur_sketch_mode                                   */
   double alpha;            /* risk-aware stopping (Sec. 3.3): 0 = off; else the
                               loop stops at eps (1+delta) sqrt(1-2 sqrt(-ln(alpha)/c))

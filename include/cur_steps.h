@@ -34,6 +34,16 @@ int cur_step_sketch(cur_ctx *ctx, const double *G, int64_t c, const void *A,
                     int64_t m, int64_t n, int64_t lda, int dtype, double *Y,
                     double *sumsq_host);
 
+/* Precision form of the initial sketch on the tensor cores (see
+ * cur_sketch_mode in cur.h): Y = G_q fix_S(A) exactly, with
+ * G_q = clamp(rint(16 G), -127, 127) and S = digits in 1..3.
+ *   G c x m FP64 (stride m); A m x n FP32 (stride lda, lda % 4 == 0, base
+ *   16-byte aligned); Y c x n FP64; sumsq_host (may be NULL) receives ||Y||_F^2.
+ *   Inf/NaN in a column of A turns that column of Y into NaN.
+ * CUR_EINVAL for unsupported c / S / alignment. */
+int cur_step_sketch_q(cur_ctx *ctx, const double *G, int64_t c, const float *A, int64_t m,
+                      int64_t n, int64_t lda, int digits, double *Y, double *sumsq_host);
+
 /* LUPP index selection (Sec. 3.2.1, 3.2.2): the candidates are the ncand
  * columns of X (nr x ncand, stride ldx, FP64; read only).  Step t picks the
  * eligible candidate with the largest |W[t, i]| of the running Schur

@@ -73,6 +73,11 @@ def lib():
         L.cur_oracle_run_naive.restype = ctypes.c_int
         L.cur_oracle_true_error.argtypes = [vp, i64, i64, i64, vp, vp, i64, vp]
         L.cur_oracle_true_error.restype = dbl
+        L.cur_oracle_run_sketched.argtypes = [vp, vp, i64, i64, i64, dbl, i64, i64, u64, vp,
+                                              i64, ctypes.c_int, ctypes.POINTER(_Out)]
+        L.cur_oracle_run_sketched.restype = ctypes.c_int
+        L.cur_oracle_gaussian_sketch_q8.argtypes = [u64, i64, i64, vp]
+        L.cur_oracle_fixed_point.argtypes = [vp, i64, i64, i64, ctypes.c_int, vp]
         L.cur_oracle_risk_threshold.argtypes = [dbl, dbl, dbl, dbl]
         L.cur_oracle_risk_threshold.restype = dbl
     return _lib
@@ -183,8 +188,9 @@ def _result(o, bufs) -> Result:
 
 def run(A: np.ndarray, tol: float, b: int, c: int | None = None, seed: int = 0,
         G: np.ndarray | None = None, max_rank: int = 0, mode: int = 1,
-        want_S: bool = False) -> Result:
-    """Algorithm 1 on A (FP64).  c defaults to floor(1.1 b) (Sec. 1.1)."""
+        want_S: bool = False, A_sketch: np.ndarray | None = None) -> Result:
+    """Algorithm 1 on A (FP64).  c defaults to floor(1.1 b) (Sec. 1.1).
+    A_sketch (optional): the matrix the initial sketch is taken of."""
     A = _f64(A)
     m, n = A.shape
     if c is None:
@@ -194,7 +200,11 @@ def run(A: np.ndarray, tol: float, b: int, c: int | None = None, seed: int = 0,
         G = _f64(G)
         assert G.shape == (c, m)
     o, bufs = _alloc_out(m, n, c, b, R, want_S)
-    rc = lib().cur_oracle_run(_p(A), m, n, n, tol, b, c, seed, _p(G), R, mode, ctypes.byref(o))
+    As = None if A_sketch is None else _f64(A_sketch)
+    if As is not None:
+        assert As.shape == A.shape
+    rc = lib().cur_oracle_run_sketched(_p(A), _p(As), m, n, n, tol, b, c, seed, _p(G), R, mode,
+                                       ctypes.byref(o))
     if rc != 0:
         raise ValueError("invalid arguments")
     return _result(o, bufs)
@@ -222,3 +232,17 @@ def true_error(A: np.ndarray, I, J, U) -> float:
 
 def risk_threshold(eps: float, delta: float, alpha: float, c: float) -> float:
     return float(lib().cur_oracle_risk_threshold(eps, delta, alpha, c))
+
+
+def gaussian_sketch_q8(seed: int, c: int, m: int) -> np.ndarray:
+    G = np.empty((c, m), dtype=np.float64)
+    lib().cur_oracle_gaussian_sketch_q8(seed, c, m, _p(G))
+    return G
+
+
+def fixed_point(A: np.ndarray, S: int) -> np.ndarray:
+    A = _f64(A)
+    m, n = A.shape
+    out = np.empty_like(A)
+    lib().cur_oracle_fixed_point(_p(A), m, n, n, S, _p(out))
+    return out

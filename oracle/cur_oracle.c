@@ -354,6 +354,13 @@ int cur_oracle_run(const double *A, int64_t m, int64_t n, int64_t lda,
                    double tol, int64_t b, int64_t c, uint64_t seed,
                    const double *Gin, int64_t max_rank, int mode,
                    cur_oracle_out *out) {
+  return cur_oracle_run_sketched(A, NULL, m, n, lda, tol, b, c, seed, Gin, max_rank, mode, out);
+}
+
+int cur_oracle_run_sketched(const double *A, const double *Asketch, int64_t m, int64_t n,
+                            int64_t lda, double tol, int64_t b, int64_t c, uint64_t seed,
+                            const double *Gin, int64_t max_rank, int mode,
+                            cur_oracle_out *out) {
   int64_t mn = m < n ? m : n;
   if (max_rank <= 0 || max_rank > mn) max_rank = mn;
   out->rank = 0; out->iters = 0; out->rho = 1.0; out->status = 0;
@@ -366,7 +373,8 @@ int cur_oracle_run(const double *A, int64_t m, int64_t n, int64_t lda,
 
   /* lines 3-4: S_0 = G A, rho_0 = ||S_0|| / ||G A|| = 1 */
   double *Y = (double *)malloc(sizeof(double) * (size_t)(c * n));
-  cur_oracle_sketch(G, c, A, m, n, lda, Y);
+  if (Asketch) cur_oracle_sketch(G, c, Asketch, m, n, n, Y);
+  else cur_oracle_sketch(G, c, A, m, n, lda, Y);
   double nY = frob(Y, c * n);
   out->normY = nY;
   out->maxabsY = maxabs(Y, c * n);
@@ -576,3 +584,43 @@ double cur_oracle_risk_threshold(double eps, double delta, double alpha, double 
   return eps * xi;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Precision form of the sketch (8-bit Gaussian, S-digit fixed-point A).    */
+/* ------------------------------------------------------------------------ */
+/* G_q[i,k] = clamp(rint(16 Z[i,k]), -127, 127) with Z the Gaussian sketch of
+ * cur_oracle_gaussian_sketch (same seed): an 8-bit rounding of the Gaussian
+ * sketch (the scale 16 cancels in rho and in the LUPP choices). */
+void cur_oracle_gaussian_sketch_q8(uint64_t seed, int64_t c, int64_t m, double *G) {
+  cur_oracle_gaussian_sketch(seed, c, m, G);
+  for (int64_t t = 0; t < c * m; ++t) {
+    double q = rint(16.0 * G[t]);
+    if (q > 127.0) q = 127.0;
+    if (q < -127.0) q = -127.0;
+    G[t] = q;
+  }
+}
+
+/* fix_S(A): every column j gets the scale 2^E_j with max_k |A[k,j]| < 2^E_j
+ * (E_j = 0 for a zero column); each entry x is written with S signed base-256
+ * digits, d_{S-1} = rint(x 2^(8-E_j)), then repeatedly d = rint(256 r) of the
+ * remainder r, so fix_S(x) = 2^(E_j - 8S) sum_s d_s 256^s (|d_s| <= 256).
+ * Rounding is to nearest, ties to even.  Afix is m x n (stride n). */
+void cur_oracle_fixed_point(const double *A, int64_t m, int64_t n, int64_t lda, int S,
+                            double *Afix) {
+  for (int64_t j = 0; j < n; ++j) {
+    double mx = 0.0;
+    for (int64_t k = 0; k < m; ++k) mx = fabs(A[k * lda + j]) > mx ? fabs(A[k * lda + j]) : mx;
+    int E = 0;
+    if (mx > 0.0) frexp(mx, &E); /* mx = f 2^E, f in [0.5, 1): mx < 2^E */
+    for (int64_t k = 0; k < m; ++k) {
+      double y = ldexp(A[k * lda + j], 8 - E);
+      double v = 0.0;
+      for (int s = S - 1; s >= 0; --s) {
+        double d = rint(y);
+        v = v * 256.0 + d;
+        y = (y - d) * 256.0;
+      }
+      Afix[k * n + j] = ldexp(v, E - 8 * S);
+    }
+  }
+}

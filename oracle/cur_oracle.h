@@ -100,6 +100,21 @@ int cur_oracle_run(const double *A, int64_t m, int64_t n, int64_t lda,
                    const double *G, int64_t max_rank, int mode,
                    cur_oracle_out *out);
 
+/* cur_oracle_run with the initial sketch taken of Asketch (m x n, stride n)
+ * instead of A: Y = G Asketch; every later step uses A.  Asketch = NULL is
+ * cur_oracle_run.  Used for the precision form of the sketch. */
+int cur_oracle_run_sketched(const double *A, const double *Asketch, int64_t m, int64_t n,
+                            int64_t lda, double tol, int64_t b, int64_t c, uint64_t seed,
+                            const double *G, int64_t max_rank, int mode,
+                            cur_oracle_out *out);
+
+/* 8-bit Gaussian sketch: clamp(rint(16 Z), -127, 127), Z as above. */
+void cur_oracle_gaussian_sketch_q8(uint64_t seed, int64_t c, int64_t m, double *G);
+
+/* S-digit base-256 fixed point of A per column (see cur_oracle.c). */
+void cur_oracle_fixed_point(const double *A, int64_t m, int64_t n, int64_t lda, int S,
+                            double *Afix);
+
 /* The naive loop of Sec. 3.1: identical selections, but the residual
  * S = A - C U R is formed in full every iteration and sketched afresh
  * (G S) instead of recycling G A.  For tiny inputs only. */

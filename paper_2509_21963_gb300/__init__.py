@@ -25,7 +25,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libcur.so")
 CUR_OK, CUR_EINVAL, CUR_ENONFINITE, CUR_ENOMEM, CUR_EBUDGET, CUR_ECUDA, CUR_ETIMEOUT, \
     CUR_TOL_UNREACHED = range(8)
 CUR_F64, CUR_F32 = 0, 1
-CUR_SKETCH_F64 = 0
+CUR_SKETCH_F64, CUR_SKETCH_BF16, CUR_SKETCH_BF16X2, CUR_SKETCH_BF16X3 = 0, 1, 2, 3
 PHASES = ("gaussian", "sketch", "lupp_col", "row_res", "lupp_row", "factors", "col_res", "core")
 
 _STATUS_NAMES = {0: "CUR_OK", 1: "CUR_EINVAL", 2: "CUR_ENONFINITE", 3: "CUR_ENOMEM",
@@ -73,6 +73,7 @@ _SIGNATURES = {
     "cur_result_free": (None, [_vp]),
     "cur_step_gaussian": (_int, [_vp, _u64, _i64, _i64, _vp]),
     "cur_step_sketch": (_int, [_vp, _vp, _i64, _vp, _i64, _i64, _i64, _int, _vp, _vp]),
+    "cur_step_sketch_q": (_int, [_vp, _vp, _i64, _vp, _i64, _i64, _i64, _int, _vp, _vp]),
     "cur_step_lupp": (_int, [_vp, _vp, _i64, _i64, _i64, _i64, _vp, _vp]),
     "cur_step_pinv": (_int, [_vp, _vp, _i64, _i64, _i64, _dbl, _vp, _vp]),
     "cur_step_lupp_noalloc": (_int, [_int, _vp, _vp, _i64, _i64, _i64, _i64, _vp, _vp,
@@ -245,6 +246,18 @@ class Context:
         _check(self.ptr, lib().cur_step_sketch(self.ptr, _vp(G.data_ptr()), c, _vp(A.data_ptr()), m, n,
                                                A.stride(0), _dtype_code(A), _vp(Y.data_ptr()),
                                                ctypes.byref(ss)))
+        return Y, ss.value
+
+    def sketch_q(self, G, A, digits: int):
+        """Precision-form sketch Y = G_q fix_S(A) (A: CUDA float32)."""
+        import torch
+        c, m = G.shape
+        n = A.shape[1]
+        Y = torch.empty(c, n, dtype=torch.float64, device=A.device)
+        ss = ctypes.c_double()
+        _check(self.ptr, lib().cur_step_sketch_q(self.ptr, _vp(G.data_ptr()), c, _vp(A.data_ptr()), m,
+                                                 n, A.stride(0), int(digits), _vp(Y.data_ptr()),
+                                                 ctypes.byref(ss)))
         return Y, ss.value
 
     def lupp(self, X, steps: int, mask=None):

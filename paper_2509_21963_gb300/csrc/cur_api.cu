@@ -36,7 +36,7 @@ struct DevBuf {
 enum BufId {
   B_OMEGA, B_S, B_LUPPW, B_SROWT, B_G1, B_G2, B_N, B_NP, B_SJK, B_T1, B_PARTS, B_SPLITK,
   B_LT, B_RT, B_I, B_J, B_MASKC, B_MASKR, B_QRSMALL, B_QRBIG, B_CORE, B_STATUS, B_AHOST,
-  B_STEP_QR, B_STEP_LUPP, B_STEP_PARTS, B_COUNT
+  B_STEP_QR, B_STEP_LUPP, B_STEP_PARTS, B_TC, B_STEP_TC, B_COUNT
 };
 
 struct cur_ctx {
@@ -258,6 +258,33 @@ int sketch_f64(cur_ctx* ctx, const double* G, int64_t c, const void* A, bool a_f
   return CUR_OK;
 }
 
+// Precision form: Y = G_q fix_S(A) on the tensor cores, ||Y||^2 into scalar[slot].
+int sketch_q(cur_ctx* ctx, int S, const double* G, int64_t c, const float* A, int64_t m,
+             int64_t n, int64_t lda, double* Y, int slot, BufId parts_id, BufId scratch_id) {
+  LaunchEnv env = env_of(ctx);
+  int ks = sketch_tc_plan_ks(env, m, n);
+  TRY(ensure(ctx, scratch_id, sketch_tc_scratch_bytes(c, m, n, ks)));
+  const int64_t nparts_max = (c * n + 16383) / 16384;
+  TRY(ensure(ctx, parts_id, sizeof(double) * (size_t)nparts_max));
+  int64_t nparts = 0;
+  CK(launch_sketch_tc(env, S, G, c, A, lda, m, n, ctx->buf[scratch_id].p, ks, Y,
+                      bp<double>(ctx, parts_id), &nparts, &dstat(ctx)->err));
+  ctx->launches += 5;
+  TRY(sum_parts(ctx, bp<double>(ctx, parts_id), nparts, &dstat(ctx)->scalar[slot]));
+  return CUR_OK;
+}
+
+int check_precision_form(cur_ctx* ctx, int S, const void* A, int64_t lda, int dtype, int64_t c) {
+  if (S < 1 || S > 3) return fail(ctx, CUR_EINVAL, "unknown sketch_mode %d", S);
+  if (dtype != CUR_F32) return fail(ctx, CUR_EINVAL, "the precision forms of the sketch need FP32 A");
+  if (lda % 4 != 0 || (reinterpret_cast<uintptr_t>(A) & 15) != 0)
+    return fail(ctx, CUR_EINVAL, "the precision forms need lda %% 4 == 0 and a 16-byte aligned A");
+  if (sketch_tc_cpad((int)c, S) < 0)
+    return fail(ctx, CUR_EINVAL, "sketch_size %lld too large for sketch_mode %d (c <= 128, <= 80 for S = 3)",
+                (long long)c, S);
+  return CUR_OK;
+}
+
 int validate(cur_ctx* ctx, const void* A, int64_t m, int64_t n, int64_t lda, int dtype,
              double tol, int b, int* c, const cur_opts* o, int64_t* max_rank, double* tol_eff) {
   if (!ctx) return CUR_EINVAL;
@@ -277,7 +304,7 @@ int validate(cur_ctx* ctx, const void* A, int64_t m, int64_t n, int64_t lda, int
     if (o->max_rank < 0) return fail(ctx, CUR_EINVAL, "max_rank < 0");
     if (o->max_rank > 0 && o->max_rank < mn) *max_rank = o->max_rank;
     if (o->sketch_mode != CUR_SKETCH_F64)
-      return fail(ctx, CUR_EINVAL, "unknown sketch_mode %d", o->sketch_mode);
+      TRY(check_precision_form(ctx, o->sketch_mode, A, lda, dtype, *c));
     if (o->alpha != 0.0) {
       if (!(o->alpha > 0.0 && o->alpha < 1.0) || !(o->delta >= 0.0))
         return fail(ctx, CUR_EINVAL, "alpha must be in (0,1) and delta >= 0");
@@ -321,7 +348,12 @@ int run_device(cur_ctx* ctx, const void* A, int64_t m, int64_t n, int64_t lda, i
   double* S = bp<double>(ctx, B_S);
   TRY(ensure(ctx, B_PARTS, sizeof(double) * 4096));
   tick(ctx, CUR_PHASE_SKETCH);
-  TRY(sketch_f64(ctx, G, c, A, f32, m, n, lda, S, 0, B_PARTS));
+  const int smode = o ? o->sketch_mode : CUR_SKETCH_F64;
+  if (smode == CUR_SKETCH_F64) {
+    TRY(sketch_f64(ctx, G, c, A, f32, m, n, lda, S, 0, B_PARTS));
+  } else {
+    TRY(sketch_q(ctx, smode, G, c, static_cast<const float*>(A), m, n, lda, S, 0, B_PARTS, B_TC));
+  }
   tick(ctx, -1);
   TRY(read_status(ctx));
   const double nY2 = ctx->st_host->scalar[0];
@@ -653,6 +685,21 @@ int cur_step_sketch(cur_ctx* ctx, const double* G, int64_t c, const void* A, int
     TRY(read_status(ctx));
     *sumsq_host = ctx->st_host->scalar[0];
   }
+  return CUR_OK;
+}
+
+int cur_step_sketch_q(cur_ctx* ctx, const double* G, int64_t c, const float* A, int64_t m,
+                      int64_t n, int64_t lda, int digits, double* Y, double* sumsq_host) {
+  if (!ctx) return CUR_EINVAL;
+  if (!G || !A || !Y || c < 1 || m < 1 || n < 1 || lda < n)
+    return fail(ctx, CUR_EINVAL, "bad arguments");
+  TRY(check_precision_form(ctx, digits, A, lda, CUR_F32, c));
+  CK(cudaSetDevice(ctx->device));
+  TRY(ensure(ctx, B_STATUS, sizeof(DevStatus)));
+  CK(cudaMemsetAsync(ctx->buf[B_STATUS].p, 0, sizeof(DevStatus), ctx->stream));
+  TRY(sketch_q(ctx, digits, G, c, A, m, n, lda, Y, 0, B_STEP_PARTS, B_STEP_TC));
+  TRY(read_status(ctx));
+  if (sumsq_host) *sumsq_host = ctx->st_host->scalar[0];
   return CUR_OK;
 }
 

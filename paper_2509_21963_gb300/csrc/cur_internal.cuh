@@ -82,6 +82,19 @@ cudaError_t launch_sketch_simt(const LaunchEnv& env, const SketchPlan& p, const 
                                int64_t m, int64_t n, double* Y, double* partial,
                                double* sumsq_part);
 
+// ---- sketch_tc.cu ------------------------------------------------------------
+// Precision form of Y = G A on tcgen05 (BF16 digit slices, exact FP32/int64
+// accumulation): Y = G_q fix_S(A), G_q = clamp(rint(16 G), +-127), S in 1..3.
+// A is FP32 with lda % 4 == 0 and a 16-byte aligned base.  Scratch layout is
+// owned by the launch (sketch_tc_scratch_bytes).  c_pad = sketch_tc_cpad(c, S)
+// must be > 0.  Writes *nparts sum-of-squares partials into sumsq_part.
+int sketch_tc_cpad(int c, int S);
+int sketch_tc_plan_ks(const LaunchEnv& env, int64_t m, int64_t n);
+size_t sketch_tc_scratch_bytes(int64_t c, int64_t m, int64_t n, int ks);
+cudaError_t launch_sketch_tc(const LaunchEnv& env, int S, const double* G, int64_t c,
+                             const float* A, int64_t lda, int64_t m, int64_t n, void* scratch,
+                             int ks, double* Y, double* sumsq_part, int64_t* nparts, int* err);
+
 // ---- gather.cu ------------------------------------------------------------
 // out[a * ldo + t] = src(r(a), c(t)) for a < rows, t < cols, where
 // r(a) = ridx ? ridx[a] : a, c(t) = cidx ? cidx[t] : t and src(i, j) =

@@ -1,0 +1,605 @@
+// sketch_tc.cu -- precision form of the initial sketch Y = G A of IterativeCUR
+// (arXiv 2509.21963, Algorithm 1 line 3; Sec. 3.4 names the sketch as a primary
+// cost) on the 5th-generation tensor cores (tcgen05, kind::f16, BF16 operands,
+// FP32 accumulators in tensor memory).
+//
+// Arithmetic (exact by construction):
+//   * G_q = clamp(rint(16 Z), -127, 127): the Gaussian sketch rounded to 8-bit
+//     integers (every value exact in BF16).
+//   * each column j of A (FP32) gets the scale 2^E_j with max_k |A(k,j)| < 2^E_j
+//     (colmax pre-pass), and every entry is written with S signed base-256
+//     digits d_s (|d_s| <= 256, exact in BF16): fix_S(x) = 2^(E_j-8S) sum d_s 256^s.
+//   * one MMA product is |q d| <= 127 * 256 < 2^15; a chunk of 256 rows sums to
+//     < 2^23, so the FP32 accumulator of each digit slice is an exact integer.
+//     Chunks are drained to int64 (exact) and combined over the K range; the
+//     FP64 result 2^(E_j-8S) sum_s 256^s D_s is exact as long as it fits 53
+//     bits (it does: < 2^47).
+// So Y = G_q fix_S(A) exactly; S = 1, 2, 3 are the "BF16", "hi+lo" and
+// "hi+mid+lo" forms, accurate to 2^-8S of each column's largest entry.
+//
+// Kernel structure (one persistent CTA per SM, 10 warps):
+//   warp 0      TMA producer: A tile (64 rows x 128 columns FP32, no swizzle)
+//               and G_q tile (c_pad rows x 64 k BF16, 128-byte swizzle = the
+//               K-major SW128 operand layout) into a stage ring.
+//   warp 1      MMA issuer (one elected thread): per stage and digit slice,
+//               four M=128 N=c_pad K=16 MMAs into the slice's accumulator.
+//   warps 2-9   converters: FP32 tile -> S BF16 digit tiles written in the
+//               K-major SW128 layout (the transpose happens here), then the
+//               chunk drain: tcgen05.ld of the accumulators -> int64.
+// Accumulators are double-buffered by chunk so the MMA of chunk z+1 overlaps
+// the drain of chunk z.  Every wait is bounded: on timeout the CTA records an
+// error and leaves its loops.
+#include <cuda.h>
+
+#include "gridbar.cuh"
+
+namespace cur {
+namespace {
+
+constexpr int kTileK = 64;        // rows of A per stage = MMA K per stage
+constexpr int kTileN = 128;       // columns of A per CTA tile = MMA M
+constexpr int kChunkTiles = 4;    // stages per exact accumulation chunk (256 rows)
+constexpr int kStages = 2;
+constexpr int kConvWarps = 8;
+constexpr int kThreads = (2 + kConvWarps) * 32;
+constexpr long long kWaitBudget = 4000000000LL;  // ~2 s at 2 GHz
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Bounded parity wait; false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t done = 0;
+  long long t0 = clock64();
+  while (true) {
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (clock64() - t0 > kWaitBudget) return false;
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                            int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, "
+      "{%3, %4}], [%2];" ::"r"(smem_u32(dst)),
+      "l"(map), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row core
+// groups 1024 bytes apart (SBO), sm_100 descriptor version 1.
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1 << 16;             // leading byte offset (unused for this layout)
+  d |= (uint64_t)(1024 >> 4) << 32;   // stride byte offset
+  d |= (uint64_t)1 << 46;             // descriptor version
+  d |= (uint64_t)2 << 61;             // SWIZZLE_128B
+  return d;
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7])
+      : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_wait_ld() {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Exact rint for |y| < 2^22 (round to nearest even through the FP32 adder).
+__device__ __forceinline__ float rint_small(float y) {
+  const float magic = 12582912.0f;  // 1.5 * 2^23
+  return __fsub_rn(__fadd_rn(y, magic), magic);
+}
+
+// FP32 accumulator holding an exact integer (|v| < 2^24) -> int32.
+__device__ __forceinline__ int f2i_exact(uint32_t bits) { return __float2int_rn(__uint_as_float(bits)); }
+
+struct TcArgs {
+  int64_t m, n;
+  int c, c_pad;
+  const int* colexp;       // E_j per column (pre-pass)
+  long long* partial;      // [ks][c][n] int64 slice-combined sums
+  int64_t kunit;           // rows of A per work unit (multiple of 256)
+  int ks;                  // work units along K
+  int64_t nstrips;         // column strips of 128
+  int* err;                // device error word
+};
+
+// Dynamic shared memory per stage: S digit tiles (128 x 64 BF16 = 16 KB each),
+// the G_q tile (c_pad x 64 BF16), the A tile (64 x 128 FP32 = 32 KB).
+template <int S, int CP>
+struct Layout {
+  static constexpr int kOpBytes = kTileN * kTileK * 2;          // 16384
+  static constexpr int kGBytes = CP * kTileK * 2;               // CP * 128
+  static constexpr int kABytes = kTileK * kTileN * 4;           // 32768
+  static constexpr int kStageBytes = S * kOpBytes + kGBytes + kABytes;
+  static constexpr int kBarOffset = kStages * kStageBytes;
+  static constexpr int kTotal = kBarOffset + 256 + 1024;        // + alignment slack
+  static constexpr uint32_t kTmemCols = (2 * S * CP <= 32) ? 32
+                                        : (2 * S * CP <= 64) ? 64
+                                        : (2 * S * CP <= 128) ? 128
+                                        : (2 * S * CP <= 256) ? 256 : 512;
+};
+
+template <int S, int CP>
+__global__ void __launch_bounds__(kThreads, 1)
+    sketch_tc_kernel(const __grid_constant__ CUtensorMap mapA,
+                     const __grid_constant__ CUtensorMap mapG, TcArgs g) {
+  using L = Layout<S, CP>;
+  static_assert(2 * S * CP <= 512, "accumulators exceed tensor memory");
+  static_assert(CP % 16 == 0 && CP >= 16 && CP <= 128, "N must be a multiple of 16, <= 128");
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                             ~uintptr_t(1023));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L::kBarOffset);
+  uint64_t* full = bars;                  // [kStages] TMA landed
+  uint64_t* conv = bars + kStages;        // [kStages] digit tiles written
+  uint64_t* empty = bars + 2 * kStages;   // [kStages] MMAs done with the stage
+  uint64_t* accf = bars + 3 * kStages;    // [2] chunk accumulators complete
+  uint64_t* acce = bars + 3 * kStages + 2;// [2] chunk accumulators drained
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 * kStages + 4);
+  int* s_abort = reinterpret_cast<int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&conv[s], kConvWarps * 32);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&accf[b], 1);
+      mbar_init(&acce[b], kConvWarps * 32);
+    }
+    *s_abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(L::kTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  // flat schedule: this CTA's work units (strip, z), each split into 64-row tiles
+  const int64_t nunits = g.nstrips * g.ks;
+  auto unit_tiles = [&](int64_t u) -> int {
+    int64_t z = u / g.nstrips;
+    int64_t k0 = z * g.kunit, k1 = min(g.m, k0 + g.kunit);
+    return (int)((k1 - k0 + kTileK - 1) / kTileK);
+  };
+
+  if (warp == 0) {
+    // ---------------- TMA producer ----------------
+    if (lane == 0) {
+      uint32_t t = 0;
+      for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
+        const int64_t strip = u % g.nstrips, z = u / g.nstrips;
+        const int nt = unit_tiles(u);
+        for (int i = 0; i < nt; ++i, ++t) {
+          const uint32_t s = t % kStages;
+          if (t >= kStages && !mbar_wait(&empty[s], ((t / kStages) - 1) & 1)) {
+            atomicCAS(g.err, 0, kDevTimeout);
+            *s_abort = 1;
+            break;
+          }
+          if (*((volatile int*)s_abort)) break;
+          uint8_t* st = smem + s * L::kStageBytes;
+          mbar_expect_tx(&full[s], (uint32_t)(L::kGBytes + L::kABytes));
+          const int krow = (int)(z * g.kunit) + i * kTileK;
+          tma_load_2d(st + S * L::kOpBytes + L::kGBytes, &mapA, &full[s],
+                      (int)(strip * kTileN), krow);
+          tma_load_2d(st + S * L::kOpBytes, &mapG, &full[s], krow, 0);
+        }
+        if (*((volatile int*)s_abort)) break;
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(CP >> 3) << 17) |
+                             ((uint32_t)(kTileN >> 4) << 24);
+      uint32_t t = 0, chunk = 0;
+      bool ok = true;
+      for (int64_t u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
+        const int nt = unit_tiles(u);
+        for (int i = 0; i < nt && ok; ++i, ++t) {
+          const uint32_t s = t % kStages;
+          const bool first = (i % kChunkTiles) == 0;
+          const bool last = (i % kChunkTiles) == kChunkTiles - 1 || i == nt - 1;
+          const uint32_t buf = chunk & 1;
+          if (first && chunk >= 2 && !mbar_wait(&acce[buf], ((chunk >> 1) - 1) & 1)) { ok = false; break; }
+          if (!mbar_wait(&conv[s], (t / kStages) & 1)) { ok = false; break; }
+          tc_fence_after();
+          uint8_t* st = smem + s * L::kStageBytes;
+          const uint32_t gaddr = smem_u32(st + S * L::kOpBytes);
+#pragma unroll
+          for (int sl = 0; sl < S; ++sl) {
+            const uint32_t aaddr = smem_u32(st + sl * L::kOpBytes);
+            const uint32_t dcol = tmem + (uint32_t)((buf * S + sl) * CP);
+#pragma unroll
+            for (int kk = 0; kk < kTileK / 16; ++kk)
+              mma_bf16(dcol, desc_sw128(aaddr + kk * 32), desc_sw128(gaddr + kk * 32), idesc,
+                       (first && kk == 0) ? 0u : 1u);
+          }
+          mma_commit(&empty[s]);
+          if (last) {
+            mma_commit(&accf[buf]);
+            ++chunk;
+          }
+        }
+      }
+      if (!ok) { atomicCAS(g.err, 0, kDevTimeout); *((volatile int*)s_abort) = 1; }
+    }
+  } else {
+    // ---------------- converters + drain ----------------
+    const int ct = threadIdx.x - 64;           // 0..255
+    const int jl = ct & (kTileN - 1);          // this thread's column in the tile
+    const int half = ct >> 7;                  // k-group parity / accumulator half
+    const int q = warp & 3;                    // TMEM lane quarter of this warp
+    const int dh = (warp - 2) >> 2;            // 0: warps 2-5, 1: warps 6-9
+    constexpr int HALF = CP / 2;               // sketch rows per drain thread
+    long long acc[HALF];
+#pragma unroll
+    for (int r = 0; r < HALF; ++r) acc[r] = 0;
+    uint32_t t = 0, chunk = 0;
+    bool ok = true;
+    for (int64_t u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
+      const int64_t strip = u % g.nstrips, z = u / g.nstrips;
+      const int nt = unit_tiles(u);
+      const int64_t jg = strip * kTileN + jl;
+      const int E = jg < g.n ? g.colexp[jg] : 0;
+      const float sc = ldexpf(1.0f, min(8 - E, 126));  // columns below 2^-118: digits lose range
+      for (int i = 0; i < nt && ok; ++i, ++t) {
+        const uint32_t s = t % kStages;
+        if (!mbar_wait(&full[s], (t / kStages) & 1)) { ok = false; break; }
+        uint8_t* st = smem + s * L::kStageBytes;
+        const float* At = reinterpret_cast<const float*>(st + S * L::kOpBytes + L::kGBytes);
+        // 8 groups of 8 rows; this thread handles groups half, half+2, half+4, half+6
+#pragma unroll
+        for (int it = 0; it < 4; ++it) {
+          const int kg = half + 2 * it;
+          uint32_t packed[S][4];
+#pragma unroll
+          for (int e = 0; e < 8; e += 2) {
+            float y0 = At[(kg * 8 + e) * kTileN + jl] * sc;
+            float y1 = At[(kg * 8 + e + 1) * kTileN + jl] * sc;
+#pragma unroll
+            for (int sl = S - 1; sl >= 0; --sl) {
+              float d0 = rint_small(y0), d1 = rint_small(y1);
+              packed[sl][e >> 1] = (__float_as_uint(d0) >> 16) | (__float_as_uint(d1) & 0xFFFF0000u);
+              y0 = __fmul_rn(__fsub_rn(y0, d0), 256.0f);
+              y1 = __fmul_rn(__fsub_rn(y1, d1), 256.0f);
+            }
+          }
+          // K-major SW128: row jl, 16-byte chunk kg at (kg ^ (jl & 7))
+          const uint32_t off = (uint32_t)((jl >> 3) * 1024 + (jl & 7) * 128 + ((kg ^ (jl & 7)) << 4));
+#pragma unroll
+          for (int sl = 0; sl < S; ++sl) {
+            uint4 v = make_uint4(packed[sl][0], packed[sl][1], packed[sl][2], packed[sl][3]);
+            *reinterpret_cast<uint4*>(st + sl * L::kOpBytes + off) = v;
+          }
+        }
+        fence_async_smem();
+        mbar_arrive(&conv[s]);
+        const bool last = (i % kChunkTiles) == kChunkTiles - 1 || i == nt - 1;
+        if (last) {
+          // drain: accumulators of this chunk -> int64
+          const uint32_t buf = chunk & 1;
+          if (!mbar_wait(&accf[buf], (chunk >> 1) & 1)) { ok = false; break; }
+          tc_fence_after();
+#pragma unroll
+          for (int gcol = 0; gcol < HALF; gcol += 8) {
+            uint32_t r[S][8];
+#pragma unroll
+            for (int sl = 0; sl < S; ++sl)
+              tmem_ld8(tmem + ((uint32_t)(q * 32) << 16) +
+                           (uint32_t)((buf * S + sl) * CP + dh * HALF + gcol),
+                       r[sl]);
+            tmem_wait_ld();
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+              long long v = 0;
+#pragma unroll
+              for (int sl = S - 1; sl >= 0; --sl) v = v * 256 + (long long)f2i_exact(r[sl][e]);
+              acc[gcol + e] += v;
+            }
+          }
+          tc_fence_before();
+          mbar_arrive(&acce[buf]);
+          ++chunk;
+        }
+      }
+      if (!ok) break;
+      // unit done: write this thread's (rows, column) sums and reset
+      const int jt = q * 32 + lane;   // the column this thread drained (TMEM lane)
+      const int64_t jw = strip * kTileN + jt;
+#pragma unroll
+      for (int r = 0; r < HALF; ++r) {
+        const int row = dh * HALF + r;
+        if (row < g.c && jw < g.n) g.partial[((int64_t)z * g.c + row) * g.n + jw] = acc[r];
+        acc[r] = 0;
+      }
+    }
+    if (!ok) { atomicCAS(g.err, 0, kDevTimeout); *((volatile int*)s_abort) = 1; }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(L::kTmemCols));
+  }
+}
+
+// ---- column scales: E_j with max_k |A(k,j)| < 2^E_j --------------------------
+__global__ void colmax_kernel(const float* __restrict__ A, int64_t lda, int64_t m, int64_t n,
+                              int64_t rows_per_cta, unsigned* __restrict__ colmax_bits) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const int64_t r0 = (int64_t)blockIdx.y * rows_per_cta, r1 = min(m, r0 + rows_per_cta);
+  unsigned mx = 0;
+  for (int64_t k = r0; k < r1; ++k) {
+    unsigned b = __float_as_uint(A[k * lda + j]) & 0x7FFFFFFFu;
+    mx = b > mx ? b : mx;  // |x| compares as an unsigned integer (NaN sorts above Inf)
+  }
+  atomicMax(&colmax_bits[j], mx);
+}
+
+__global__ void colexp_kernel(const unsigned* __restrict__ colmax_bits, int64_t n,
+                              int* __restrict__ colexp) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const unsigned b = colmax_bits[j];
+  int E = 0;
+  if (b >= 0x7F800000u) E = 1 << 20;          // Inf/NaN: flagged by the reduction
+  else if (b != 0) frexpf(__uint_as_float(b), &E);
+  colexp[j] = E;
+}
+
+// Y[i, j] = 2^(E_j - 8S) sum_z partial[z][i][j], plus per-CTA sums of squares.
+__global__ void tc_reduce_kernel(const long long* __restrict__ partial, int ks, int64_t c,
+                                 int64_t n, int S, const int* __restrict__ colexp,
+                                 double* __restrict__ Y, double* __restrict__ sumsq_part,
+                                 int64_t per_cta) {
+  __shared__ double red[8];
+  const int64_t total = c * n;
+  const int64_t beg = (int64_t)blockIdx.x * per_cta, end = min(total, beg + per_cta);
+  double ss = 0.0;
+  for (int64_t e = beg + threadIdx.x; e < end; e += 256) {
+    long long s = 0;
+    for (int z = 0; z < ks; ++z) s += partial[(int64_t)z * total + e];
+    const int64_t j = e % n;
+    const int E = colexp[j];
+    double y = (E >= (1 << 20)) ? __longlong_as_double(0x7FF8000000000000LL)
+                                : ldexp((double)s, E - 8 * S);
+    Y[e] = y;
+    ss = fma(y, y, ss);
+  }
+  for (int o = 16; o > 0; o >>= 1) ss += __shfl_down_sync(0xffffffffu, ss, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = ss;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += red[w];
+    sumsq_part[blockIdx.x] = t;
+  }
+}
+
+// ---- G_q: 8-bit Gaussian sketch as BF16 (row stride ldq, zero padded) --------
+__global__ void gaussian_q8_kernel(const double* __restrict__ G, int64_t c, int64_t m,
+                                   int64_t ldq, uint16_t* __restrict__ Gq) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= c * ldq) return;
+  const int64_t i = e / ldq, k = e - i * ldq;
+  float q = 0.0f;
+  if (k < m) {
+    double v = rint(16.0 * G[i * m + k]);
+    v = v > 127.0 ? 127.0 : (v < -127.0 ? -127.0 : v);
+    q = (float)v;
+  }
+  Gq[e] = (uint16_t)(__float_as_uint(q) >> 16);  // exact: |q| <= 127
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+template <int S, int CP>
+cudaError_t launch_tc(const LaunchEnv& env, const CUtensorMap& mA, const CUtensorMap& mG,
+                      const TcArgs& a, int grid) {
+  using L = Layout<S, CP>;
+  cudaError_t e = cudaFuncSetAttribute((const void*)sketch_tc_kernel<S, CP>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, L::kTotal);
+  if (e != cudaSuccess) return e;
+  sketch_tc_kernel<S, CP><<<grid, kThreads, L::kTotal, env.stream>>>(mA, mG, a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int sketch_tc_cpad(int c, int S) {
+  int cp = (c + 15) / 16 * 16;
+  if (cp < 16) cp = 16;
+  // instantiated widths
+  const int widths[] = {16, 32, 48, 64, 80, 96, 128};
+  for (int w : widths)
+    if (w >= cp && 2 * S * w <= 512) return w;
+  return -1;
+}
+
+size_t sketch_tc_scratch_bytes(int64_t c, int64_t m, int64_t n, int ks) {
+  const int64_t ldq = (m + 63) / 64 * 64;
+  size_t b = 0;
+  auto add = [&](size_t x) { b += (x + 255) / 256 * 256; };
+  add(sizeof(uint16_t) * (size_t)(c * ldq));     // G_q
+  add(sizeof(unsigned) * (size_t)n);             // column max bits
+  add(sizeof(int) * (size_t)n);                  // column exponents
+  add(sizeof(long long) * (size_t)ks * c * n);   // partial sums
+  return b;
+}
+
+int sketch_tc_plan_ks(const LaunchEnv& env, int64_t m, int64_t n) {
+  const int64_t strips = (n + kTileN - 1) / kTileN;
+  const int64_t chunks = (m + kTileK * kChunkTiles - 1) / (kTileK * kChunkTiles);
+  // about 8 work units per SM (balance), each at least 2 chunks of rows
+  int64_t ks = (8LL * env.num_sms + strips - 1) / strips;
+  int64_t ks_max = (chunks + 1) / 2;
+  if (ks > ks_max) ks = ks_max;
+  return ks < 1 ? 1 : (int)ks;
+}
+
+cudaError_t launch_sketch_tc(const LaunchEnv& env, int S, const double* G, int64_t c,
+                             const float* A, int64_t lda, int64_t m, int64_t n, void* scratch,
+                             int ks, double* Y, double* sumsq_part, int64_t* nparts, int* err) {
+  const int CP = sketch_tc_cpad((int)c, S);
+  if (CP < 0) return cudaErrorInvalidValue;
+  const int64_t ldq = (m + 63) / 64 * 64;
+  char* p = static_cast<char*>(scratch);
+  auto take = [&](size_t x) { char* r = p; p += (x + 255) / 256 * 256; return r; };
+  uint16_t* Gq = (uint16_t*)take(sizeof(uint16_t) * (size_t)(c * ldq));
+  unsigned* cmax = (unsigned*)take(sizeof(unsigned) * (size_t)n);
+  int* cexp = (int*)take(sizeof(int) * (size_t)n);
+  long long* partial = (long long*)take(sizeof(long long) * (size_t)ks * c * n);
+
+  // G_q (BF16, rows padded to a multiple of 64 so TMA strides are 16-byte multiples)
+  {
+    int64_t tot = c * ldq;
+    gaussian_q8_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, env.stream>>>(G, c, m, ldq, Gq);
+  }
+  // column scales
+  cudaError_t e = cudaMemsetAsync(cmax, 0, sizeof(unsigned) * (size_t)n, env.stream);
+  if (e != cudaSuccess) return e;
+  {
+    int64_t rows_per = 512;
+    dim3 grid((unsigned)((n + 255) / 256), (unsigned)((m + rows_per - 1) / rows_per));
+    colmax_kernel<<<grid, 256, 0, env.stream>>>(A, lda, m, n, rows_per, cmax);
+    colexp_kernel<<<(unsigned)((n + 255) / 256), 256, 0, env.stream>>>(cmax, n, cexp);
+  }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return cudaErrorNotSupported;
+  CUtensorMap mA, mG;
+  {
+    cuuint64_t gdim[2] = {(cuuint64_t)n, (cuuint64_t)m};
+    cuuint64_t gstride[1] = {(cuuint64_t)lda * 4};
+    cuuint32_t box[2] = {kTileN, kTileK};
+    cuuint32_t es[2] = {1, 1};
+    if (enc(&mA, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)A, gdim, gstride, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return cudaErrorInvalidValue;
+  }
+  {
+    cuuint64_t gdim[2] = {(cuuint64_t)ldq, (cuuint64_t)c};
+    cuuint64_t gstride[1] = {(cuuint64_t)ldq * 2};
+    cuuint32_t box[2] = {kTileK, (cuuint32_t)CP};
+    cuuint32_t es[2] = {1, 1};
+    if (enc(&mG, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)Gq, gdim, gstride, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return cudaErrorInvalidValue;
+  }
+  TcArgs a;
+  a.m = m; a.n = n; a.c = (int)c; a.c_pad = CP; a.colexp = cexp; a.partial = partial;
+  const int64_t chunks = (m + kTileK * kChunkTiles - 1) / (kTileK * kChunkTiles);
+  const int64_t chunks_per = (chunks + ks - 1) / ks;
+  a.kunit = chunks_per * kTileK * kChunkTiles;
+  a.ks = (int)((m + a.kunit - 1) / a.kunit);
+  a.nstrips = (n + kTileN - 1) / kTileN;
+  a.err = err;
+  int64_t units = a.nstrips * a.ks;
+  int grid = (int)(units < env.num_sms ? units : env.num_sms);
+
+#define CUR_TC_CASE(SS, CC)                                    \
+  if (S == SS && CP == CC) e = launch_tc<SS, CC>(env, mA, mG, a, grid); \
+  else
+  CUR_TC_CASE(1, 16) CUR_TC_CASE(1, 32) CUR_TC_CASE(1, 48) CUR_TC_CASE(1, 64)
+  CUR_TC_CASE(1, 80) CUR_TC_CASE(1, 96) CUR_TC_CASE(1, 128)
+  CUR_TC_CASE(2, 16) CUR_TC_CASE(2, 32) CUR_TC_CASE(2, 48) CUR_TC_CASE(2, 64)
+  CUR_TC_CASE(2, 80) CUR_TC_CASE(2, 96) CUR_TC_CASE(2, 128)
+  CUR_TC_CASE(3, 16) CUR_TC_CASE(3, 32) CUR_TC_CASE(3, 48) CUR_TC_CASE(3, 64)
+  CUR_TC_CASE(3, 80)
+  e = cudaErrorInvalidValue;
+#undef CUR_TC_CASE
+  if (e != cudaSuccess) return e;
+
+  const int64_t total = c * n;
+  const int64_t per = 16384;
+  const int64_t nblk = (total + per - 1) / per;
+  tc_reduce_kernel<<<(unsigned)nblk, 256, 0, env.stream>>>(partial, a.ks, c, n, S, cexp, Y,
+                                                           sumsq_part, per);
+  *nparts = nblk;
+  return cudaGetLastError();
+}
+
+}  // namespace cur

@@ -152,7 +152,7 @@ def _decided_prefix(ref, b, col_scale, tau=1e-9):
     return min(ref.rank, k * b)
 
 
-def _check_parity(A, got, ref, b, require_full=True):
+def _check_parity(A, got, ref, b, require_full=True, rho_rtol=None):
     n_dec = _decided_prefix(ref, b, ref.maxabsY)
     if require_full:
         assert n_dec == ref.rank, "oracle decisions at rounding level; choose another seed"
@@ -163,6 +163,8 @@ def _check_parity(A, got, ref, b, require_full=True):
     assert got.rank == ref.rank and got.iterations == ref.iters and got.status == ref.status
     hist_prev = np.concatenate([[1.0], ref.rho_hist[:-1]])
     bound = 1e-10 * ref.rho_hist + 20 * (b + 1) * U_RND * np.cumsum(hist_prev)
+    if rho_rtol is not None:
+        bound = np.maximum(bound, rho_rtol * ref.rho_hist)
     assert np.all(np.abs(got.rho_history - ref.rho_hist) <= bound)
     assert abs(got.rho - ref.rho) <= bound[-1]
     if ref.rank:
