@@ -132,14 +132,109 @@ __global__ void __launch_bounds__(kThreads) lupp_kernel(LuppParams p) {
   }
 }
 
+// Same selection with each CTA's candidate slice resident in shared memory:
+// Wsh[rr * per + li] for candidate lo + li.  Used whenever the slice fits.
+// The elimination of a step is spread over (row, candidate) pairs so that all
+// threads work even when a CTA owns fewer candidates than threads.
+__global__ void __launch_bounds__(kThreads) lupp_smem_kernel(LuppParams p, int per) {
+  extern __shared__ double sh[];
+  double* Wsh = sh;                                   // nr * per
+  double* pv = Wsh + (size_t)p.nr * per;              // nr
+  double* lm = pv + p.nr;                             // per multipliers (0: skip)
+  __shared__ Best red[kThreads / 32];
+  __shared__ Best s_win;
+  __shared__ int s_wcta;
+  const int G = gridDim.x, cta = blockIdx.x, tid = threadIdx.x;
+  const int lane = tid & 31, wid = tid >> 5;
+  const int64_t lo = (int64_t)cta * per;
+  const int own = (int)max((int64_t)0, min((int64_t)per, p.ncand - lo));
+  const int stride = p.nr + 2;
+
+  for (int e = tid; e < p.nr * own; e += kThreads) {
+    int rr = e / own, li = e - rr * own;
+    Wsh[rr * per + li] = p.X[rr * p.ldx + lo + li];
+  }
+  __syncthreads();
+
+  for (int t = 0; t < p.steps; ++t) {
+    double* slot = p.slots + ((size_t)(t & 1) * G) * stride;
+    Best b{-1.0, LLONG_MAX};
+    for (int li = tid; li < own; li += kThreads) {
+      if (p.mask[lo + li]) continue;
+      double a = fabs(Wsh[t * per + li]);
+      if (better(a, lo + li, b)) { b.a = a; b.i = lo + li; }
+    }
+    b = warp_best(b);
+    if (lane == 0) red[wid] = b;
+    __syncthreads();
+    if (wid == 0) {
+      Best c = lane < kThreads / 32 ? red[lane] : Best{-1.0, LLONG_MAX};
+      c = warp_best(c);
+      if (lane == 0) s_win = c;
+    }
+    __syncthreads();
+    Best mine = s_win;
+    double* my = slot + (size_t)cta * stride;
+    if (tid == 0) { my[0] = mine.a; my[1] = __longlong_as_double(mine.i); }
+    if (mine.i != LLONG_MAX)
+      for (int rr = t + tid; rr < p.nr; rr += kThreads) my[2 + rr] = Wsh[rr * per + (mine.i - lo)];
+    __threadfence();
+    if (!grid_barrier(p.bar, p.st)) return;
+    if (wid == 0) {
+      Best c{-1.0, LLONG_MAX};
+      int ccta = -1;
+      for (int g = lane; g < G; g += 32) {
+        const double* s = slot + (size_t)g * stride;
+        double a = __ldcg(s);
+        long long i = __double_as_longlong(__ldcg(s + 1));
+        if (better(a, i, c)) { c.a = a; c.i = i; ccta = g; }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        double oa = __shfl_down_sync(0xffffffffu, c.a, o);
+        long long oi = __shfl_down_sync(0xffffffffu, c.i, o);
+        int oc = __shfl_down_sync(0xffffffffu, ccta, o);
+        if (better(oa, oi, c)) { c.a = oa; c.i = oi; ccta = oc; }
+      }
+      if (lane == 0) { s_win = c; s_wcta = ccta; }
+    }
+    __syncthreads();
+    Best w = s_win;
+    if (w.i == LLONG_MAX) {
+      if (tid == 0) dev_set_err(p.st, kDevNoCandidate);
+      return;
+    }
+    const double* wcol = slot + (size_t)s_wcta * stride + 2;
+    for (int rr = t + tid; rr < p.nr; rr += kThreads) pv[rr] = __ldcg(wcol + rr);
+    if (cta == 0 && tid == 0) p.piv[t] = w.i;
+    if (tid == 0 && w.i >= lo && w.i < lo + own) p.mask[w.i] = 1;
+    __syncthreads();
+    if (w.a > 0.0 && t + 1 < p.nr) {
+      const double pt = pv[t];
+      for (int li = tid; li < own; li += kThreads)
+        lm[li] = p.mask[lo + li] ? 0.0 : Wsh[t * per + li] / pt;
+      __syncthreads();
+      const int rows = p.nr - t - 1;
+      for (int e = tid; e < rows * own; e += kThreads) {
+        int rr = t + 1 + e / own, li = e % own;
+        double l = lm[li];
+        if (l != 0.0) Wsh[rr * per + li] = fma(-l, pv[rr], Wsh[rr * per + li]);
+      }
+    }
+    __syncthreads();
+  }
+}
+
 }  // namespace
 
 size_t lupp_work_doubles(int64_t nr, int64_t ncand, int max_grid) {
   return (size_t)nr * ncand + 2 * (size_t)max_grid * (nr + 2);
 }
 
+// Largest dynamic shared memory the resident-slice variant may use per CTA.
+constexpr size_t kLuppSmemMax = 200 * 1024;
+
 int lupp_grid(const LaunchEnv& env, int64_t nr, int64_t ncand) {
-  int64_t g = (nr * ncand + 16383) / 16384;
+  int64_t g = (nr * ncand + 4095) / 4096;
   int64_t cap = env.num_sms;
   if (g > cap) g = cap;
   if (g > ncand) g = ncand;
@@ -155,6 +250,19 @@ cudaError_t launch_lupp(const LaunchEnv& env, const double* X, int64_t ldx, int6
   LuppParams p;
   p.X = X; p.ldx = ldx; p.nr = (int)nr; p.ncand = ncand; p.steps = (int)steps;
   p.mask = mask; p.piv = piv; p.W = w.W; p.slots = w.slot_val; p.bar = w.bar; p.st = st;
+  const int64_t per = (ncand + grid - 1) / grid;
+  const size_t smem_res = sizeof(double) * ((size_t)nr * per + nr + per);
+  if (smem_res <= kLuppSmemMax) {
+    if (smem_res > 48 * 1024) {
+      e = cudaFuncSetAttribute((const void*)lupp_smem_kernel,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_res);
+      if (e != cudaSuccess) return e;
+    }
+    int per_i = (int)per;
+    void* args[] = {&p, &per_i};
+    return cudaLaunchCooperativeKernel((const void*)lupp_smem_kernel, dim3(grid), dim3(kThreads),
+                                       args, smem_res, env.stream);
+  }
   void* args[] = {&p};
   size_t smem = sizeof(double) * (size_t)(nr > 0 ? nr : 1);
   return cudaLaunchCooperativeKernel((const void*)lupp_kernel, dim3(grid), dim3(kThreads), args,

@@ -16,6 +16,13 @@
 
 #include "gridbar.cuh"
 
+// Shared-memory bytes of the single-CTA variant (0 if it does not apply).
+static size_t qrcp_small_smem(int64_t p, int64_t q) {
+  int64_t kmax = p < q ? p : q;
+  size_t b = sizeof(double) * (size_t)(q * p + p * p + q + 4 * kmax) + sizeof(int) * (size_t)(2 * q);
+  return b <= 200 * 1024 ? b : 0;
+}
+
 namespace cur {
 namespace {
 
@@ -208,6 +215,142 @@ __global__ void __launch_bounds__(kThreads) qrcp_solve_kernel(SolveParams S) {
   }
 }
 
+// Single-CTA variant for small p, q (every N_k and small cores).  GB300 runs
+// FP64 at ~2 DFMA/clk/SM, so warp-wide FP64 reductions and redundant lane
+// arithmetic dominate small problems; this variant gives every thread one
+// column: R is row-major in shared memory (R[i*q + col]: consecutive lanes,
+// consecutive columns), the pivot column is read as a broadcast, and no
+// reduction is needed except the argmax.  Pivot columns are frozen in place,
+// so reflector j is (vhead[j], R[j+1.., perm[j]]) and R(i, i') = R[i, perm[i']]
+// for i < i'.  The same launch forms X = P [R_11^{-1} Q_1^T; 0] with one thread
+// per column of the identity (vectors in shared memory).
+constexpr int kSmallThreads = 256;
+
+__global__ void __launch_bounds__(kSmallThreads) qrcp_small_kernel(QrcpParams P, double* X,
+                                                                   int64_t ldx) {
+  extern __shared__ double sm[];
+  const int p = (int)P.p, q = (int)P.q, kmax = p < q ? p : q;
+  double* R = sm;                                   // p * q, row-major
+  double* Y = R + (size_t)p * q;                    // p * p, row-major (column l = thread l)
+  double* nrm = Y + (size_t)p * p;                  // q
+  double* rdiag = nrm + q;                          // kmax
+  double* rinv = rdiag + kmax;                      // kmax
+  double* tau = rinv + kmax;                        // kmax
+  double* vhead = tau + kmax;                       // kmax
+  int* perm = reinterpret_cast<int*>(vhead + kmax); // q
+  int* used = perm + q;                             // q
+  __shared__ double s_red_a[kSmallThreads / 32];
+  __shared__ int s_red_i[kSmallThreads / 32];
+  __shared__ int s_jp, s_k;
+  __shared__ double s_tau;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+
+  for (int e = tid; e < p * q; e += kSmallThreads) {
+    int i = e / q, col = e - i * q;
+    R[e] = P.M[(int64_t)i * P.ldm + col];
+  }
+  for (int col = tid; col < q; col += kSmallThreads) used[col] = 0;
+  __syncthreads();
+
+  for (int j = 0; j < kmax; ++j) {
+    // squared norms over rows j..p-1 of the unused columns, one thread each
+    double ba = -1.0;
+    int bi = INT_MAX;
+    for (int col = tid; col < q; col += kSmallThreads) {
+      if (used[col]) continue;
+      double sacc = 0.0;
+      for (int i = j; i < p; ++i) { double x = R[i * q + col]; sacc = fma(x, x, sacc); }
+      if (sacc > ba) { ba = sacc; bi = col; }   // increasing col per thread: ties keep the smaller
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      double oa = __shfl_down_sync(0xffffffffu, ba, o);
+      int oi = __shfl_down_sync(0xffffffffu, bi, o);
+      if (oa > ba || (oa == ba && oi < bi)) { ba = oa; bi = oi; }
+    }
+    if (lane == 0) { s_red_a[wid] = ba; s_red_i[wid] = bi; }
+    __syncthreads();
+    if (tid == 0) {
+      double a = -1.0; int ii = INT_MAX;
+      for (int w = 0; w < kSmallThreads / 32; ++w)
+        if (s_red_a[w] > a || (s_red_a[w] == a && s_red_i[w] < ii)) { a = s_red_a[w]; ii = s_red_i[w]; }
+      double x0 = R[j * q + ii];
+      double normx = sqrt(a);
+      double alpha = normx == 0.0 ? 0.0 : (x0 >= 0.0 ? -normx : normx);
+      double vh = x0 - alpha;
+      double t = 0.0;
+      if (alpha != 0.0) {            // tau = 2 / ||v||^2, v = (x0 - alpha, x_{j+1..p-1})
+        double vv = vh * vh;
+        for (int i = j + 1; i < p; ++i) { double x = R[i * q + ii]; vv = fma(x, x, vv); }
+        t = 2.0 / vv;
+      }
+      s_jp = ii; s_tau = t;
+      perm[j] = ii; used[ii] = 1; rdiag[j] = alpha; vhead[j] = vh; tau[j] = t;
+    }
+    __syncthreads();
+    const int jp = s_jp;
+    const double tj = s_tau;
+    if (tj != 0.0) {
+      const double vh = vhead[j];
+      for (int col = tid; col < q; col += kSmallThreads) {
+        if (used[col]) continue;
+        double d = vh * R[j * q + col];
+        for (int i = j + 1; i < p; ++i) d = fma(R[i * q + jp], R[i * q + col], d);
+        d *= tj;
+        R[j * q + col] = fma(-d, vh, R[j * q + col]);
+        for (int i = j + 1; i < p; ++i) R[i * q + col] = fma(-d, R[i * q + jp], R[i * q + col]);
+      }
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    double thr;
+    double r0 = kmax > 0 ? fabs(rdiag[0]) : 0.0;
+    if (P.thr_mode == 0) {
+      thr = (double)(p > q ? p : q) * 0x1.0p-52 * r0;
+    } else if (P.thr_mode == 1) {
+      thr = P.thr;
+    } else {
+      double sc = *P.scale_dev;
+      if (sc < 0.0) { sc = 0x1.0p-52 * r0; *P.scale_dev = sc; }
+      thr = P.thr * sc;
+    }
+    int k = 0;
+    while (k < kmax && fabs(rdiag[k]) > thr) ++k;
+    s_k = k;
+    *P.w.rank = k;
+    if (q > kmax) {  // columns never pivoted, in increasing order
+      int pos = kmax;
+      for (int col = 0; col < q; ++col)
+        if (!used[col]) perm[pos++] = col;
+    }
+  }
+  __syncthreads();
+  const int k = s_k;
+  for (int i = tid; i < k; i += kSmallThreads) rinv[i] = 1.0 / rdiag[i];
+  __syncthreads();
+  for (int l = tid; l < p; l += kSmallThreads) {
+    for (int i = 0; i < p; ++i) Y[i * p + l] = (i == l) ? 1.0 : 0.0;
+    for (int jj = 0; jj < k; ++jj) {   // y = H_{k-1} ... H_0 e_l
+      const double tjj = tau[jj];
+      if (tjj == 0.0) continue;
+      const int pc = perm[jj];
+      const double vh = vhead[jj];
+      double d = vh * Y[jj * p + l];
+      for (int i = jj + 1; i < p; ++i) d = fma(R[i * q + pc], Y[i * p + l], d);
+      d *= tjj;
+      Y[jj * p + l] = fma(-d, vh, Y[jj * p + l]);
+      for (int i = jj + 1; i < p; ++i) Y[i * p + l] = fma(-d, R[i * q + pc], Y[i * p + l]);
+    }
+    for (int i = k - 1; i >= 0; --i) {  // back substitution with R_11, column oriented
+      const double zi = Y[i * p + l] * rinv[i];
+      Y[i * p + l] = zi;
+      const int pc = perm[i];
+      for (int a = 0; a < i; ++a) Y[a * p + l] = fma(-zi, R[a * q + pc], Y[a * p + l]);
+    }
+    for (int i = 0; i < q; ++i) X[(int64_t)perm[i] * ldx + l] = (i < k) ? Y[i * p + l] : 0.0;
+  }
+}
+
 }  // namespace
 
 size_t qrcp_work_bytes(int64_t p, int64_t q, int max_grid) {
@@ -262,6 +405,15 @@ cudaError_t launch_qrcp_pinv(const LaunchEnv& env, const double* M, int64_t p, i
   QrcpParams P;
   P.M = M; P.p = p; P.q = q; P.ldm = ldm; P.thr_mode = thr_mode; P.thr = thr;
   P.scale_dev = scale_dev; P.w = w; P.st = st;
+  if (size_t ssm = qrcp_small_smem(p, q)) {
+    if (ssm > 48 * 1024) {
+      e = cudaFuncSetAttribute((const void*)qrcp_small_kernel,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm);
+      if (e != cudaSuccess) return e;
+    }
+    qrcp_small_kernel<<<1, kSmallThreads, ssm, env.stream>>>(P, X, ldx);
+    return cudaGetLastError();
+  }
   size_t smem = sizeof(double) * (size_t)p;
   if (smem > 48 * 1024) {
     e = cudaFuncSetAttribute((const void*)qrcp_factor_kernel,
