@@ -151,11 +151,73 @@ __global__ void __launch_bounds__(NT) sum_parts_kernel(const double* parts, int6
   if (threadIdx.x == 0) out[0] = s;
 }
 
+// Skinny products of the residual updates: D (M x N) = alpha op(A) B + beta Cin
+// with a small M (b or c rows), any K, a wide row-major B.  One thread owns 8
+// rows of one output column; op(A) is staged through shared memory in K
+// chunks of 32 and read as a broadcast, B is read coalesced along the column
+// index.  The grid has ceil(N/256) x ceil(M/8) small CTAs (hundreds), which the
+// block scheduler balances over the SMs without a half-empty last wave.
+constexpr int kSkRows = 8, kSkK = 32, kSkThreads = 256;
+
+template <bool TA>
+__global__ void __launch_bounds__(kSkThreads) gemm_skinny_kernel(GemmArgs g) {
+  __shared__ double As[kSkRows][kSkK];
+  __shared__ double red[kSkThreads / 32];
+  const int tid = threadIdx.x;
+  const int64_t j = (int64_t)blockIdx.x * kSkThreads + tid;
+  const int64_t r0 = (int64_t)blockIdx.y * kSkRows;
+  double acc[kSkRows];
+#pragma unroll
+  for (int r = 0; r < kSkRows; ++r) acc[r] = 0.0;
+  for (int64_t k0 = 0; k0 < g.K; k0 += kSkK) {
+    {
+      const int r = tid / kSkK, kk = tid % kSkK;   // 256 threads = 8 x 32 entries
+      const int64_t gr = r0 + r, gk = k0 + kk;
+      double v = 0.0;
+      if (gr < g.M && gk < g.K) v = TA ? g.A[gk * g.lda + gr] : g.A[gr * g.lda + gk];
+      As[r][kk] = v;
+    }
+    __syncthreads();
+    if (j < g.N) {
+      const int kend = (int)min((int64_t)kSkK, g.K - k0);
+      const double* B = static_cast<const double*>(g.B) + k0 * g.ldb + j;
+      for (int kk = 0; kk < kend; ++kk) {
+        const double b = B[(int64_t)kk * g.ldb];
+#pragma unroll
+        for (int r = 0; r < kSkRows; ++r) acc[r] = fma(As[r][kk], b, acc[r]);
+      }
+    }
+    __syncthreads();
+  }
+  double ss = 0.0;
+  if (j < g.N) {
+#pragma unroll
+    for (int r = 0; r < kSkRows; ++r) {
+      const int64_t gr = r0 + r;
+      if (gr >= g.M) break;
+      double d = g.alpha * acc[r];
+      if (g.beta != 0.0) d = fma(g.beta, g.Cin[gr * g.ldcin + j], d);
+      g.D[gr * g.ldd + j] = d;
+      ss = fma(d, d, ss);
+    }
+  }
+  if (g.sumsq_part) {
+    double s = block_sum(ss, red);
+    if (tid == 0) g.sumsq_part[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = s;
+  }
+}
+
 constexpr int64_t kReducePerCta = 8192;
 
 }  // namespace
 
+static bool use_skinny(const GemmArgs& g) {
+  return !g.transB && !g.b_is_f32 && g.ksplit <= 1 && g.M <= 256;
+}
+
 int64_t gemm_num_sumsq_parts(const GemmArgs& g) {
+  if (use_skinny(g))
+    return ((g.N + kSkThreads - 1) / kSkThreads) * ((g.M + kSkRows - 1) / kSkRows);
   if (g.ksplit > 1) return (g.M * g.N + kReducePerCta - 1) / kReducePerCta;
   return ((g.M + BM - 1) / BM) * ((g.N + BN - 1) / BN);
 }
@@ -167,6 +229,12 @@ cudaError_t launch_gemm(const LaunchEnv& env, const GemmArgs& g) {
   a.ksplit = ks;
   if (g.K <= 0) {  // D = beta * Cin (no product)
     a.alpha = 0.0;
+  }
+  if (use_skinny(a)) {
+    dim3 grid((unsigned)((g.N + kSkThreads - 1) / kSkThreads), (unsigned)((g.M + kSkRows - 1) / kSkRows));
+    if (a.transA) gemm_skinny_kernel<true><<<grid, kSkThreads, 0, env.stream>>>(a);
+    else gemm_skinny_kernel<false><<<grid, kSkThreads, 0, env.stream>>>(a);
+    return cudaGetLastError();
   }
   dim3 grid((unsigned)((g.N + BN - 1) / BN), (unsigned)((g.M + BM - 1) / BM), (unsigned)ks);
   if (a.b_is_f32) gemm_kernel<true><<<grid, NT, 0, env.stream>>>(a);

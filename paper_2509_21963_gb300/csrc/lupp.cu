@@ -209,15 +209,14 @@ __global__ void __launch_bounds__(kThreads) lupp_smem_kernel(LuppParams p, int p
     if (tid == 0 && w.i >= lo && w.i < lo + own) p.mask[w.i] = 1;
     __syncthreads();
     if (w.a > 0.0 && t + 1 < p.nr) {
-      const double pt = pv[t];
+      const double rp = 1.0 / pv[t];     // multipliers l_i = W[t, i] / pivot
       for (int li = tid; li < own; li += kThreads)
-        lm[li] = p.mask[lo + li] ? 0.0 : Wsh[t * per + li] / pt;
+        lm[li] = p.mask[lo + li] ? 0.0 : Wsh[t * per + li] * rp;
       __syncthreads();
-      const int rows = p.nr - t - 1;
-      for (int e = tid; e < rows * own; e += kThreads) {
-        int rr = t + 1 + e / own, li = e % own;
-        double l = lm[li];
-        if (l != 0.0) Wsh[rr * per + li] = fma(-l, pv[rr], Wsh[rr * per + li]);
+      for (int rr = t + 1 + wid; rr < p.nr; rr += kThreads / 32) {   // warp per row
+        const double pr = pv[rr];
+        double* wr = Wsh + rr * per;
+        for (int li = lane; li < own; li += 32) wr[li] = fma(-lm[li], pr, wr[li]);
       }
     }
     __syncthreads();

@@ -173,6 +173,169 @@ __global__ void __launch_bounds__(kThreads) qrcp_factor_kernel(QrcpParams P) {
   }
 }
 
+// Cooperative variant with each CTA's columns resident in shared memory
+// (Rloc[li * p + i] for column col = cta + li * G).  Every CTA publishes its
+// best candidate's norm, index and current column to a double-buffered slot,
+// so one bounded grid barrier per step suffices; the reflector is rebuilt by
+// every CTA from the winner's slot.  At exit the columns go back to Rc for the
+// solve kernel.
+__global__ void __launch_bounds__(kThreads) qrcp_factor_smem_kernel(QrcpParams P, int nloc) {
+  extern __shared__ double shm[];
+  const int G = gridDim.x, cta = blockIdx.x, tid = threadIdx.x;
+  const int lane = tid & 31, wid = tid >> 5;
+  const int p = (int)P.p, q = (int)P.q, kmax = p < q ? p : q;
+  double* Rloc = shm;                          // nloc * p
+  double* v = Rloc + (size_t)nloc * p;         // p (reflector)
+  int* usedl = reinterpret_cast<int*>(v + p);  // nloc
+  __shared__ double s_red_a[kWarps];
+  __shared__ long long s_red_i[kWarps];
+  __shared__ long long s_jp;
+  __shared__ int s_wcta;
+  __shared__ double s_tau, s_alpha, s_nrm2;
+  const int stride = p + 2;
+
+  for (int li = wid; li < nloc; li += kWarps) {
+    const int col = cta + li * G;
+    for (int i = lane; i < p; i += 32) Rloc[li * p + i] = col < q ? P.M[(int64_t)i * P.ldm + col] : 0.0;
+    if (lane == 0) usedl[li] = col < q ? 0 : 1;
+  }
+  __syncthreads();
+
+  for (int j = 0; j < kmax; ++j) {
+    double* slot = P.w.slots + (size_t)((j & 1) * G) * stride;
+    double ba = -1.0;
+    long long bi = LLONG_MAX;
+    for (int li = wid; li < nloc; li += kWarps) {
+      if (usedl[li]) continue;
+      const double* r = Rloc + li * p;
+      double s0 = 0.0, s1 = 0.0;
+      int i = j + lane;
+      for (; i + 32 < p; i += 64) { s0 = fma(r[i], r[i], s0); s1 = fma(r[i + 32], r[i + 32], s1); }
+      if (i < p) s0 = fma(r[i], r[i], s0);
+      double sn = warp_sum(s0 + s1);
+      const long long col = cta + (long long)li * G;
+      if (sn > ba || (sn == ba && col < bi)) { ba = sn; bi = col; }
+    }
+    if (lane == 0) { s_red_a[wid] = ba; s_red_i[wid] = bi; }
+    __syncthreads();
+    if (tid == 0) {
+      double a = -1.0; long long ii = LLONG_MAX;
+      for (int w = 0; w < kWarps; ++w)
+        if (s_red_a[w] > a || (s_red_a[w] == a && s_red_i[w] < ii)) { a = s_red_a[w]; ii = s_red_i[w]; }
+      s_red_a[0] = a; s_red_i[0] = ii;
+    }
+    __syncthreads();
+    {
+      double* my = slot + (size_t)cta * stride;
+      const long long bii = s_red_i[0];
+      if (tid == 0) { my[0] = s_red_a[0]; my[1] = __longlong_as_double(bii); }
+      if (bii != LLONG_MAX) {
+        const double* r = Rloc + (int)((bii - cta) / G) * p;
+        for (int i = j + tid; i < p; i += kThreads) my[2 + i] = r[i];
+      }
+    }
+    __threadfence();
+    if (!grid_barrier(P.w.bar, P.st)) return;
+    if (wid == 0) {
+      double a = -1.0; long long ii = LLONG_MAX; int wc = -1;
+      for (int g = lane; g < G; g += 32) {
+        const double* sg = slot + (size_t)g * stride;
+        double ga = __ldcg(sg);
+        long long gi = __double_as_longlong(__ldcg(sg + 1));
+        if (ga > a || (ga == a && gi < ii)) { a = ga; ii = gi; wc = g; }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        double oa = __shfl_down_sync(0xffffffffu, a, o);
+        long long oi = __shfl_down_sync(0xffffffffu, ii, o);
+        int oc = __shfl_down_sync(0xffffffffu, wc, o);
+        if (oa > a || (oa == a && oi < ii)) { a = oa; ii = oi; wc = oc; }
+      }
+      if (lane == 0) { s_nrm2 = a; s_jp = ii; s_wcta = wc; }
+    }
+    __syncthreads();
+    const long long jp = s_jp;
+    if (jp == LLONG_MAX) { if (tid == 0) dev_set_err(P.st, kDevNoCandidate); return; }
+    const double* wsrc = slot + (size_t)s_wcta * stride + 2;
+    for (int i = j + tid; i < p; i += kThreads) v[i] = __ldcg(wsrc + i);
+    __syncthreads();
+    if (tid == 0) {
+      double normx = sqrt(s_nrm2), x0 = v[j];
+      if (normx == 0.0) {
+        s_alpha = 0.0;
+      } else {
+        s_alpha = x0 >= 0.0 ? -normx : normx;
+        v[j] = x0 - s_alpha;
+      }
+    }
+    __syncthreads();
+    if (s_alpha != 0.0) {
+      double sacc = 0.0;
+      for (int i = j + tid; i < p; i += kThreads) sacc = fma(v[i], v[i], sacc);
+      sacc = warp_sum(sacc);
+      if (lane == 0) s_red_a[wid] = sacc;
+      __syncthreads();
+      if (tid == 0) {
+        double t = 0.0;
+        for (int w = 0; w < kWarps; ++w) t += s_red_a[w];
+        s_tau = 2.0 / t;
+      }
+    } else if (tid == 0) {
+      s_tau = 0.0;
+    }
+    __syncthreads();
+    const double tau = s_tau;
+    if (cta == 0) {
+      if (tid == 0) { P.w.perm[j] = jp; P.w.rdiag[j] = s_alpha; P.w.tau[j] = tau; }
+      for (int i = j + tid; i < p; i += kThreads) P.w.V[(int64_t)j * p + i] = v[i];
+    }
+    if (tid == 0 && (jp % G) == cta) usedl[(int)((jp - cta) / G)] = 1;
+    __syncthreads();
+    if (tau != 0.0) {
+      for (int li = wid; li < nloc; li += kWarps) {
+        if (usedl[li]) continue;
+        double* r = Rloc + li * p;
+        double d0 = 0.0, d1 = 0.0;
+        int i = j + lane;
+        for (; i + 32 < p; i += 64) { d0 = fma(v[i], r[i], d0); d1 = fma(v[i + 32], r[i + 32], d1); }
+        if (i < p) d0 = fma(v[i], r[i], d0);
+        const double d = warp_sum(d0 + d1) * tau;
+        for (int i2 = j + lane; i2 < p; i2 += 32) r[i2] = fma(-d, v[i2], r[i2]);
+      }
+    }
+    __syncthreads();
+  }
+  // write the columns back for the solve (frozen pivot columns hold R above the diagonal)
+  for (int li = wid; li < nloc; li += kWarps) {
+    const int col = cta + li * G;
+    if (col >= q) continue;
+    for (int i = lane; i < p; i += 32) P.w.Rc[(int64_t)col * p + i] = Rloc[li * p + i];
+  }
+  if (cta == 0 && tid == 0) {
+    double thr;
+    double r0 = kmax > 0 ? fabs(P.w.rdiag[0]) : 0.0;
+    if (P.thr_mode == 0) {
+      thr = (double)(p > q ? p : q) * 0x1.0p-52 * r0;
+    } else if (P.thr_mode == 1) {
+      thr = P.thr;
+    } else {
+      double sc = *P.scale_dev;
+      if (sc < 0.0) { sc = 0x1.0p-52 * r0; *P.scale_dev = sc; }
+      thr = P.thr * sc;
+    }
+    int64_t k = 0;
+    while (k < kmax && fabs(P.w.rdiag[k]) > thr) ++k;
+    *P.w.rank = k;
+    if (q > kmax) {
+      int64_t pos = kmax;
+      for (int64_t col = 0; col < q; ++col) {
+        bool u = false;
+        for (int64_t jj = 0; jj < kmax; ++jj) u |= (P.w.perm[jj] == col);
+        if (!u) P.w.perm[pos++] = col;
+      }
+    }
+  }
+}
+
 struct SolveParams {
   int64_t p, q;
   const double* Rc; const double* V; const double* tau; const double* rdiag;
@@ -216,22 +379,31 @@ __global__ void __launch_bounds__(kThreads) qrcp_solve_kernel(SolveParams S) {
 }
 
 // Single-CTA variant for small p, q (every N_k and small cores).  GB300 runs
-// FP64 at ~2 DFMA/clk/SM, so warp-wide FP64 reductions and redundant lane
-// arithmetic dominate small problems; this variant gives every thread one
-// column: R is row-major in shared memory (R[i*q + col]: consecutive lanes,
-// consecutive columns), the pivot column is read as a broadcast, and no
-// reduction is needed except the argmax.  Pivot columns are frozen in place,
-// so reflector j is (vhead[j], R[j+1.., perm[j]]) and R(i, i') = R[i, perm[i']]
-// for i < i'.  The same launch forms X = P [R_11^{-1} Q_1^T; 0] with one thread
-// per column of the identity (vectors in shared memory).
-constexpr int kSmallThreads = 256;
+// FP64 at ~2 DFMA/clk/SM, so a 50 x 50 problem has too little work for one
+// thread per column to hide FP64 and shared-memory latency.  Here every column
+// gets a group of 8 threads that split its rows (segments i = i0 + s, s + 8,
+// ...) and combine with a 3-step shuffle; R is row-major in shared memory
+// (R[i*q + col]) and the pivot column is read as a broadcast.  Pivot columns
+// are frozen in place, so reflector j is (vhead[j], R[j+1.., perm[j]]) and
+// R(i, i') = R[i, perm[i']] for i < i'.  The same launch forms
+// X = P [R_11^{-1} Q_1^T; 0] with one thread group per column of the identity.
+constexpr int kSmallThreads = 512;
+constexpr int kSeg = 8;                            // threads per column
+constexpr int kGroups = kSmallThreads / kSeg;      // columns in flight
+
+__device__ __forceinline__ double seg_sum(double v) {
+  v += __shfl_xor_sync(0xffffffffu, v, 4);
+  v += __shfl_xor_sync(0xffffffffu, v, 2);
+  v += __shfl_xor_sync(0xffffffffu, v, 1);
+  return v;
+}
 
 __global__ void __launch_bounds__(kSmallThreads) qrcp_small_kernel(QrcpParams P, double* X,
                                                                    int64_t ldx) {
   extern __shared__ double sm[];
   const int p = (int)P.p, q = (int)P.q, kmax = p < q ? p : q;
   double* R = sm;                                   // p * q, row-major
-  double* Y = R + (size_t)p * q;                    // p * p, row-major (column l = thread l)
+  double* Y = R + (size_t)p * q;                    // p * p, row-major (column l of the identity)
   double* nrm = Y + (size_t)p * p;                  // q
   double* rdiag = nrm + q;                          // kmax
   double* rinv = rdiag + kmax;                      // kmax
@@ -239,11 +411,10 @@ __global__ void __launch_bounds__(kSmallThreads) qrcp_small_kernel(QrcpParams P,
   double* vhead = tau + kmax;                       // kmax
   int* perm = reinterpret_cast<int*>(vhead + kmax); // q
   int* used = perm + q;                             // q
-  __shared__ double s_red_a[kSmallThreads / 32];
-  __shared__ int s_red_i[kSmallThreads / 32];
   __shared__ int s_jp, s_k;
   __shared__ double s_tau;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int grp = tid / kSeg, sg = tid % kSeg;
 
   for (int e = tid; e < p * q; e += kSmallThreads) {
     int i = e / q, col = e - i * q;
@@ -253,51 +424,59 @@ __global__ void __launch_bounds__(kSmallThreads) qrcp_small_kernel(QrcpParams P,
   __syncthreads();
 
   for (int j = 0; j < kmax; ++j) {
-    // squared norms over rows j..p-1 of the unused columns, one thread each
-    double ba = -1.0;
-    int bi = INT_MAX;
-    for (int col = tid; col < q; col += kSmallThreads) {
-      if (used[col]) continue;
+    // squared norms over rows j..p-1 of the unused columns
+    for (int col0 = 0; col0 < q; col0 += kGroups) {   // uniform trip count for the shuffles
+      const int col = col0 + grp;
       double sacc = 0.0;
-      for (int i = j; i < p; ++i) { double x = R[i * q + col]; sacc = fma(x, x, sacc); }
-      if (sacc > ba) { ba = sacc; bi = col; }   // increasing col per thread: ties keep the smaller
+      if (col < q && !used[col])
+        for (int i = j + sg; i < p; i += kSeg) { double x = R[i * q + col]; sacc = fma(x, x, sacc); }
+      sacc = seg_sum(sacc);
+      if (col < q && sg == 0) nrm[col] = used[col] ? -1.0 : sacc;
     }
-    for (int o = 16; o > 0; o >>= 1) {
-      double oa = __shfl_down_sync(0xffffffffu, ba, o);
-      int oi = __shfl_down_sync(0xffffffffu, bi, o);
-      if (oa > ba || (oa == ba && oi < bi)) { ba = oa; bi = oi; }
-    }
-    if (lane == 0) { s_red_a[wid] = ba; s_red_i[wid] = bi; }
     __syncthreads();
-    if (tid == 0) {
-      double a = -1.0; int ii = INT_MAX;
-      for (int w = 0; w < kSmallThreads / 32; ++w)
-        if (s_red_a[w] > a || (s_red_a[w] == a && s_red_i[w] < ii)) { a = s_red_a[w]; ii = s_red_i[w]; }
-      double x0 = R[j * q + ii];
-      double normx = sqrt(a);
-      double alpha = normx == 0.0 ? 0.0 : (x0 >= 0.0 ? -normx : normx);
-      double vh = x0 - alpha;
-      double t = 0.0;
-      if (alpha != 0.0) {            // tau = 2 / ||v||^2, v = (x0 - alpha, x_{j+1..p-1})
-        double vv = vh * vh;
-        for (int i = j + 1; i < p; ++i) { double x = R[i * q + ii]; vv = fma(x, x, vv); }
-        t = 2.0 / vv;
+    if (wid == 0) {   // argmax over columns: largest norm, smallest index
+      double ba = -1.0;
+      int bi = INT_MAX;
+      for (int col = lane; col < q; col += 32)
+        if (nrm[col] > ba) { ba = nrm[col]; bi = col; }
+      for (int o = 16; o > 0; o >>= 1) {
+        double oa = __shfl_down_sync(0xffffffffu, ba, o);
+        int oi = __shfl_down_sync(0xffffffffu, bi, o);
+        if (oa > ba || (oa == ba && oi < bi)) { ba = oa; bi = oi; }
       }
-      s_jp = ii; s_tau = t;
-      perm[j] = ii; used[ii] = 1; rdiag[j] = alpha; vhead[j] = vh; tau[j] = t;
+      const int ii = __shfl_sync(0xffffffffu, bi, 0);
+      const double a = __shfl_sync(0xffffffffu, ba, 0);
+      double vv = 0.0;          // ||x_{j+1..p-1}||^2 of the pivot column
+      for (int i = j + 1 + lane; i < p; i += 32) { double x = R[i * q + ii]; vv = fma(x, x, vv); }
+      vv = warp_sum(vv);
+      if (lane == 0) {
+        const double x0 = R[j * q + ii];
+        const double normx = sqrt(a);
+        const double alpha = normx == 0.0 ? 0.0 : (x0 >= 0.0 ? -normx : normx);
+        const double vh = x0 - alpha;
+        const double t = alpha != 0.0 ? 2.0 / fma(vh, vh, vv) : 0.0;
+        s_jp = ii; s_tau = t;
+        perm[j] = ii; used[ii] = 1; rdiag[j] = alpha; vhead[j] = vh; tau[j] = t;
+      }
     }
     __syncthreads();
     const int jp = s_jp;
     const double tj = s_tau;
     if (tj != 0.0) {
       const double vh = vhead[j];
-      for (int col = tid; col < q; col += kSmallThreads) {
-        if (used[col]) continue;
-        double d = vh * R[j * q + col];
-        for (int i = j + 1; i < p; ++i) d = fma(R[i * q + jp], R[i * q + col], d);
-        d *= tj;
-        R[j * q + col] = fma(-d, vh, R[j * q + col]);
-        for (int i = j + 1; i < p; ++i) R[i * q + col] = fma(-d, R[i * q + jp], R[i * q + col]);
+      for (int col0 = 0; col0 < q; col0 += kGroups) {
+        const int col = col0 + grp;
+        const bool act = col < q && !used[col];
+        double d = 0.0;
+        if (act) {
+          if (sg == 0) d = vh * R[j * q + col];
+          for (int i = j + 1 + sg; i < p; i += kSeg) d = fma(R[i * q + jp], R[i * q + col], d);
+        }
+        d = seg_sum(d) * tj;
+        if (act) {
+          if (sg == 0) R[j * q + col] = fma(-d, vh, R[j * q + col]);
+          for (int i = j + 1 + sg; i < p; i += kSeg) R[i * q + col] = fma(-d, R[i * q + jp], R[i * q + col]);
+        }
       }
     }
     __syncthreads();
@@ -327,27 +506,41 @@ __global__ void __launch_bounds__(kSmallThreads) qrcp_small_kernel(QrcpParams P,
   __syncthreads();
   const int k = s_k;
   for (int i = tid; i < k; i += kSmallThreads) rinv[i] = 1.0 / rdiag[i];
+  for (int e = tid; e < p * p; e += kSmallThreads) Y[e] = (e / p == e % p) ? 1.0 : 0.0;
   __syncthreads();
-  for (int l = tid; l < p; l += kSmallThreads) {
-    for (int i = 0; i < p; ++i) Y[i * p + l] = (i == l) ? 1.0 : 0.0;
+  for (int l0 = 0; l0 < p; l0 += kGroups) {
+    const int l = l0 + grp;
+    const bool act = l < p;
     for (int jj = 0; jj < k; ++jj) {   // y = H_{k-1} ... H_0 e_l
+      __syncwarp();                     // rows written by the neighbouring lanes last step
       const double tjj = tau[jj];
       if (tjj == 0.0) continue;
       const int pc = perm[jj];
       const double vh = vhead[jj];
-      double d = vh * Y[jj * p + l];
-      for (int i = jj + 1; i < p; ++i) d = fma(R[i * q + pc], Y[i * p + l], d);
-      d *= tjj;
-      Y[jj * p + l] = fma(-d, vh, Y[jj * p + l]);
-      for (int i = jj + 1; i < p; ++i) Y[i * p + l] = fma(-d, R[i * q + pc], Y[i * p + l]);
+      double d = 0.0;
+      if (act) {
+        if (sg == 0) d = vh * Y[jj * p + l];
+        for (int i = jj + 1 + sg; i < p; i += kSeg) d = fma(R[i * q + pc], Y[i * p + l], d);
+      }
+      d = seg_sum(d) * tjj;
+      if (act) {
+        if (sg == 0) Y[jj * p + l] = fma(-d, vh, Y[jj * p + l]);
+        for (int i = jj + 1 + sg; i < p; i += kSeg) Y[i * p + l] = fma(-d, R[i * q + pc], Y[i * p + l]);
+      }
     }
     for (int i = k - 1; i >= 0; --i) {  // back substitution with R_11, column oriented
-      const double zi = Y[i * p + l] * rinv[i];
-      Y[i * p + l] = zi;
-      const int pc = perm[i];
-      for (int a = 0; a < i; ++a) Y[a * p + l] = fma(-zi, R[a * q + pc], Y[a * p + l]);
+      __syncwarp();
+      const double zi = act ? Y[i * p + l] * rinv[i] : 0.0;
+      __syncwarp();
+      if (act) {
+        if (sg == 0) Y[i * p + l] = zi;
+        const int pc = perm[i];
+        for (int a2 = sg; a2 < i; a2 += kSeg) Y[a2 * p + l] = fma(-zi, R[a2 * q + pc], Y[a2 * p + l]);
+      }
     }
-    for (int i = 0; i < q; ++i) X[(int64_t)perm[i] * ldx + l] = (i < k) ? Y[i * p + l] : 0.0;
+    __syncwarp();
+    if (act)
+      for (int i = sg; i < q; i += kSeg) X[(int64_t)perm[i] * ldx + l] = (i < k) ? Y[i * p + l] : 0.0;
   }
 }
 
@@ -363,7 +556,7 @@ size_t qrcp_work_bytes(int64_t p, int64_t q, int max_grid) {
   add(sizeof(double) * (size_t)kmax);           // rdiag
   add(sizeof(int64_t) * (size_t)q);             // perm
   add((size_t)q);                               // used
-  add(sizeof(double) * 4 * (size_t)max_grid);   // slots
+  add(sizeof(double) * 2 * (size_t)max_grid * (size_t)(p + 2));   // slots
   add(sizeof(GridBar));
   add(sizeof(int64_t));                         // rank
   add(sizeof(double) * (size_t)(p * p));        // solve work
@@ -380,19 +573,25 @@ void qrcp_carve(void* base, int64_t p, int64_t q, int max_grid, QrcpWork* w) {
   w->rdiag = (double*)take(sizeof(double) * (size_t)kmax);
   w->perm = (int64_t*)take(sizeof(int64_t) * (size_t)q);
   w->used = (uint8_t*)take((size_t)q);
-  w->slots = (double*)take(sizeof(double) * 4 * (size_t)max_grid);
+  w->slots = (double*)take(sizeof(double) * 2 * (size_t)max_grid * (size_t)(p + 2));
   w->bar = (GridBar*)take(sizeof(GridBar));
   w->rank = (int64_t*)take(sizeof(int64_t));
   w->Ysolve = (double*)take(sizeof(double) * (size_t)(p * p));
   w->max_grid = max_grid;
 }
 
+// Shared memory of the resident-column cooperative variant for a grid of g.
+static size_t qrcp_coop_smem(int64_t p, int64_t q, int g) {
+  int64_t nloc = (q + g - 1) / g;
+  return sizeof(double) * (size_t)(nloc * p + p) + sizeof(int) * (size_t)nloc;
+}
+
 int qrcp_grid(const LaunchEnv& env, int64_t p, int64_t q) {
-  (void)p;
   if (q <= 128) return 1;
-  int64_t g = q / 16;
+  int64_t g = (q + 7) / 8;   // about 8 columns (one per warp) per CTA
   if (g > env.num_sms) g = env.num_sms;
-  return g < 1 ? 1 : (int)g;
+  if (g < 1) g = 1;
+  return (int)g;
 }
 
 cudaError_t launch_qrcp_pinv(const LaunchEnv& env, const double* M, int64_t p, int64_t q,
@@ -414,15 +613,28 @@ cudaError_t launch_qrcp_pinv(const LaunchEnv& env, const double* M, int64_t p, i
     qrcp_small_kernel<<<1, kSmallThreads, ssm, env.stream>>>(P, X, ldx);
     return cudaGetLastError();
   }
-  size_t smem = sizeof(double) * (size_t)p;
-  if (smem > 48 * 1024) {
-    e = cudaFuncSetAttribute((const void*)qrcp_factor_kernel,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+  const size_t csm = qrcp_coop_smem(p, q, grid);
+  if (csm <= 200 * 1024) {
+    if (csm > 48 * 1024) {
+      e = cudaFuncSetAttribute((const void*)qrcp_factor_smem_kernel,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm);
+      if (e != cudaSuccess) return e;
+    }
+    int nloc = (int)((q + grid - 1) / grid);
+    void* args[] = {&P, &nloc};
+    e = cudaLaunchCooperativeKernel((const void*)qrcp_factor_smem_kernel, dim3(grid),
+                                    dim3(kThreads), args, csm, env.stream);
+  } else {
+    size_t smem = sizeof(double) * (size_t)p;
+    if (smem > 48 * 1024) {
+      e = cudaFuncSetAttribute((const void*)qrcp_factor_kernel,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    void* args[] = {&P};
+    e = cudaLaunchCooperativeKernel((const void*)qrcp_factor_kernel, dim3(grid), dim3(kThreads),
+                                    args, smem, env.stream);
   }
-  void* args[] = {&P};
-  e = cudaLaunchCooperativeKernel((const void*)qrcp_factor_kernel, dim3(grid), dim3(kThreads),
-                                  args, smem, env.stream);
   if (e != cudaSuccess) return e;
   SolveParams S;
   S.p = p; S.q = q; S.Rc = w.Rc; S.V = w.V; S.tau = w.tau; S.rdiag = w.rdiag; S.perm = w.perm;

@@ -39,7 +39,6 @@ namespace {
 constexpr int kTileK = 64;        // rows of A per stage = MMA K per stage
 constexpr int kTileN = 128;       // columns of A per CTA tile = MMA M
 constexpr int kChunkTiles = 4;    // stages per exact accumulation chunk (256 rows)
-constexpr int kStages = 2;
 constexpr int kConvWarps = 8;
 constexpr int kThreads = (2 + kConvWarps) * 32;
 constexpr long long kWaitBudget = 4000000000LL;  // ~2 s at 2 GHz
@@ -147,23 +146,30 @@ struct TcArgs {
   int64_t m, n;
   int c, c_pad;
   const int* colexp;       // E_j per column (pre-pass)
-  long long* partial;      // [ks][c][n] int64 slice-combined sums
+  unsigned long long* acc; // c x n int64 sums (two's complement), zeroed by the host
   int64_t kunit;           // rows of A per work unit (multiple of 256)
   int ks;                  // work units along K
   int64_t nstrips;         // column strips of 128
   int* err;                // device error word
 };
 
-// Dynamic shared memory per stage: S digit tiles (128 x 64 BF16 = 16 KB each),
-// the G_q tile (c_pad x 64 BF16), the A tile (64 x 128 FP32 = 32 KB).
+// Dynamic shared memory: an A ring of NA FP32 tiles (64 x 128 = 32 KB each),
+// freed by the converters, and an operand ring of 2 stages, each holding S
+// digit tiles (128 x 64 BF16 = 16 KB) and the G_q tile (c_pad x 64 BF16),
+// freed by the MMA commit.  NA is as deep as ~210 KB allows (2..4).
 template <int S, int CP>
 struct Layout {
   static constexpr int kOpBytes = kTileN * kTileK * 2;          // 16384
   static constexpr int kGBytes = CP * kTileK * 2;               // CP * 128
   static constexpr int kABytes = kTileK * kTileN * 4;           // 32768
-  static constexpr int kStageBytes = S * kOpBytes + kGBytes + kABytes;
-  static constexpr int kBarOffset = kStages * kStageBytes;
-  static constexpr int kTotal = kBarOffset + 256 + 1024;        // + alignment slack
+  static constexpr int kOpStage = S * kOpBytes + kGBytes;
+  static constexpr int kNO = 2;
+  static constexpr int kBudget = 212 * 1024;
+  static constexpr int kNAraw = (kBudget - kNO * kOpStage) / kABytes;
+  static constexpr int kNA = kNAraw > 4 ? 4 : (kNAraw < 2 ? 2 : kNAraw);
+  static constexpr int kOpOffset = kNA * kABytes;
+  static constexpr int kBarOffset = kOpOffset + kNO * kOpStage;
+  static constexpr int kTotal = kBarOffset + 512 + 1024;        // barriers + alignment slack
   static constexpr uint32_t kTmemCols = (2 * S * CP <= 32) ? 32
                                         : (2 * S * CP <= 64) ? 64
                                         : (2 * S * CP <= 128) ? 128
@@ -175,26 +181,34 @@ __global__ void __launch_bounds__(kThreads, 1)
     sketch_tc_kernel(const __grid_constant__ CUtensorMap mapA,
                      const __grid_constant__ CUtensorMap mapG, TcArgs g) {
   using L = Layout<S, CP>;
+  constexpr int NA = L::kNA, NO = L::kNO;
   static_assert(2 * S * CP <= 512, "accumulators exceed tensor memory");
   static_assert(CP % 16 == 0 && CP >= 16 && CP <= 128, "N must be a multiple of 16, <= 128");
+  static_assert(L::kTotal <= 227 * 1024, "shared memory");
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~uintptr_t(1023));
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L::kBarOffset);
-  uint64_t* full = bars;                  // [kStages] TMA landed
-  uint64_t* conv = bars + kStages;        // [kStages] digit tiles written
-  uint64_t* empty = bars + 2 * kStages;   // [kStages] MMAs done with the stage
-  uint64_t* accf = bars + 3 * kStages;    // [2] chunk accumulators complete
-  uint64_t* acce = bars + 3 * kStages + 2;// [2] chunk accumulators drained
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 * kStages + 4);
+  uint64_t* fullA = bars;                 // [NA] A tile landed (TMA)
+  uint64_t* emptyA = fullA + NA;          // [NA] A tile converted
+  uint64_t* fullG = emptyA + NA;          // [NO] G_q tile landed (TMA)
+  uint64_t* conv = fullG + NO;            // [NO] digit tiles written
+  uint64_t* emptyO = conv + NO;           // [NO] MMAs done with the operand stage
+  uint64_t* accf = emptyO + NO;           // [2] chunk accumulators complete
+  uint64_t* acce = accf + 2;              // [2] chunk accumulators drained
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acce + 2);
   int* s_abort = reinterpret_cast<int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kStages; ++s) {
-      mbar_init(&full[s], 1);
+    for (int s = 0; s < NA; ++s) {
+      mbar_init(&fullA[s], 1);
+      mbar_init(&emptyA[s], kConvWarps * 32);
+    }
+    for (int s = 0; s < NO; ++s) {
+      mbar_init(&fullG[s], 1);
       mbar_init(&conv[s], kConvWarps * 32);
-      mbar_init(&empty[s], 1);
+      mbar_init(&emptyO[s], 1);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&accf[b], 1);
@@ -214,7 +228,6 @@ __global__ void __launch_bounds__(kThreads, 1)
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
-  // flat schedule: this CTA's work units (strip, z), each split into 64-row tiles
   const int64_t nunits = g.nstrips * g.ks;
   auto unit_tiles = [&](int64_t u) -> int {
     int64_t z = u / g.nstrips;
@@ -223,26 +236,23 @@ __global__ void __launch_bounds__(kThreads, 1)
   };
 
   if (warp == 0) {
-    // ---------------- TMA producer ----------------
+    // ---------------- TMA producer of the FP32 A tiles ----------------
     if (lane == 0) {
       uint32_t t = 0;
       for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
         const int64_t strip = u % g.nstrips, z = u / g.nstrips;
         const int nt = unit_tiles(u);
         for (int i = 0; i < nt; ++i, ++t) {
-          const uint32_t s = t % kStages;
-          if (t >= kStages && !mbar_wait(&empty[s], ((t / kStages) - 1) & 1)) {
+          const uint32_t s = t % NA;
+          if (t >= (uint32_t)NA && !mbar_wait(&emptyA[s], ((t / NA) - 1) & 1)) {
             atomicCAS(g.err, 0, kDevTimeout);
-            *s_abort = 1;
+            *((volatile int*)s_abort) = 1;
             break;
           }
           if (*((volatile int*)s_abort)) break;
-          uint8_t* st = smem + s * L::kStageBytes;
-          mbar_expect_tx(&full[s], (uint32_t)(L::kGBytes + L::kABytes));
-          const int krow = (int)(z * g.kunit) + i * kTileK;
-          tma_load_2d(st + S * L::kOpBytes + L::kGBytes, &mapA, &full[s],
-                      (int)(strip * kTileN), krow);
-          tma_load_2d(st + S * L::kOpBytes, &mapG, &full[s], krow, 0);
+          mbar_expect_tx(&fullA[s], (uint32_t)L::kABytes);
+          tma_load_2d(smem + s * L::kABytes, &mapA, &fullA[s], (int)(strip * kTileN),
+                      (int)(z * g.kunit) + i * kTileK);
         }
         if (*((volatile int*)s_abort)) break;
       }
@@ -257,14 +267,15 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int64_t u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
         const int nt = unit_tiles(u);
         for (int i = 0; i < nt && ok; ++i, ++t) {
-          const uint32_t s = t % kStages;
+          const uint32_t so = t % NO;
           const bool first = (i % kChunkTiles) == 0;
           const bool last = (i % kChunkTiles) == kChunkTiles - 1 || i == nt - 1;
           const uint32_t buf = chunk & 1;
           if (first && chunk >= 2 && !mbar_wait(&acce[buf], ((chunk >> 1) - 1) & 1)) { ok = false; break; }
-          if (!mbar_wait(&conv[s], (t / kStages) & 1)) { ok = false; break; }
+          if (!mbar_wait(&conv[so], (t / NO) & 1)) { ok = false; break; }
+          if (!mbar_wait(&fullG[so], (t / NO) & 1)) { ok = false; break; }
           tc_fence_after();
-          uint8_t* st = smem + s * L::kStageBytes;
+          uint8_t* st = smem + L::kOpOffset + so * L::kOpStage;
           const uint32_t gaddr = smem_u32(st + S * L::kOpBytes);
 #pragma unroll
           for (int sl = 0; sl < S; ++sl) {
@@ -275,7 +286,7 @@ __global__ void __launch_bounds__(kThreads, 1)
               mma_bf16(dcol, desc_sw128(aaddr + kk * 32), desc_sw128(gaddr + kk * 32), idesc,
                        (first && kk == 0) ? 0u : 1u);
           }
-          mma_commit(&empty[s]);
+          mma_commit(&emptyO[so]);
           if (last) {
             mma_commit(&accf[buf]);
             ++chunk;
@@ -285,10 +296,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (!ok) { atomicCAS(g.err, 0, kDevTimeout); *((volatile int*)s_abort) = 1; }
     }
   } else {
-    // ---------------- converters + drain ----------------
+    // ---------------- converters (+ G_q tile loads) + drain ----------------
     const int ct = threadIdx.x - 64;           // 0..255
     const int jl = ct & (kTileN - 1);          // this thread's column in the tile
-    const int half = ct >> 7;                  // k-group parity / accumulator half
+    const int half = ct >> 7;                  // k-group parity
     const int q = warp & 3;                    // TMEM lane quarter of this warp
     const int dh = (warp - 2) >> 2;            // 0: warps 2-5, 1: warps 6-9
     constexpr int HALF = CP / 2;               // sketch rows per drain thread
@@ -304,11 +315,16 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int E = jg < g.n ? g.colexp[jg] : 0;
       const float sc = ldexpf(1.0f, min(8 - E, 126));  // columns below 2^-118: digits lose range
       for (int i = 0; i < nt && ok; ++i, ++t) {
-        const uint32_t s = t % kStages;
-        if (!mbar_wait(&full[s], (t / kStages) & 1)) { ok = false; break; }
-        uint8_t* st = smem + s * L::kStageBytes;
-        const float* At = reinterpret_cast<const float*>(st + S * L::kOpBytes + L::kGBytes);
-        // 8 groups of 8 rows; this thread handles groups half, half+2, half+4, half+6
+        const uint32_t sa = t % NA, so = t % NO;
+        // the operand stage must be free of the MMAs that read it last time
+        if (t >= (uint32_t)NO && !mbar_wait(&emptyO[so], ((t / NO) - 1) & 1)) { ok = false; break; }
+        uint8_t* st = smem + L::kOpOffset + so * L::kOpStage;
+        if (ct == 0) {
+          mbar_expect_tx(&fullG[so], (uint32_t)L::kGBytes);
+          tma_load_2d(st + S * L::kOpBytes, &mapG, &fullG[so], (int)(z * g.kunit) + i * kTileK, 0);
+        }
+        if (!mbar_wait(&fullA[sa], (t / NA) & 1)) { ok = false; break; }
+        const float* At = reinterpret_cast<const float*>(smem + sa * L::kABytes);
 #pragma unroll
         for (int it = 0; it < 4; ++it) {
           const int kg = half + 2 * it;
@@ -333,8 +349,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             *reinterpret_cast<uint4*>(st + sl * L::kOpBytes + off) = v;
           }
         }
+        mbar_arrive(&emptyA[sa]);   // the FP32 tile may be refilled
         fence_async_smem();
-        mbar_arrive(&conv[s]);
+        mbar_arrive(&conv[so]);
         const bool last = (i % kChunkTiles) == kChunkTiles - 1 || i == nt - 1;
         if (last) {
           // drain: accumulators of this chunk -> int64
@@ -364,13 +381,14 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
       }
       if (!ok) break;
-      // unit done: write this thread's (rows, column) sums and reset
+      // unit done: add this thread's (rows, column) sums into the global int64 sums
       const int jt = q * 32 + lane;   // the column this thread drained (TMEM lane)
       const int64_t jw = strip * kTileN + jt;
 #pragma unroll
       for (int r = 0; r < HALF; ++r) {
         const int row = dh * HALF + r;
-        if (row < g.c && jw < g.n) g.partial[((int64_t)z * g.c + row) * g.n + jw] = acc[r];
+        if (row < g.c && jw < g.n && acc[r] != 0)
+          atomicAdd(&g.acc[(int64_t)row * g.n + jw], (unsigned long long)acc[r]);
         acc[r] = 0;
       }
     }
@@ -410,22 +428,19 @@ __global__ void colexp_kernel(const unsigned* __restrict__ colmax_bits, int64_t 
   colexp[j] = E;
 }
 
-// Y[i, j] = 2^(E_j - 8S) sum_z partial[z][i][j], plus per-CTA sums of squares.
-__global__ void tc_reduce_kernel(const long long* __restrict__ partial, int ks, int64_t c,
-                                 int64_t n, int S, const int* __restrict__ colexp,
-                                 double* __restrict__ Y, double* __restrict__ sumsq_part,
-                                 int64_t per_cta) {
+// Y[i, j] = 2^(E_j - 8S) acc[i][j] (exact: |acc| < 2^53), plus per-CTA sums of squares.
+__global__ void tc_reduce_kernel(const long long* __restrict__ acc, int64_t c, int64_t n, int S,
+                                 const int* __restrict__ colexp, double* __restrict__ Y,
+                                 double* __restrict__ sumsq_part, int64_t per_cta) {
   __shared__ double red[8];
   const int64_t total = c * n;
   const int64_t beg = (int64_t)blockIdx.x * per_cta, end = min(total, beg + per_cta);
   double ss = 0.0;
   for (int64_t e = beg + threadIdx.x; e < end; e += 256) {
-    long long s = 0;
-    for (int z = 0; z < ks; ++z) s += partial[(int64_t)z * total + e];
     const int64_t j = e % n;
     const int E = colexp[j];
     double y = (E >= (1 << 20)) ? __longlong_as_double(0x7FF8000000000000LL)
-                                : ldexp((double)s, E - 8 * S);
+                                : ldexp((double)acc[e], E - 8 * S);
     Y[e] = y;
     ss = fma(y, y, ss);
   }
@@ -464,8 +479,8 @@ EncodeTiledFn encode_fn() {
   if (!fn) {
     void* p = nullptr;
     cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) ==
-            cudaSuccess &&
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
       fn = reinterpret_cast<EncodeTiledFn>(p);
   }
@@ -502,7 +517,7 @@ size_t sketch_tc_scratch_bytes(int64_t c, int64_t m, int64_t n, int ks) {
   add(sizeof(uint16_t) * (size_t)(c * ldq));     // G_q
   add(sizeof(unsigned) * (size_t)n);             // column max bits
   add(sizeof(int) * (size_t)n);                  // column exponents
-  add(sizeof(long long) * (size_t)ks * c * n);   // partial sums
+  add(sizeof(long long) * (size_t)c * n);        // int64 sums
   return b;
 }
 
@@ -527,7 +542,7 @@ cudaError_t launch_sketch_tc(const LaunchEnv& env, int S, const double* G, int64
   uint16_t* Gq = (uint16_t*)take(sizeof(uint16_t) * (size_t)(c * ldq));
   unsigned* cmax = (unsigned*)take(sizeof(unsigned) * (size_t)n);
   int* cexp = (int*)take(sizeof(int) * (size_t)n);
-  long long* partial = (long long*)take(sizeof(long long) * (size_t)ks * c * n);
+  long long* acc64 = (long long*)take(sizeof(long long) * (size_t)c * n);
 
   // G_q (BF16, rows padded to a multiple of 64 so TMA strides are 16-byte multiples)
   {
@@ -536,6 +551,7 @@ cudaError_t launch_sketch_tc(const LaunchEnv& env, int S, const double* G, int64
   }
   // column scales
   cudaError_t e = cudaMemsetAsync(cmax, 0, sizeof(unsigned) * (size_t)n, env.stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(acc64, 0, sizeof(long long) * (size_t)(c * n), env.stream);
   if (e != cudaSuccess) return e;
   {
     int64_t rows_per = 512;
@@ -570,7 +586,8 @@ cudaError_t launch_sketch_tc(const LaunchEnv& env, int S, const double* G, int64
       return cudaErrorInvalidValue;
   }
   TcArgs a;
-  a.m = m; a.n = n; a.c = (int)c; a.c_pad = CP; a.colexp = cexp; a.partial = partial;
+  a.m = m; a.n = n; a.c = (int)c; a.c_pad = CP; a.colexp = cexp;
+  a.acc = reinterpret_cast<unsigned long long*>(acc64);
   const int64_t chunks = (m + kTileK * kChunkTiles - 1) / (kTileK * kChunkTiles);
   const int64_t chunks_per = (chunks + ks - 1) / ks;
   a.kunit = chunks_per * kTileK * kChunkTiles;
@@ -596,8 +613,8 @@ cudaError_t launch_sketch_tc(const LaunchEnv& env, int S, const double* G, int64
   const int64_t total = c * n;
   const int64_t per = 16384;
   const int64_t nblk = (total + per - 1) / per;
-  tc_reduce_kernel<<<(unsigned)nblk, 256, 0, env.stream>>>(partial, a.ks, c, n, S, cexp, Y,
-                                                           sumsq_part, per);
+  tc_reduce_kernel<<<(unsigned)nblk, 256, 0, env.stream>>>(acc64, c, n, S, cexp, Y, sumsq_part,
+                                                           per);
   *nparts = nblk;
   return cudaGetLastError();
 }

@@ -102,3 +102,16 @@ def decay_matrix_torch(m: int, n: int, spectrum: str, seed: int, noise: float = 
         A[r0:r1] = blk.to(dtype)
     del U, V
     return A
+
+
+def low_rank_gaussian_torch(m: int, n: int, r: int, seed: int, device="cuda"):
+    """The Low-Rank matrix of Sec. 5.1 built on the GPU in FP64: G1 G2^T with
+    standard Gaussian G1 (m x r), G2 (n x r), so its rank is exactly r."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    G1 = torch.randn(m, r, device=device, generator=g, dtype=torch.float64)
+    G2 = torch.randn(n, r, device=device, generator=g, dtype=torch.float64)
+    A = G1 @ G2.T
+    del G1, G2
+    return A
