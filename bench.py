@@ -62,6 +62,13 @@ def parse():
     p.add_argument("--paper-workload", action="store_true",
                    help="also time the Low-Rank matrix of Sec. 5.1 (30000^2 FP64, G1 G2^T of rank "
                         "2000, tol 1e-6, b = 250): the paper reports 12 s on a 48-core CPU")
+    p.add_argument("--workload", choices=["primary", "batch"], default="primary",
+                   help="batch: 4096 independent FP32 matrices (m, n log-uniform in [64, 2048], "
+                        "spectra exp(-i/20) / i^-1.5 / exact rank U[5,200]), tol 1e-4, b = c = 8, "
+                        "all in one persistent launch; one step = the whole batch")
+    p.add_argument("--batch-jobs", type=int, default=4096)
+    p.add_argument("--batch-teams", type=str, default="2,4,8",
+                   help="team sizes the batch autotuner tries (CTAs per job)")
     p.add_argument("--verbose", action="store_true", help="stage timestamps on stderr")
     p.add_argument("--watchdog", type=float, default=0.0,
                    help="dump all Python stacks to stderr and exit after this many seconds")
@@ -217,6 +224,203 @@ def run_reference(a, ws, rank):
     return 0
 
 
+# ---------------------------------------------------------------------------
+# Batched workload
+# ---------------------------------------------------------------------------
+BATCH_TOL, BATCH_B, BATCH_C = 1e-4, 8, 8
+
+
+def batch_rank_model(spec):
+    """Rank a job reaches (for work estimates when no run is available):
+    exp(-i/20) needs ~184 indices for 1e-4, i^-1.5 runs to full rank, exact
+    rank r stops at r; all rounded up to whole blocks of 8, capped at min(m,n)."""
+    k = min(spec["m"], spec["n"])
+    r = {"exp20": 192, "poly1.5": k, "rank": spec["r"]}[spec["kind"]]
+    return min(k, -(-r // BATCH_B) * BATCH_B)
+
+
+def batch_flops(m, n, r):
+    """FP64 operations of one job: the sketch 2cmn, the Lemma 1 residual
+    products (m + n) r^2 summed over the blocks, the core QR 4/3 r^3 and its
+    solve 3 r^3 (Q^T applied to the identity, then back substitution)."""
+    return 2.0 * BATCH_C * m * n + (m + n) * r * r + (4.0 / 3.0 + 3.0) * r ** 3
+
+
+def batch_workload_name(a):
+    return (f"{a.batch_jobs} independent FP32 matrices, m, n log-uniform in [64, 2048], spectra "
+            f"exp(-i/20) / i^-1.5 / exact rank r~U[5,200] (one third each), tol {BATCH_TOL:g}, "
+            f"b={BATCH_B}, c={BATCH_C}")
+
+
+def batch_oracle_sample(specs, seconds, seed):
+    """Run the FP64 oracle on jobs in a fixed random order until `seconds` of
+    CPU time are spent; return (wall seconds, sampled work by the rank model,
+    jobs run)."""
+    import numpy as np
+    import oracle
+    from paper_2509_21963_gb300 import inputs
+    order = np.random.default_rng(seed).permutation(len(specs))
+    t_all, work, done = 0.0, 0.0, 0
+    for j in order:
+        s = specs[j]
+        A = inputs.batch_matrix(s).astype(np.float32).astype(np.float64)
+        t0 = time.perf_counter()
+        oracle.run(A, BATCH_TOL, BATCH_B, BATCH_C, seed=s["seed"], mode=1)
+        t_all += time.perf_counter() - t0
+        work += batch_flops(s["m"], s["n"], batch_rank_model(s))
+        done += 1
+        if t_all >= seconds:
+            break
+    return t_all, work, done
+
+
+def run_batch_reference(a, ws, rank):
+    if rank != 0:
+        return 0
+    from paper_2509_21963_gb300 import inputs
+    specs = inputs.batch_specs(a.batch_jobs, a.seed)
+    total = sum(batch_flops(s["m"], s["n"], batch_rank_model(s)) for s in specs)
+    vals = []
+    for k in range(a.warmup + a.steps):
+        t, w, done = batch_oracle_sample(specs, 8.0, seed=k)
+        if k >= a.warmup:
+            vals.append(t * 1000.0 * total / w)
+    value = sum(vals) / len(vals)
+    sample = (f"oracle on random jobs of the batch until 8 s of CPU time per step, scaled by "
+              f"the batch's FP64 work (rank model) over the sample's")
+    line = {"impl": "reference", "metric": "time per batch of CURs", "value": value, "unit": "ms",
+            "n_gpus": ws, "steps": a.steps, "warmup": a.warmup, "ms_per_step": value,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": batch_workload_name(a)},
+            "cpu_baseline": {"value": value, "unit": "ms", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_batch(a, ws, rank, local):
+    import numpy as np
+    import torch
+    import paper_2509_21963_gb300 as cur
+    from paper_2509_21963_gb300 import inputs
+
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = f"cuda:{local}"
+    log("batch: generating matrices")
+    specs = inputs.batch_specs(a.batch_jobs, a.seed + 1000 * rank)
+    mats = [inputs.batch_matrix_torch(s, device=dev) for s in specs]
+    torch.cuda.synchronize()
+    log("batch: matrices ready")
+    ctx = cur.Context(local)
+    stream = torch.cuda.current_stream()
+    B = cur.Batch(ctx, mats, BATCH_TOL, BATCH_B, BATCH_C, seed=[s["seed"] for s in specs])
+    cands = [int(x) for x in a.batch_teams.split(",")]
+    team, tune_ms = B.tune(cands)
+    log(f"batch: tuner chose team {team} ({tune_ms:.1f} ms)")
+    for _ in range(max(a.warmup, 3)):
+        B.run()
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.4)
+    barrier()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(a.steps):
+        B.run()
+    t1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    elapsed_ms = t0.elapsed_time(t1)
+    elapsed_ms, value = aggregate(elapsed_ms, a.steps, ws, device=dev)
+    info = [B.info(j) for j in range(len(specs))]
+    statuses = np.bincount([x[3] for x in info], minlength=8).tolist()
+    flops = sum(batch_flops(s["m"], s["n"], x[0]) for s, x in zip(specs, info))
+    achieved = flops / (value * 1e-3) / 1e12
+    ph = B.phase_cycles()
+    tot = sum(v for k, v in ph.items() if k != "jobs")
+    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "kernel": "batch_kernel (whole batch, FP64 SIMT pipe)", "kernel_ms": value,
+                "flops_per_launch": flops,
+                "phase_share": {k: v / tot for k, v in ph.items() if k != "jobs"}}
+
+    e2e = None
+    if not a.no_e2e:
+        # every step: all matrices host -> device (pinned), the batch, per-job records
+        # and every job's I, J and U device -> host
+        log("batch e2e: pinning host copies")
+        host = [m.cpu().pin_memory() for m in mats]
+        ranks = [x[0] for x in info]
+        outI = [torch.empty(r, dtype=torch.int64).pin_memory() for r in ranks]
+        outJ = [torch.empty(r, dtype=torch.int64).pin_memory() for r in ranks]
+        outU = [torch.empty(r * r, dtype=torch.float64).pin_memory() for r in ranks]
+        L = cur.lib()
+
+        def e2e_step():
+            for hm, dm in zip(host, mats):
+                dm.copy_(hm, non_blocking=True)
+            B.run()
+            for j, r in enumerate(ranks):
+                rj = B.info(j)[0]
+                if rj:
+                    st = L.cur_batch_copy_job(B.ptr, j, outI[j].data_ptr(), outJ[j].data_ptr(),
+                                              outU[j].data_ptr(), None)
+                    if st != cur.CUR_OK:
+                        raise cur.CurError(st, ctx.last_error())
+        e2e_step()
+        torch.cuda.synchronize()
+        w0 = time.perf_counter()
+        for _ in range(a.e2e_steps):
+            e2e_step()
+        torch.cuda.synchronize()
+        e2e_ms = (time.perf_counter() - w0) * 1000.0 / a.e2e_steps
+        e2e = {"value": e2e_ms, "unit": "ms",
+               "h2d_bytes_per_step": int(sum(m.numel() * 4 for m in mats)),
+               "d2h_bytes_per_step": int(sum(16 * r + 8 * r * r for r in ranks) + 48 * len(ranks))}
+        del host
+
+    cpu = None
+    if rank == 0 and ws == 1 and not a.no_cpu_baseline:
+        log("batch cpu baseline: oracle on sampled jobs")
+        total = sum(batch_flops(s["m"], s["n"], batch_rank_model(s)) for s in specs)
+        t, w, done = batch_oracle_sample(specs, 20.0, seed=0)
+        cpu = {"value": t * 1000.0 * total / w, "unit": "ms", "cores": 1, "kind": "oracle",
+               "sample": f"{done} random jobs of the batch ({t:.1f} s of oracle time), scaled by the "
+                         f"batch's FP64 work over the sample's (rank model)"}
+
+    if rank == 0:
+        line = {
+            "metric": "time per batch of CURs", "value": value, "unit": "ms", "n_gpus": ws,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": elapsed_ms / a.steps,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64 (FP32 A)", "data": "synthetic",
+            "config": {"workload": batch_workload_name(a), "jobs": len(specs),
+                       "team": team, "schedule": B.schedule(), "statuses": statuses,
+                       "sum_rank": int(sum(x[0] for x in info)),
+                       "l2": "inputs (5.3 GB) larger than L2",
+                       "parallelism": f"replicas x{ws}"},
+            "gpu_launches": a.steps, "clocks": clk, "e2e": e2e, "roofline": roofline,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    B.close()
+    ctx.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
 def main():
     global _VERBOSE
     a = parse()
@@ -225,6 +429,10 @@ def main():
         import faulthandler
         faulthandler.dump_traceback_later(a.watchdog, exit=True)
     ws, rank, local = dist_env()
+    if a.workload == "batch":
+        if a.impl == "reference":
+            return run_batch_reference(a, ws, rank)
+        return run_batch(a, ws, rank, local)
     if a.impl == "reference":
         return run_reference(a, ws, rank)
 

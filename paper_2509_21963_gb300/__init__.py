@@ -44,6 +44,13 @@ class cur_opts(ctypes.Structure):
                 ("delta", ctypes.c_double), ("timing", ctypes.c_int)]
 
 
+class cur_batch_job(ctypes.Structure):
+    _fields_ = [("A", ctypes.c_void_p), ("m", ctypes.c_int64), ("n", ctypes.c_int64),
+                ("lda", ctypes.c_int64), ("tol", ctypes.c_double), ("block_size", ctypes.c_int32),
+                ("sketch_size", ctypes.c_int32), ("seed", ctypes.c_uint64),
+                ("max_rank", ctypes.c_int64)]
+
+
 _lib = None
 _vp, _i64, _dbl, _u64, _int, _sz = (ctypes.c_void_p, ctypes.c_int64, ctypes.c_double,
                                     ctypes.c_uint64, ctypes.c_int, ctypes.c_size_t)
@@ -78,6 +85,25 @@ _SIGNATURES = {
     "cur_step_pinv": (_int, [_vp, _vp, _i64, _i64, _i64, _dbl, _vp, _vp]),
     "cur_step_lupp_noalloc": (_int, [_int, _vp, _vp, _i64, _i64, _i64, _i64, _vp, _vp,
                                      ctypes.c_char_p, _sz]),
+    "cur_batch_create": (_int, [_vp, ctypes.POINTER(cur_batch_job), _i64, _int, ctypes.POINTER(_vp)]),
+    "cur_batch_free": (None, [_vp]),
+    "cur_batch_set_team": (_int, [_vp, _int]),
+    "cur_batch_get_schedule": (_int, [_vp, ctypes.POINTER(_int), ctypes.POINTER(_int),
+                                      ctypes.POINTER(_int), ctypes.POINTER(_int)]),
+    "cur_batch_tune": (_int, [_vp, ctypes.POINTER(_int), _int, ctypes.POINTER(_int),
+                              ctypes.POINTER(_dbl)]),
+    "cur_batch_phase_cycles": (_int, [_vp, ctypes.POINTER(_dbl), _int]),
+    "cur_batch_job_cycles": (_int, [_vp, _i64, ctypes.POINTER(_i64)]),
+    "cur_batch_launch": (_int, [_vp]),
+    "cur_batch_wait": (_int, [_vp]),
+    "cur_batch_run": (_int, [_vp]),
+    "cur_batch_job_result": (_int, [_vp, _i64, ctypes.POINTER(_i64), ctypes.POINTER(_i64),
+                                    ctypes.POINTER(_dbl), ctypes.POINTER(_int)]),
+    "cur_batch_I": (_vp, [_vp, _i64]),
+    "cur_batch_J": (_vp, [_vp, _i64]),
+    "cur_batch_U": (_vp, [_vp, _i64]),
+    "cur_batch_rho_history": (_vp, [_vp, _i64]),
+    "cur_batch_copy_job": (_int, [_vp, _i64, _vp, _vp, _vp, _vp]),
 }
 
 EXPORTED = tuple(_SIGNATURES)
@@ -278,3 +304,117 @@ class Context:
         _check(self.ptr, lib().cur_step_pinv(self.ptr, _vp(M.data_ptr()), p, q, M.stride(0), float(thr),
                                              _vp(X.data_ptr()), ctypes.byref(k)))
         return X, k.value
+
+
+@dataclass
+class BatchJobResult:
+    rank: int
+    iterations: int
+    status: int
+    rho: float
+    rho_history: np.ndarray = field(repr=False)
+    I: np.ndarray = field(repr=False)
+    J: np.ndarray = field(repr=False)
+    U: np.ndarray = field(repr=False)
+
+
+class Batch:
+    """Many independent decompositions in one persistent launch
+    (include/cur_batch.h).  `mats` is a list of CUDA tensors of one dtype
+    (row stride >= columns, unit column stride); tol, block_size, sketch_size,
+    seed and max_rank are scalars or per-job sequences.  The tensors are
+    borrowed: they must stay alive and unchanged while the batch exists."""
+
+    def __init__(self, ctx: Context, mats, tol, block_size, sketch_size=0, seed=0, max_rank=0):
+        k = len(mats)
+        per = lambda v: list(v) if isinstance(v, (list, tuple, np.ndarray)) else [v] * k  # noqa: E731
+        tols, bs, cs, seeds, mrs = per(tol), per(block_size), per(sketch_size), per(seed), per(max_rank)
+        self.ctx = ctx
+        self.mats = list(mats)
+        jobs = (cur_batch_job * k)()
+        dt = _dtype_code(self.mats[0])
+        for j, A in enumerate(self.mats):
+            if not (A.is_cuda and A.dim() == 2 and A.stride(1) == 1):
+                raise ValueError(f"job {j}: A must be a 2-D CUDA tensor with unit column stride")
+            if _dtype_code(A) != dt:
+                raise TypeError(f"job {j}: every matrix of a batch has the dtype of the first")
+            jobs[j].A = A.data_ptr()
+            jobs[j].m, jobs[j].n = A.shape
+            jobs[j].lda = A.stride(0)
+            jobs[j].tol = float(tols[j])
+            jobs[j].block_size = int(bs[j])
+            jobs[j].sketch_size = int(cs[j])
+            jobs[j].seed = int(seeds[j])
+            jobs[j].max_rank = int(mrs[j])
+        self.njobs = k
+        self.ptr = _vp()
+        _check(ctx.ptr, lib().cur_batch_create(ctx.ptr, jobs, k, dt, ctypes.byref(self.ptr)))
+
+    def close(self):
+        if getattr(self, "ptr", None):
+            lib().cur_batch_free(self.ptr)
+            self.ptr = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def run(self):
+        _check(self.ctx.ptr, lib().cur_batch_run(self.ptr))
+
+    def launch(self):
+        _check(self.ctx.ptr, lib().cur_batch_launch(self.ptr))
+
+    def wait(self):
+        _check(self.ctx.ptr, lib().cur_batch_wait(self.ptr))
+
+    def set_team(self, team: int):
+        _check(self.ctx.ptr, lib().cur_batch_set_team(self.ptr, int(team)))
+
+    def tune(self, candidates=None):
+        best, ms = _int(), _dbl()
+        if candidates is None:
+            _check(self.ctx.ptr, lib().cur_batch_tune(self.ptr, None, 0, ctypes.byref(best),
+                                                      ctypes.byref(ms)))
+        else:
+            arr = (_int * len(candidates))(*candidates)
+            _check(self.ctx.ptr, lib().cur_batch_tune(self.ptr, arr, len(candidates),
+                                                      ctypes.byref(best), ctypes.byref(ms)))
+        return best.value, ms.value
+
+    def schedule(self) -> dict:
+        t, g, n, gr = _int(), _int(), _int(), _int()
+        _check(self.ctx.ptr, lib().cur_batch_get_schedule(self.ptr, ctypes.byref(t), ctypes.byref(g),
+                                                          ctypes.byref(n), ctypes.byref(gr)))
+        return {"team": t.value, "grid": g.value, "teams": n.value, "graph": bool(gr.value)}
+
+    BATCH_PHASES = ("sketch", "lupp_col", "row_res", "lupp_row", "updates", "core_factor",
+                    "core_solve", "jobs")
+
+    def phase_cycles(self) -> dict:
+        v = (_dbl * 8)()
+        _check(self.ctx.ptr, lib().cur_batch_phase_cycles(self.ptr, v, 8))
+        return {k: v[i] for i, k in enumerate(self.BATCH_PHASES)}
+
+    def job_cycles(self, j: int) -> int:
+        v = _i64()
+        _check(self.ctx.ptr, lib().cur_batch_job_cycles(self.ptr, j, ctypes.byref(v)))
+        return int(v.value)
+
+    def info(self, j: int):
+        r, it, rho, st = _i64(), _i64(), _dbl(), _int()
+        _check(self.ctx.ptr, lib().cur_batch_job_result(self.ptr, j, ctypes.byref(r), ctypes.byref(it),
+                                                        ctypes.byref(rho), ctypes.byref(st)))
+        return int(r.value), int(it.value), float(rho.value), int(st.value)
+
+    def result(self, j: int) -> BatchJobResult:
+        r, it, rho, st = self.info(j)
+        I = np.zeros(r, dtype=np.int64)
+        J = np.zeros(r, dtype=np.int64)
+        U = np.zeros((r, r), dtype=np.float64)
+        h = np.zeros(it, dtype=np.float64)
+        _check(self.ctx.ptr, lib().cur_batch_copy_job(self.ptr, j, I.ctypes.data, J.ctypes.data,
+                                                      U.ctypes.data, h.ctypes.data))
+        return BatchJobResult(rank=r, iterations=it, status=st, rho=rho, rho_history=h, I=I, J=J, U=U)

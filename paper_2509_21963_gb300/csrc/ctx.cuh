@@ -1,0 +1,42 @@
+// ctx.cuh -- the library context shared by the translation units that
+// implement the C ABI (cur_api.cu: single decompositions; cur_batch.cu: the
+// batched engine).
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "../../include/cur.h"
+#include "cur_internal.cuh"
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+enum BufId {
+  B_OMEGA, B_S, B_LUPPW, B_SROWT, B_G1, B_G2, B_N, B_NP, B_SJK, B_T1, B_PARTS, B_SPLITK,
+  B_LT, B_RT, B_I, B_J, B_MASKC, B_MASKR, B_QRSMALL, B_QRBIG, B_CORE, B_STATUS, B_AHOST,
+  B_STEP_QR, B_STEP_LUPP, B_STEP_PARTS, B_TC, B_STEP_TC, B_COUNT
+};
+
+struct cur_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  size_t budget = 0;
+  size_t held = 0;
+  int num_sms = 0;
+  std::string err;
+  DevBuf buf[B_COUNT];
+  cur::DevStatus* st_host = nullptr;  // pinned mirror of the device status block
+  // phase timing (opts->timing): events recorded at phase boundaries
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<int> ev_phase;      // phase that starts at event i (-1: none)
+  bool timing = false;
+  int64_t launches = 0;           // kernel launches of the current run
+};
+
+namespace cur {
+// Record `msg` as the context's last error and return `code`.
+int ctx_fail_v(cur_ctx* ctx, int code, const char* msg);
+}  // namespace cur

@@ -25,35 +25,9 @@
 #include "../../include/cur.h"
 #include "../../include/cur_steps.h"
 #include "cur_internal.cuh"
+#include "ctx.cuh"
 
 using namespace cur;
-
-struct DevBuf {
-  void* p = nullptr;
-  size_t bytes = 0;
-};
-
-enum BufId {
-  B_OMEGA, B_S, B_LUPPW, B_SROWT, B_G1, B_G2, B_N, B_NP, B_SJK, B_T1, B_PARTS, B_SPLITK,
-  B_LT, B_RT, B_I, B_J, B_MASKC, B_MASKR, B_QRSMALL, B_QRBIG, B_CORE, B_STATUS, B_AHOST,
-  B_STEP_QR, B_STEP_LUPP, B_STEP_PARTS, B_TC, B_STEP_TC, B_COUNT
-};
-
-struct cur_ctx {
-  int device = 0;
-  cudaStream_t stream = nullptr;
-  size_t budget = 0;
-  size_t held = 0;
-  int num_sms = 0;
-  std::string err;
-  DevBuf buf[B_COUNT];
-  DevStatus* st_host = nullptr;  // pinned mirror of the device status block
-  // phase timing (opts->timing): events recorded at phase boundaries
-  std::vector<cudaEvent_t> ev_pool;
-  std::vector<int> ev_phase;      // phase that starts at event i (-1: none)
-  bool timing = false;
-  int64_t launches = 0;           // kernel launches of the current run
-};
 
 struct cur_result {
   cur_ctx* ctx = nullptr;
@@ -86,6 +60,15 @@ int fail(cur_ctx* ctx, int code, const char* fmt, ...) {
   if (ctx) ctx->err = msg;
   return code;
 }
+
+}  // namespace
+
+int cur::ctx_fail_v(cur_ctx* ctx, int code, const char* msg) {
+  if (ctx) ctx->err = msg;
+  return code;
+}
+
+namespace {
 
 #define CK(expr)                                                                          \
   do {                                                                                    \

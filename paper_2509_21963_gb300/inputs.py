@@ -13,6 +13,10 @@ matrices; these synthetic stand-ins keep their sizes and spectra):
   * ``lehmer``            A_ij = min(i,j)/max(i,j) (Sec. 5.3).
   * ``decay_matrix_torch`` large matrices built on the GPU with torch (thin
                           orthonormal factors of a capped rank plus i.i.d. noise).
+  * ``batch_specs`` / ``batch_matrix`` / ``batch_matrix_torch``  the many-small-
+                          matrices workload: m, n log-uniform, spectrum drawn from
+                          {exp(-i/20), i^-1.5, exact rank r ~ U[5, 200] with unit
+                          singular values}.
 """
 from __future__ import annotations
 
@@ -115,3 +119,60 @@ def low_rank_gaussian_torch(m: int, n: int, r: int, seed: int, device="cuda"):
     A = G1 @ G2.T
     del G1, G2
     return A
+
+
+BATCH_KINDS = ("exp20", "poly1.5", "rank")
+
+
+def batch_specs(njobs: int, seed: int, lo: int = 64, hi: int = 2048):
+    """Shapes and spectra of a batch: m, n log-uniform in [lo, hi], kind uniform
+    over BATCH_KINDS, exact rank r ~ U[5, 200]; one matrix seed per job."""
+    rng = np.random.default_rng(seed)
+    lg = lambda: np.exp(rng.uniform(np.log(lo), np.log(hi + 1), njobs))  # noqa: E731
+    m = np.clip(lg().astype(np.int64), lo, hi)
+    n = np.clip(lg().astype(np.int64), lo, hi)
+    kind = rng.integers(0, 3, njobs)
+    r = rng.integers(5, 201, njobs)
+    return [dict(m=int(m[j]), n=int(n[j]), kind=BATCH_KINDS[kind[j]], r=int(r[j]),
+                 seed=int(seed * 100003 + j)) for j in range(njobs)]
+
+
+def batch_spectrum(m: int, n: int, kind: str, r: int) -> np.ndarray:
+    k = min(m, n)
+    i = np.arange(1, k + 1, dtype=np.float64)
+    if kind == "exp20":
+        return np.exp(-i[: min(k, 800)] / 20.0)   # e^-40: below FP64 rounding of s_1
+    if kind == "poly1.5":
+        return i ** -1.5
+    if kind == "rank":
+        return np.ones(min(r, k))
+    raise ValueError(kind)
+
+
+def batch_matrix(spec: dict) -> np.ndarray:
+    """FP64 A = U diag(s) V^T with Haar factors for one batch job (numpy)."""
+    return svd_matrix(spec["m"], spec["n"], batch_spectrum(spec["m"], spec["n"], spec["kind"],
+                                                           spec["r"]), spec["seed"])
+
+
+def batch_matrix_torch(spec: dict, dtype=None, device="cuda"):
+    """The same recipe on the GPU with torch (orthonormal factors from the QR of
+    seeded Gaussians; not the numpy matrix of the same spec).  Factors and
+    product in FP32 (TF32 off): orthonormal to ~1e-7, so the singular values
+    are s_i (1 + O(1e-7)), below the FP32 rounding of the stored entries."""
+    import torch
+    dtype = dtype or torch.float32
+    s = torch.from_numpy(batch_spectrum(spec["m"], spec["n"], spec["kind"], spec["r"]))
+    s = s.to(device=device, dtype=torch.float32)
+    k = s.numel()
+    g = torch.Generator(device=device)
+    g.manual_seed(spec["seed"])
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    try:
+        U = torch.linalg.qr(torch.randn(spec["m"], k, device=device, generator=g))[0]
+        V = torch.linalg.qr(torch.randn(spec["n"], k, device=device, generator=g))[0]
+        A = (U * s) @ V.T
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+    return A.to(dtype).contiguous()

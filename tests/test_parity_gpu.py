@@ -169,25 +169,71 @@ def _check_parity(A, got, ref, b, require_full=True, rho_rtol=None):
     bound = 1e-10 * ref.rho_hist + 100 * U_RND * np.cumsum((r_l + b + 1) * hist_prev)
     if rho_rtol is not None:
         bound = np.maximum(bound, rho_rtol * ref.rho_hist)
-    assert np.all(np.abs(got.rho_history - ref.rho_hist) <= bound)
-    assert abs(got.rho - ref.rho) <= bound[-1]
+    # Once |I| = |J| = min(m, n) every row (or column) is selected and the exact
+    # residual is zero (S_k vanishes on I and J, Lemma 1): rho there is rounding
+    # noise on both sides, held to a noise ceiling instead of to each other.
+    full = np.minimum(b * np.arange(1, len(hist_prev) + 1), ref.rank) >= min(A.shape)
+    gh = np.asarray(got.rho_history)
+    assert np.all(np.abs(gh - ref.rho_hist)[~full] <= bound[~full])
+    assert np.all(gh[full] <= 1e-9) and np.all(ref.rho_hist[full] <= 1e-9)
+    if not full[-1]:
+        assert abs(got.rho - ref.rho) <= bound[-1]
     if ref.rank:
         _check_core(A, got, ref)
 
 
+def _inv_ext(M):
+    """Inverse by Gauss-Jordan elimination with partial pivoting in np.longdouble
+    (x87 80-bit or IEEE quad): the reference the FP64 cores are measured against."""
+    p = M.shape[0]
+    W = np.array(M, dtype=np.longdouble)
+    X = np.eye(p, dtype=np.longdouble)
+    for k in range(p):
+        q = k + int(np.argmax(np.abs(W[k:, k])))
+        if q != k:
+            W[[k, q]] = W[[q, k]]
+            X[[k, q]] = X[[q, k]]
+        piv = W[k, k]
+        W[k] /= piv
+        X[k] /= piv
+        f = W[:, k].copy()
+        f[k] = 0
+        W -= np.outer(f, W[k])
+        X -= np.outer(f, X[k])
+    return X
+
+
 def _check_core(A, got, ref):
-    """Gate U; return the bound used for the CUR it defines (relative to ||A||)."""
+    """Gate U; return a bound on ||C (U_g - U_o) R|| / ||A||.
+
+    For a nonsingular core M = A(I,J) both sides approximate M^{-1}; their
+    distance is set by each side's own rounding error, which grows with
+    kappa(M) (measured: 6 p^2 u ||CU|| ||M|| ||UR|| for the oracle itself at
+    kappa ~ 1e8, up to 1e-5 relative in U at kappa ~ 1e11).  So the GPU core is
+    held to the oracle's accuracy: measured against an extended-precision
+    inverse, ||C (U_g - M^-1) R|| <= 4 ||C (U_o - M^-1) R|| + 1e-13 ||A|| and
+    ||U_g - M^-1|| <= 4 ||U_o - M^-1|| + 1e-13 ||M^-1||.  A numerically singular
+    core (rank below p in the oracle's pivoted QR) has no unique answer: the
+    CUR it defines must then be as accurate as the oracle's."""
     p = ref.rank
     C, R, M = A[:, ref.J], A[ref.I, :], A[np.ix_(ref.I, ref.J)]
-    kappa = np.linalg.cond(M)
     nA = np.linalg.norm(A)
-    dU_rel = np.linalg.norm(got.U - ref.U) / np.linalg.norm(ref.U)
-    assert dU_rel <= max(1e-10, 32 * p ** 1.5 * kappa * U_RND)
-    dCUR = np.linalg.norm(C @ (got.U - ref.U) @ R) / nA
-    scale = np.linalg.norm(C @ ref.U) * np.linalg.norm(M) * np.linalg.norm(ref.U @ R) / nA
-    bound = max(1e-10, 32 * p ** 1.5 * U_RND * scale)
-    assert dCUR <= bound
-    return bound
+    if np.linalg.matrix_rank(M) < p:
+        e_g = oracle.true_error(A, got.I, got.J, got.U)
+        e_o = oracle.true_error(A, ref.I, ref.J, ref.U)
+        assert e_g <= 1.1 * e_o + 1e-12
+        return abs(e_g - e_o) + 1e-12
+    Mi = _inv_ext(M)
+    def errs(U):
+        # the difference in extended precision; its (small) value then in FP64
+        D = (np.asarray(U, dtype=np.longdouble) - Mi).astype(np.float64)
+        return np.linalg.norm(C @ D @ R) / nA, np.linalg.norm(D)
+    cg, ug = errs(got.U)
+    co, uo = errs(ref.U)
+    nMi = np.linalg.norm(Mi.astype(np.float64))
+    assert ug <= 4 * uo + 1e-13 * nMi, (ug, uo)
+    assert cg <= 4 * co + 1e-13, (cg, co)
+    return cg + co
 
 
 @pytest.mark.parametrize("seed", [0, 1, 2])
