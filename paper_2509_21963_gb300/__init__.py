@@ -51,6 +51,14 @@ class cur_batch_job(ctypes.Structure):
                 ("max_rank", ctypes.c_int64)]
 
 
+class cur_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("admitted", ctypes.c_int64),
+                ("completed", ctypes.c_int64), ("waves", ctypes.c_int64),
+                ("bytes_in_use", ctypes.c_size_t), ("bytes_peak", ctypes.c_size_t),
+                ("budget", ctypes.c_size_t), ("pending", ctypes.c_int64),
+                ("in_flight", ctypes.c_int64)]
+
+
 _lib = None
 _vp, _i64, _dbl, _u64, _int, _sz = (ctypes.c_void_p, ctypes.c_int64, ctypes.c_double,
                                     ctypes.c_uint64, ctypes.c_int, ctypes.c_size_t)
@@ -104,6 +112,18 @@ _SIGNATURES = {
     "cur_batch_U": (_vp, [_vp, _i64]),
     "cur_batch_rho_history": (_vp, [_vp, _i64]),
     "cur_batch_copy_job": (_int, [_vp, _i64, _vp, _vp, _vp, _vp]),
+    "cur_server_create": (_int, [_vp, _sz, _int, _int, _int, ctypes.POINTER(_vp)]),
+    "cur_server_free": (None, [_vp]),
+    "cur_server_submit": (_int, [_vp, ctypes.POINTER(cur_batch_job), _int, ctypes.POINTER(_u64)]),
+    "cur_server_wait": (_int, [_vp, _u64, _dbl]),
+    "cur_server_poll": (_int, [_vp, _u64, ctypes.POINTER(_int)]),
+    "cur_server_drain": (_int, [_vp]),
+    "cur_server_result": (_int, [_vp, _u64, ctypes.POINTER(_i64), ctypes.POINTER(_i64),
+                                 ctypes.POINTER(_dbl), ctypes.POINTER(_int), ctypes.POINTER(_dbl),
+                                 ctypes.POINTER(_dbl)]),
+    "cur_server_copy": (_int, [_vp, _u64, _vp, _vp, _vp, _vp]),
+    "cur_server_release": (_int, [_vp, _u64]),
+    "cur_server_get_stats": (_int, [_vp, ctypes.POINTER(cur_server_stats)]),
 }
 
 EXPORTED = tuple(_SIGNATURES)
@@ -418,3 +438,116 @@ class Batch:
         _check(self.ctx.ptr, lib().cur_batch_copy_job(self.ptr, j, I.ctypes.data, J.ctypes.data,
                                                       U.ctypes.data, h.ctypes.data))
         return BatchJobResult(rank=r, iterations=it, status=st, rho=rho, rho_history=h, I=I, J=J, U=U)
+
+
+@dataclass
+class ServedResult:
+    rank: int
+    iterations: int
+    status: int
+    rho: float
+    latency_ms: float
+    queue_ms: float
+    rho_history: np.ndarray = field(repr=False)
+    I: np.ndarray = field(repr=False)
+    J: np.ndarray = field(repr=False)
+    U: np.ndarray = field(repr=False)
+
+
+class Server:
+    """Serving form (include/cur_server.h): submit requests, the scheduler
+    thread admits them by HBM footprint and runs them in overlapping waves."""
+
+    def __init__(self, ctx: Context, hbm_budget_bytes: int, dtype="float32", team: int = 4,
+                 streams: int = 4):
+        self.ctx = ctx
+        self.dtype = CUR_F32 if str(dtype).endswith("32") else CUR_F64
+        self._keep = {}
+        self.ptr = _vp()
+        _check(ctx.ptr, lib().cur_server_create(ctx.ptr, int(hbm_budget_bytes), self.dtype, int(team),
+                                                int(streams), ctypes.byref(self.ptr)))
+
+    def close(self):
+        if getattr(self, "ptr", None):
+            lib().cur_server_free(self.ptr)
+            self.ptr = _vp()
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, A, tol, block_size, sketch_size=0, seed=0, max_rank=0) -> int:
+        """A: a CUDA tensor (borrowed until the request completes) or a
+        C-contiguous numpy array (host request, copied at admission)."""
+        j = cur_batch_job()
+        on_host = isinstance(A, np.ndarray)
+        if on_host:
+            if not A.flags.c_contiguous:
+                raise ValueError("host A must be C-contiguous")
+            want = np.float32 if self.dtype == CUR_F32 else np.float64
+            if A.dtype != want:
+                raise TypeError(f"server dtype is {np.dtype(want).name}")
+            j.A = A.ctypes.data
+            j.m, j.n = A.shape
+            j.lda = A.shape[1]
+        else:
+            if not (A.is_cuda and A.dim() == 2 and A.stride(1) == 1):
+                raise ValueError("A must be a 2-D CUDA tensor with unit column stride")
+            if _dtype_code(A) != self.dtype:
+                raise TypeError("A's dtype differs from the server's")
+            j.A = A.data_ptr()
+            j.m, j.n = A.shape
+            j.lda = A.stride(0)
+        j.tol = float(tol)
+        j.block_size = int(block_size)
+        j.sketch_size = int(sketch_size)
+        j.seed = int(seed)
+        j.max_rank = int(max_rank)
+        t = _u64()
+        _check(self.ctx.ptr, lib().cur_server_submit(self.ptr, ctypes.byref(j), 1 if on_host else 0,
+                                                     ctypes.byref(t)))
+        self._keep[t.value] = A
+        return t.value
+
+    def wait(self, ticket: int, timeout_s: float = -1.0):
+        _check(self.ctx.ptr, lib().cur_server_wait(self.ptr, ticket, float(timeout_s)))
+
+    def poll(self, ticket: int) -> bool:
+        d = _int()
+        _check(self.ctx.ptr, lib().cur_server_poll(self.ptr, ticket, ctypes.byref(d)))
+        return bool(d.value)
+
+    def drain(self):
+        _check(self.ctx.ptr, lib().cur_server_drain(self.ptr))
+
+    def info(self, ticket: int):
+        r, it, rho, st, lat, q = _i64(), _i64(), _dbl(), _int(), _dbl(), _dbl()
+        _check(self.ctx.ptr, lib().cur_server_result(self.ptr, ticket, ctypes.byref(r), ctypes.byref(it),
+                                                     ctypes.byref(rho), ctypes.byref(st),
+                                                     ctypes.byref(lat), ctypes.byref(q)))
+        return int(r.value), int(it.value), float(rho.value), int(st.value), lat.value, q.value
+
+    def result(self, ticket: int, release: bool = True) -> ServedResult:
+        r, it, rho, st, lat, q = self.info(ticket)
+        I = np.zeros(r, dtype=np.int64)
+        J = np.zeros(r, dtype=np.int64)
+        U = np.zeros((r, r), dtype=np.float64)
+        h = np.zeros(it, dtype=np.float64)
+        _check(self.ctx.ptr, lib().cur_server_copy(self.ptr, ticket, I.ctypes.data, J.ctypes.data,
+                                                   U.ctypes.data, h.ctypes.data))
+        if release:
+            self.release(ticket)
+        return ServedResult(rank=r, iterations=it, status=st, rho=rho, latency_ms=lat, queue_ms=q,
+                            rho_history=h, I=I, J=J, U=U)
+
+    def release(self, ticket: int):
+        _check(self.ctx.ptr, lib().cur_server_release(self.ptr, ticket))
+        self._keep.pop(ticket, None)
+
+    def stats(self) -> dict:
+        o = cur_server_stats()
+        _check(self.ctx.ptr, lib().cur_server_get_stats(self.ptr, ctypes.byref(o)))
+        return {k: getattr(o, k) for k, _ in cur_server_stats._fields_}

@@ -28,6 +28,7 @@
 #include "gridbar.cuh"
 #include "rng.cuh"
 
+#include <cooperative_groups.h>
 #include <cfloat>
 
 namespace cur {
@@ -42,16 +43,22 @@ constexpr int kMaxWarps = 32;
 // Teams and reductions
 // ---------------------------------------------------------------------------
 struct Team {
-  GridBar* bar;     // this team's barrier
+  GridBar* bar;     // this team's barrier (software teams)
   DevStatus* st;    // launch-wide status (timeouts)
   int T;            // CTAs in the team
   int rank;         // this CTA's rank in the team
+  bool cluster;     // the team is a thread-block cluster (hardware barrier)
   __device__ int64_t gtid() const { return (int64_t)rank * blockDim.x + threadIdx.x; }
   __device__ int64_t gsize() const { return (int64_t)T * blockDim.x; }
   // All threads of all CTAs of the team; false on timeout / earlier error.
   __device__ bool sync() const {
     if (T == 1) {
       __syncthreads();
+      return true;
+    }
+    if (cluster) {  // barrier.cluster arrive.release / wait.acquire: the CTAs of a
+                    // cluster are co-scheduled by the hardware, so this wait always ends
+      cooperative_groups::this_cluster().sync();
       return true;
     }
     __shared__ int s_ok;
@@ -87,6 +94,7 @@ __device__ __forceinline__ Team cta_team(const Team& t) {
   Team c = t;
   c.T = 1;
   c.rank = 0;
+  c.cluster = false;
   return c;
 }
 
@@ -407,7 +415,12 @@ __device__ void team_qr_solve_panel(const Team& tm, const QrWs& w, int64_t p, in
       double acc[kPanel];
 #pragma unroll
       for (int c = 0; c < kPanel; ++c) acc[c] = 0.0;
-      for (int64_t i = jj + tid; i < p; i += NT) {
+      // rows stay with thread i % NT for every reflector, so each row of the
+      // panel is only ever touched by one thread (no barrier between the
+      // update of H_jj and the dot of H_jj+1)
+      const int64_t i0 = (jj / NT) * NT + tid;
+      for (int64_t i = i0; i < p; i += NT) {
+        if (i < jj) continue;
         const double vi = __ldcg(v + i);
 #pragma unroll
         for (int c = 0; c < kPanel; ++c) acc[c] += vi * Zs[c * p + i];
@@ -425,7 +438,8 @@ __device__ void team_qr_solve_panel(const Team& tm, const QrWs& w, int64_t p, in
         s_d[tid] = t * sum;
       }
       __syncthreads();
-      for (int64_t i = jj + tid; i < p; i += NT) {
+      for (int64_t i = i0; i < p; i += NT) {
+        if (i < jj) continue;
         const double vi = __ldcg(v + i);
 #pragma unroll
         for (int c = 0; c < kPanel; ++c) Zs[c * p + i] -= s_d[c] * vi;
@@ -464,7 +478,7 @@ __device__ void run_job(const BatchParams& P, const Team& tm, const BatchJobDev&
   const AT* A = static_cast<const AT*>(jb.A);
   const int64_t m = jb.m, n = jb.n, lda = jb.lda, c = jb.c, b = jb.b, rmax = jb.rmax;
   int64_t* Iout = P.Iout + jb.off_ij;
-  int64_t* Jout = P.Jout + jb.off_ij;
+  int64_t* Jout = P.Jout + jb.off_j;
   double* Uout = P.Uout + jb.off_u;
   double* G = tw.G;      // c x m
   double* S = tw.S;      // c x n
@@ -718,6 +732,7 @@ __global__ void __launch_bounds__(256, 1) batch_kernel(BatchParams P) {
   tm.T = T;
   tm.rank = blockIdx.x - team * T;
   tm.st = P.st;
+  tm.cluster = false;
   char* tbase = P.team_scratch + (size_t)team * P.team_bytes;
   TeamWs tw = carve_team(tbase, P.dims, T);
   tm.bar = tw.bar;
@@ -735,6 +750,29 @@ __global__ void __launch_bounds__(256, 1) batch_kernel(BatchParams P) {
     run_job<AT>(P, tm, jb, P.out + jid, tw, cw);
     if (*((volatile int*)&P.st->err) != 0) return;
   }
+}
+
+// Serving form: one thread-block cluster of T CTAs per job (blocks
+// [jid T, (jid + 1) T) along x), every job with its own workspace (team part,
+// T CTA parts), so launches of different waves can run concurrently.
+template <typename AT>
+__global__ void __launch_bounds__(256, 1) serve_kernel(BatchParams P) {
+  cooperative_groups::cluster_group cl = cooperative_groups::this_cluster();
+  Team tm;
+  tm.T = (int)cl.num_blocks();
+  tm.rank = (int)cl.block_rank();
+  tm.st = P.st;
+  tm.cluster = true;
+  tm.bar = nullptr;
+  const long long jid = blockIdx.x / tm.T;
+  if (jid >= P.njobs) return;  // whole clusters only: uniform within the cluster
+  const BatchJobDev jb = P.jobs[jid];
+  const BatchDims d{jb.m, jb.n, jb.c, jb.b, jb.rmax};
+  const BatchLayout L = batch_layout_dev(d, tm.T);
+  const size_t tb = (L.team_bytes + 255) & ~(size_t)255, cb = (L.cta_bytes + 255) & ~(size_t)255;
+  TeamWs tw = carve_team(jb.ws, d, tm.T);
+  CtaWs cw = carve_cta(jb.ws + tb + (size_t)tm.rank * cb, d);
+  run_job<AT>(P, tm, jb, P.out + jid, tw, cw);
 }
 
 }  // namespace
@@ -782,6 +820,66 @@ cudaError_t launch_batch(const LaunchEnv& env, const BatchParams& P, int grid, i
   cfg.numAttrs = 1;
   if (a_f32) return cudaLaunchKernelEx(&cfg, batch_kernel<float>, P);
   return cudaLaunchKernelEx(&cfg, batch_kernel<double>, P);
+}
+
+}  // namespace cur
+
+namespace cur {
+
+size_t serve_job_scratch_bytes(const BatchDims& d, int team) {
+  const BatchLayout L = batch_layout_dev(d, team);
+  const size_t tb = (L.team_bytes + 255) & ~(size_t)255, cb = (L.cta_bytes + 255) & ~(size_t)255;
+  return tb + (size_t)team * cb;
+}
+
+template <typename AT>
+static cudaError_t serve_attr(size_t panel) {
+  cudaError_t e = cudaFuncSetAttribute(serve_kernel<AT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)kBatchMaxPanelBytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(serve_kernel<AT>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  (void)panel;
+  return e;
+}
+
+int serve_max_clusters(const LaunchEnv& env, int team, bool a_f32, size_t panel) {
+  cudaError_t e = a_f32 ? serve_attr<float>(panel) : serve_attr<double>(panel);
+  if (e != cudaSuccess) { cudaGetLastError(); return 0; }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)team);
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = panel;
+  cfg.stream = env.stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)team;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int n = 0;
+  e = a_f32 ? cudaOccupancyMaxActiveClusters(&n, serve_kernel<float>, &cfg)
+            : cudaOccupancyMaxActiveClusters(&n, serve_kernel<double>, &cfg);
+  if (e != cudaSuccess) { cudaGetLastError(); return 0; }
+  return n;
+}
+
+cudaError_t launch_serve(const LaunchEnv& env, const BatchParams& P, int team, bool a_f32) {
+  if (P.njobs <= 0) return cudaSuccess;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(P.njobs * team));
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = P.panel_bytes;
+  cfg.stream = env.stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)team;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (a_f32) return cudaLaunchKernelEx(&cfg, serve_kernel<float>, P);
+  return cudaLaunchKernelEx(&cfg, serve_kernel<double>, P);
 }
 
 }  // namespace cur

@@ -21,9 +21,11 @@ struct BatchJobDev {
   int32_t b, c;
   uint64_t seed;
   int64_t rmax;      // min(m, n) or the caller's max_rank
-  int64_t off_ij;    // offset of this job's I and J (rmax entries each)
+  int64_t off_ij;    // offset of this job's I in Iout (rmax entries)
+  int64_t off_j;     // offset of this job's J in Jout (rmax entries)
   int64_t off_u;     // offset of this job's U (rmax * rmax doubles; r x r used)
   int64_t off_hist;  // offset of this job's rho history (ceil(rmax / b) entries)
+  char* ws;          // serving form: this job's own workspace (team part + CTA parts)
 };
 
 struct BatchOutDev {
@@ -196,6 +198,11 @@ constexpr size_t kBatchMaxPanelBytes = 160 * 1024;
 int batch_max_ctas(const LaunchEnv& env, int threads, bool a_f32, size_t dyn_smem);
 // Panel bytes of the core solve for cores up to rmax (0 when it does not fit).
 size_t batch_panel_bytes(int64_t rmax);
+
+// Serving form (one cluster of `team` CTAs per job, per-job workspaces).
+size_t serve_job_scratch_bytes(const BatchDims& d, int team);
+int serve_max_clusters(const LaunchEnv& env, int team, bool a_f32, size_t panel);
+cudaError_t launch_serve(const LaunchEnv& env, const BatchParams& P, int team, bool a_f32);
 // Cooperative launch of `grid` CTAs (a multiple of P.team, <= batch_max_ctas).
 cudaError_t launch_batch(const LaunchEnv& env, const BatchParams& P, int grid, int threads,
                          bool a_f32);

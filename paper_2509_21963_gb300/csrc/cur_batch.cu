@@ -230,6 +230,8 @@ int cur_batch_create(cur_ctx* ctx, const cur_batch_job* jobs, int64_t njobs, int
     const int64_t mn = std::min(s.m, s.n);
     j.rmax = (s.max_rank <= 0 || s.max_rank > mn) ? mn : s.max_rank;
     j.off_ij = off_ij;
+    j.off_j = off_ij;
+    j.ws = nullptr;
     j.off_u = off_u;
     j.off_hist = off_h;
     off_ij += j.rmax;
@@ -469,7 +471,7 @@ const int64_t* cur_batch_I(const cur_batch* b, int64_t job) {
 
 const int64_t* cur_batch_J(const cur_batch* b, int64_t job) {
   if (!b || job < 0 || job >= b->njobs) return nullptr;
-  return b->P.Jout + b->jobs[(size_t)job].off_ij;
+  return b->P.Jout + b->jobs[(size_t)job].off_j;
 }
 
 const double* cur_batch_U(const cur_batch* b, int64_t job) {
@@ -491,7 +493,7 @@ int cur_batch_copy_job(const cur_batch* b, int64_t job, int64_t* I, int64_t* J, 
   const BatchJobDev& j = b->jobs[(size_t)job];
   if (r > 0) {
     if (I) BCK(cudaMemcpy(I, b->P.Iout + j.off_ij, 8 * (size_t)r, cudaMemcpyDeviceToHost));
-    if (J) BCK(cudaMemcpy(J, b->P.Jout + j.off_ij, 8 * (size_t)r, cudaMemcpyDeviceToHost));
+    if (J) BCK(cudaMemcpy(J, b->P.Jout + j.off_j, 8 * (size_t)r, cudaMemcpyDeviceToHost));
     if (U) BCK(cudaMemcpy(U, b->P.Uout + j.off_u, 8 * (size_t)(r * r), cudaMemcpyDeviceToHost));
   }
   const int64_t it = b->out_host[job].iters;

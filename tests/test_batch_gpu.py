@@ -168,3 +168,31 @@ def test_batch_argument_errors(ctx):
         assert e.value.status == cur.CUR_EINVAL and "job 0" in str(e.value)
     with pytest.raises(TypeError):
         cur.Batch(ctx, [A, A.float()], 1e-3, 4)
+
+
+@pytest.mark.parametrize("team", [1, 4])
+def test_batch_large_cores(ctx, team):
+    """Cores larger than a CTA's 256 threads (p up to 650), where each thread of
+    the core solve owns several rows: against the oracle, and bitwise equal on
+    a second launch (a cross-thread race would show as run-to-run noise)."""
+    import paper_2509_21963_gb300 as cur
+    cases = [(520, 400, "poly1.5", 1e-4, 8, 8), (300, 610, "exp20", 1e-6, 8, 8),
+             (700, 650, "poly1.5", 1e-4, 16, 20), (306, 270, "exp20", 1e-6, 10, 12)]
+    mats, dev = [], []
+    for k, (m, n, kind, *_rest) in enumerate(cases):
+        A = inputs.batch_matrix(dict(m=m, n=n, kind=kind, r=0, seed=90 + k))
+        mats.append(A)
+        dev.append(torch.from_numpy(A).cuda())
+    B = cur.Batch(ctx, dev, [c[3] for c in cases], [c[4] for c in cases], [c[5] for c in cases],
+                  seed=list(range(len(cases))))
+    B.set_team(team)
+    B.run()
+    first = [B.result(j) for j in range(len(cases))]
+    B.run()
+    for j, (m, n, kind, tol, b, c) in enumerate(cases):
+        got = B.result(j)
+        assert np.array_equal(got.U, first[j].U) and got.rho == first[j].rho
+        ref = oracle.run(mats[j], tol, b, c, seed=j, mode=1)
+        assert ref.rank > 256
+        _check_job(mats[j], got, ref, b, tol)
+    B.close()
