@@ -62,11 +62,21 @@ def parse():
     p.add_argument("--paper-workload", action="store_true",
                    help="also time the Low-Rank matrix of Sec. 5.1 (30000^2 FP64, G1 G2^T of rank "
                         "2000, tol 1e-6, b = 250): the paper reports 12 s on a 48-core CPU")
-    p.add_argument("--workload", choices=["primary", "batch"], default="primary",
+    p.add_argument("--workload", choices=["primary", "batch", "serve"], default="primary",
                    help="batch: 4096 independent FP32 matrices (m, n log-uniform in [64, 2048], "
                         "spectra exp(-i/20) / i^-1.5 / exact rank U[5,200]), tol 1e-4, b = c = 8, "
                         "all in one persistent launch; one step = the whole batch")
     p.add_argument("--batch-jobs", type=int, default=4096)
+    p.add_argument("--serve-requests", type=int, default=300)
+    p.add_argument("--serve-rate", type=float, default=200.0, help="Poisson arrival rate (1/s)")
+    p.add_argument("--serve-min", type=int, default=512)
+    p.add_argument("--serve-max", type=int, default=4096)
+    p.add_argument("--serve-team", type=int, default=8)
+    p.add_argument("--serve-streams", type=int, default=4)
+    p.add_argument("--serve-budget-gb", type=float, default=120.0)
+    p.add_argument("--serve-big", type=int, default=500000,
+                   help="requests with m*n at or above this run alone on the whole GPU")
+    p.add_argument("--no-plain-serial", action="store_true")
     p.add_argument("--batch-teams", type=str, default="2,4,8",
                    help="team sizes the batch autotuner tries (CTAs per job)")
     p.add_argument("--verbose", action="store_true", help="stage timestamps on stderr")
@@ -421,6 +431,230 @@ def run_batch(a, ws, rank, local):
     return 0
 
 
+# ---------------------------------------------------------------------------
+# Serving workload
+# ---------------------------------------------------------------------------
+SERVE_B, SERVE_C = 50, 55
+SERVE_TOLS = (1e-2, 1e-4, 1e-6)
+
+
+def serve_stream(a, seed):
+    """Arrival times (s), shapes/spectra and tolerances of the request stream."""
+    import numpy as np
+    from paper_2509_21963_gb300 import inputs
+    rng = np.random.default_rng(seed)
+    arrivals = np.cumsum(rng.exponential(1.0 / a.serve_rate, a.serve_requests))
+    specs = inputs.batch_specs(a.serve_requests, seed + 1, a.serve_min, a.serve_max)
+    tols = [float(t) for t in rng.choice(SERVE_TOLS, a.serve_requests)]
+    return arrivals, specs, tols
+
+
+def serve_rank_model(spec, tol, b):
+    """Rank a request reaches: exp(-i/20) needs 20 ln(1/tol), i^-1.5 about
+    0.65 / tol, exact rank r stops at r; whole blocks of b, capped at min(m, n)."""
+    import math
+    k = min(spec["m"], spec["n"])
+    r = {"exp20": 20 * math.log(1 / tol), "poly1.5": 0.65 / tol, "rank": spec["r"]}[spec["kind"]]
+    return int(min(k, -(-int(r) // b) * b))
+
+
+def serve_flops(m, n, r, b=SERVE_B, c=SERVE_C):
+    return 2.0 * c * m * n + (m + n) * r * r + (4.0 / 3.0 + 3.0) * r ** 3
+
+
+def serve_workload_name(a):
+    return (f"{a.serve_requests} requests, Poisson {a.serve_rate:g}/s, FP32 A with m, n "
+            f"log-uniform in [{a.serve_min}, {a.serve_max}], spectra exp(-i/20) / i^-1.5 / exact "
+            f"rank r~U[5,200], tol uniform over {{1e-2, 1e-4, 1e-6}}, b={SERVE_B}, c={SERVE_C}, "
+            f"{a.serve_budget_gb:g} GB admission budget")
+
+
+def pct(xs, q):
+    import numpy as np
+    return float(np.percentile(np.asarray(xs, dtype=np.float64), q)) if len(xs) else None
+
+
+def serve_oracle_sample(specs, tols, seconds, seed):
+    import numpy as np
+    import oracle
+    from paper_2509_21963_gb300 import inputs
+    order = np.random.default_rng(seed).permutation(len(specs))
+    t_all, work, done = 0.0, 0.0, 0
+    for j in order:
+        s = specs[j]
+        w = serve_flops(s["m"], s["n"], serve_rank_model(s, tols[j], SERVE_B))
+        if w > 5e10 and done > 0:
+            continue  # keep the sample bounded: skip jobs of more than ~1 min on one core
+        A = inputs.batch_matrix(s).astype(np.float32).astype(np.float64)
+        t0 = time.perf_counter()
+        oracle.run(A, tols[j], SERVE_B, SERVE_C, seed=s["seed"], mode=1)
+        t_all += time.perf_counter() - t0
+        work += w
+        done += 1
+        if t_all >= seconds:
+            break
+    return t_all, work, done
+
+
+def run_serve_reference(a, ws, rank):
+    if rank != 0:
+        return 0
+    arrivals, specs, tols = serve_stream(a, a.seed)
+    total = sum(serve_flops(s["m"], s["n"], serve_rank_model(s, t, SERVE_B)) for s, t in zip(specs, tols))
+    vals = []
+    for k in range(a.warmup + a.steps):
+        t, w, done = serve_oracle_sample(specs, tols, 8.0, seed=k)
+        if k >= a.warmup:
+            vals.append(t * 1000.0 * total / w / len(specs))
+    value = sum(vals) / len(vals)
+    line = {"impl": "reference", "metric": "served latency p50 per request", "value": value,
+            "unit": "ms", "n_gpus": ws, "steps": a.steps, "warmup": a.warmup, "ms_per_step": value,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": serve_workload_name(a)},
+            "cpu_baseline": {"value": value, "unit": "ms", "cores": 1, "kind": "oracle",
+                             "sample": "mean oracle time per request over random requests of the "
+                                       "stream (8 s per step), scaled by FP64 work (rank model)"},
+            "e2e": {"value": value, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_serve(a, ws, rank, local):
+    import numpy as np
+    import torch
+    import paper_2509_21963_gb300 as cur
+    from paper_2509_21963_gb300 import inputs
+
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = f"cuda:{local}"
+    arrivals, specs, tols = serve_stream(a, a.seed + 1000 * rank)
+    log("serve: generating matrices")
+    mats = [inputs.batch_matrix_torch(s, device=dev) for s in specs]
+    torch.cuda.synchronize()
+    log("serve: matrices ready")
+    ctx = cur.Context(local)
+    budget = int(a.serve_budget_gb * (1 << 30))
+    S = cur.Server(ctx, budget, "float32", team=a.serve_team, streams=a.serve_streams,
+                   big_elements=a.serve_big)
+
+    # warm-up: a few small requests through the server and the plain path
+    small = sorted(range(len(specs)), key=lambda j: specs[j]["m"] * specs[j]["n"])[:4]
+    for j in small:
+        S.wait(S.submit(mats[j], tols[j], SERVE_B, SERVE_C, seed=specs[j]["seed"]))
+        ctx.run(mats[j], tols[j], SERVE_B, SERVE_C, specs[j]["seed"])
+    S.drain()
+    for st in list(S._keep):
+        S.release(st)
+
+    def play(host):
+        """Submit every request at its arrival time; returns per-request
+        (latency, queue, rank, status) and the makespan in s."""
+        srcs = [m.cpu().numpy() for m in mats] if host else mats
+        barrier_sync()
+        t0 = time.perf_counter()
+        tickets = []
+        for k in range(len(specs)):
+            delay = arrivals[k] - (time.perf_counter() - t0)
+            if delay > 0:
+                time.sleep(delay)
+            tickets.append(S.submit(srcs[k], tols[k], SERVE_B, SERVE_C, seed=specs[k]["seed"]))
+        out = []
+        for tk in tickets:
+            S.wait(tk)
+            r, it, rho, st, lat, q = S.info(tk)
+            out.append((lat, q, r, st))
+            S.release(tk)
+        return out, time.perf_counter() - t0
+
+    def barrier_sync():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.4)
+    log("serve: playing the stream (device-resident requests)")
+    res, makespan = play(False)
+    clk = clocks.stop()
+    lat = [x[0] for x in res]
+    stats = S.stats()
+    flops = sum(serve_flops(s["m"], s["n"], x[2]) for s, x in zip(specs, res))
+    statuses = np.bincount([x[3] for x in res], minlength=8).tolist()
+    met = sum(1 for x in res if x[3] == cur.CUR_OK)
+    log(f"serve: p50 {pct(lat, 50):.1f} ms p99 {pct(lat, 99):.1f} ms makespan {makespan:.2f} s")
+
+    e2e = None
+    if not a.no_e2e:
+        log("serve: playing the stream again with host-resident requests")
+        res_h, makespan_h = play(True)
+        lat_h = [x[0] for x in res_h]
+        e2e = {"value": pct(lat_h, 50), "unit": "ms", "p99_ms": pct(lat_h, 99),
+               "throughput_rps": len(res_h) / makespan_h,
+               "h2d_bytes_per_step": int(sum(m.numel() * 4 for m in mats)),
+               "d2h_bytes_per_step": 0,
+               "note": "requests carry host memory; the server copies each A at admission"}
+
+    plain = None
+    if not a.no_plain_serial:
+        # the plain single-matrix path (cur_run), one request at a time in arrival order:
+        # each starts when it has arrived and the previous one has finished
+        log("serve: plain path, serially")
+        end, lat_p = 0.0, []
+        for k in range(len(specs)):
+            torch.cuda.synchronize()
+            w0 = time.perf_counter()
+            ctx.run(mats[k], tols[k], SERVE_B, SERVE_C, specs[k]["seed"])
+            torch.cuda.synchronize()
+            d = time.perf_counter() - w0
+            start = max(arrivals[k], end)
+            end = start + d
+            lat_p.append((end - arrivals[k]) * 1000.0)
+        plain = {"p50_ms": pct(lat_p, 50), "p99_ms": pct(lat_p, 99),
+                 "throughput_rps": len(specs) / end, "busy_s": end}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not a.no_cpu_baseline:
+        log("serve: cpu baseline")
+        total = sum(serve_flops(s["m"], s["n"], serve_rank_model(s, t, SERVE_B))
+                    for s, t in zip(specs, tols))
+        t, w, done = serve_oracle_sample(specs, tols, 20.0, seed=0)
+        cpu = {"value": t * 1000.0 * total / w / len(specs), "unit": "ms per request", "cores": 1,
+               "kind": "oracle",
+               "sample": f"{done} random requests of the stream ({t:.1f} s of oracle time); mean "
+                         f"time per request scaled by FP64 work (rank model)"}
+
+    if rank == 0:
+        line = {
+            "metric": "served latency p50 per request", "value": pct(lat, 50), "unit": "ms",
+            "n_gpus": ws, "steps": 1, "warmup": 1, "ms_per_step": makespan * 1000.0,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64 (FP32 A)", "data": "synthetic",
+            "p99_ms": pct(lat, 99), "throughput_rps": len(res) / makespan,
+            "queue_p50_ms": pct([x[1] for x in res], 50), "met_tolerance": met,
+            "config": {"workload": serve_workload_name(a), "team": a.serve_team,
+                       "streams": a.serve_streams, "big_elements": a.serve_big,
+                       "statuses": statuses,
+                       "waves": stats["waves"], "bytes_peak": stats["bytes_peak"],
+                       "parallelism": f"replicas x{ws}"},
+            "gpu_launches": stats["waves"], "clocks": clk, "e2e": e2e,
+            "roofline": {"bound": "alu", "achieved": flops / makespan / 1e12,
+                         "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": flops / makespan / 1e12 / FP64_PEAK_TFLOPS, "traffic": None,
+                         "kernel": "serve_kernel waves over the makespan (FP64 SIMT pipe)"},
+            "plain_serial": plain, "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    S.close()
+    ctx.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
 def main():
     global _VERBOSE
     a = parse()
@@ -433,6 +667,10 @@ def main():
         if a.impl == "reference":
             return run_batch_reference(a, ws, rank)
         return run_batch(a, ws, rank, local)
+    if a.workload == "serve":
+        if a.impl == "reference":
+            return run_serve_reference(a, ws, rank)
+        return run_serve(a, ws, rank, local)
     if a.impl == "reference":
         return run_reference(a, ws, rank)
 

@@ -57,21 +57,27 @@ typedef struct cur_server_stats {
 } cur_server_stats;
 
 /* Create a server.
- *   hbm_budget  bytes of device memory the server may hold for requests
- *               (one arena, allocated here; CUR_ENOMEM if it cannot be).
- *   dtype       CUR_F32 or CUR_F64: the element type of every request's A.
- *   team        CTAs (thread-block cluster size, 1..8) per request.
- *   streams     CUDA streams waves are spread over (1..16).
+ *   hbm_budget    bytes of device memory the server may hold for requests
+ *                 (one arena, allocated here; CUR_ENOMEM if it cannot be).
+ *   dtype         CUR_F32 or CUR_F64: the element type of every request's A.
+ *   team          CTAs (thread-block cluster size, 1..8) per request.
+ *   streams       CUDA streams waves are spread over (1..16).
+ *   big_elements  requests with m * n >= big_elements (0: none) are large:
+ *                 each runs alone on the whole GPU through the single-matrix
+ *                 path (the kernels of cur_run, on a private context and
+ *                 stream, workspace outside the arena) once the waves in
+ *                 flight have drained; smaller requests keep flowing in waves
+ *                 before and after it.
  * The scheduler thread starts here and stops in cur_server_free. */
 int cur_server_create(cur_ctx *ctx, size_t hbm_budget, int dtype, int team, int streams,
-                      cur_server **out);
+                      int64_t big_elements, cur_server **out);
 
 /* Stop the scheduler (after the requests in flight finish) and release
  * everything.  NULL is a no-op. */
 void cur_server_free(cur_server *srv);
 
 /* Queue a request.  job: as for cur_batch_create (block_size <= 64,
- * sketch_size <= 128).  a_on_host = 0: job->A is device memory, borrowed
+ * sketch_size <= 128; large requests follow cur_run's rules).  a_on_host = 0: job->A is device memory, borrowed
  * until the request completes; a_on_host = 1: job->A is host memory, copied
  * to the device when the request is admitted (it must stay valid until then).
  * *ticket identifies the request.  CUR_EINVAL for a malformed job,

@@ -112,7 +112,7 @@ _SIGNATURES = {
     "cur_batch_U": (_vp, [_vp, _i64]),
     "cur_batch_rho_history": (_vp, [_vp, _i64]),
     "cur_batch_copy_job": (_int, [_vp, _i64, _vp, _vp, _vp, _vp]),
-    "cur_server_create": (_int, [_vp, _sz, _int, _int, _int, ctypes.POINTER(_vp)]),
+    "cur_server_create": (_int, [_vp, _sz, _int, _int, _int, _i64, ctypes.POINTER(_vp)]),
     "cur_server_free": (None, [_vp]),
     "cur_server_submit": (_int, [_vp, ctypes.POINTER(cur_batch_job), _int, ctypes.POINTER(_u64)]),
     "cur_server_wait": (_int, [_vp, _u64, _dbl]),
@@ -459,13 +459,14 @@ class Server:
     thread admits them by HBM footprint and runs them in overlapping waves."""
 
     def __init__(self, ctx: Context, hbm_budget_bytes: int, dtype="float32", team: int = 4,
-                 streams: int = 4):
+                 streams: int = 4, big_elements: int = 0):
         self.ctx = ctx
         self.dtype = CUR_F32 if str(dtype).endswith("32") else CUR_F64
         self._keep = {}
         self.ptr = _vp()
         _check(ctx.ptr, lib().cur_server_create(ctx.ptr, int(hbm_budget_bytes), self.dtype, int(team),
-                                                int(streams), ctypes.byref(self.ptr)))
+                                                int(streams), int(big_elements),
+                                                ctypes.byref(self.ptr)))
 
     def close(self):
         if getattr(self, "ptr", None):

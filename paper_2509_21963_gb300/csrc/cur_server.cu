@@ -90,6 +90,7 @@ struct Req {
   BatchOutDev out{};
   double t_submit = 0, t_admit = 0, t_done = 0;
   int state = kPending;
+  bool big = false;  // runs alone on the whole GPU through the single-matrix path
 };
 
 struct Wave {
@@ -107,6 +108,9 @@ constexpr size_t kDescPool = 64ull << 20;
 
 struct cur_server {
   cur_ctx* ctx = nullptr;
+  cur_ctx* big_ctx = nullptr;        // private context (own stream) of the large-request path
+  cudaStream_t big_stream = nullptr;
+  int64_t big_elements = 0;          // m * n at or above which a request runs alone
   bool a_f32 = true;
   int team = 4;
   std::vector<cudaStream_t> streams;
@@ -152,10 +156,13 @@ void release_scratch(cur_server* s, Req* r) {
 
 bool try_admit(cur_server* s, Req* r) {
   size_t so = 0, oo = 0, ao = 0;
-  if (!s->arena.alloc(r->scratch_bytes, &so)) return false;
-  if (!s->arena.alloc(r->out_bytes, &oo)) { s->arena.release(so, r->scratch_bytes); return false; }
+  if (r->scratch_bytes && !s->arena.alloc(r->scratch_bytes, &so)) return false;
+  if (!s->arena.alloc(r->out_bytes, &oo)) {
+    if (r->scratch_bytes) s->arena.release(so, r->scratch_bytes);
+    return false;
+  }
   if (r->a_bytes && !s->arena.alloc(r->a_bytes, &ao)) {
-    s->arena.release(so, r->scratch_bytes);
+    if (r->scratch_bytes) s->arena.release(so, r->scratch_bytes);
     s->arena.release(oo, r->out_bytes);
     return false;
   }
@@ -281,6 +288,59 @@ void finish_wave(cur_server* s, Wave& w, cudaError_t q) {
   w.ev = nullptr;
 }
 
+// Run one large request alone through the single-matrix path (cur_run_opts
+// on the private context), then copy its I, J, U and rho history into the
+// request's output block.  Called with the lock released and no wave in flight.
+void run_big(cur_server* s, Req* r) {
+  const size_t es = s->a_f32 ? 4 : 8;
+  const void* A = r->job.A;
+  int64_t lda = r->job.lda;
+  cudaError_t e = cudaSuccess;
+  if (r->a_on_host) {
+    e = cudaMemcpy2DAsync(s->arena_base + r->a_off, (size_t)r->job.n * es, r->job.A,
+                          (size_t)r->job.lda * es, (size_t)r->job.n * es, (size_t)r->job.m,
+                          cudaMemcpyHostToDevice, s->big_stream);
+    A = s->arena_base + r->a_off;
+    lda = r->job.n;
+  }
+  cur_opts o{};
+  o.max_rank = r->rmax;
+  cur_result* res = nullptr;
+  int st = e == cudaSuccess ? cur_run_opts(s->big_ctx, A, r->job.m, r->job.n, lda,
+                                           s->a_f32 ? CUR_F32 : CUR_F64, r->job.tol,
+                                           r->job.block_size, r->c, r->job.seed, &o, &res)
+                            : CUR_ECUDA;
+  r->out = BatchOutDev{};
+  if (res) {
+    const int64_t k = cur_result_rank(res), it = cur_result_iterations(res);
+    r->out.rank = k;
+    r->out.iters = it;
+    r->out.rho = cur_result_err(res);
+    r->out.normY = cur_result_sketch_norm(res);
+    r->out.status = cur_result_status(res);
+    char* base = s->arena_base;
+    if (k > 0) {
+      e = cudaMemcpyAsync(base + r->off_I, cur_result_I(res), 8 * (size_t)k,
+                          cudaMemcpyDeviceToDevice, s->big_stream);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(base + r->off_J, cur_result_J(res), 8 * (size_t)k,
+                            cudaMemcpyDeviceToDevice, s->big_stream);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(base + r->off_U, cur_result_U(res), 8 * (size_t)(k * k),
+                            cudaMemcpyDeviceToDevice, s->big_stream);
+    }
+    const double* h = cur_result_rho_history(res);
+    if (e == cudaSuccess && it > 0 && h)
+      e = cudaMemcpyAsync(base + r->off_h, h, 8 * (size_t)it, cudaMemcpyHostToDevice,
+                          s->big_stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->big_stream);
+    cur_result_free(res);
+    if (e != cudaSuccess) r->out.status = CUR_ECUDA;
+  } else {
+    r->out.status = st == CUR_OK ? CUR_ECUDA : st;
+  }
+}
+
 void admit(cur_server* s) {
   int skipped = 0;
   for (auto it = s->pending.begin(); it != s->pending.end() && skipped <= kBackfill;) {
@@ -313,7 +373,38 @@ void worker_main(cur_server* s) {
     }
     if (progressed) s->cv_done.notify_all();
     admit(s);
-    if (!s->ready.empty()) {
+    // a large request at the head of the ready list runs alone once the waves
+    // in flight have drained (no wave is launched while one is waiting)
+    auto big_it = std::find_if(s->ready.begin(), s->ready.end(), [](Req* q) { return q->big; });
+    if (big_it != s->ready.end()) {
+      if (big_it == s->ready.begin()) {
+        if (s->inflight.empty()) {
+          Req* r = *big_it;
+          s->ready.erase(big_it);
+          r->state = kRunning;
+          lk.unlock();
+          run_big(s, r);
+          lk.lock();
+          r->t_done = now_ms();
+          r->state = kDone;
+          if (r->a_bytes) s->arena.release(r->a_off, r->a_bytes);
+          r->a_bytes = 0;
+          s->n_completed += 1;
+          s->n_waves += 1;
+          s->cv_done.notify_all();
+          progressed = true;
+        }
+      } else {
+        // small requests ahead of the large one go out as one wave first
+        const size_t nsmall = (size_t)(big_it - s->ready.begin());
+        std::vector<Req*> rest(big_it, s->ready.end());
+        s->ready.resize(nsmall);
+        launch_wave(s);
+        const bool launched = s->ready.empty();
+        s->ready.insert(s->ready.end(), rest.begin(), rest.end());
+        if (launched) progressed = true;
+      }
+    } else if (!s->ready.empty()) {
       const size_t before = s->ready.size();
       launch_wave(s);
       if (s->ready.size() != before) progressed = true;
@@ -343,7 +434,7 @@ Req* find(cur_server* s, uint64_t ticket) {
 extern "C" {
 
 int cur_server_create(cur_ctx* ctx, size_t hbm_budget, int dtype, int team, int streams,
-                      cur_server** out) {
+                      int64_t big_elements, cur_server** out) {
   if (!out) return sfail(ctx, CUR_EINVAL, "out is NULL");
   *out = nullptr;
   if (!ctx) return CUR_EINVAL;
@@ -363,6 +454,7 @@ int cur_server_create(cur_ctx* ctx, size_t hbm_budget, int dtype, int team, int 
   s->ctx = ctx;
   s->a_f32 = f32;
   s->team = team;
+  s->big_elements = big_elements > 0 ? big_elements : 0;
   cudaError_t e = cudaMalloc((void**)&s->arena_base, hbm_budget);
   if (e == cudaSuccess) e = cudaMalloc((void**)&s->desc_base, kDescPool);
   if (e == cudaSuccess) e = cudaMalloc((void**)&s->st, sizeof(DevStatus) + 256);
@@ -376,6 +468,9 @@ int cur_server_create(cur_ctx* ctx, size_t hbm_budget, int dtype, int team, int 
     if (e == cudaSuccess) s->streams.push_back(st);
   }
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->readback, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->big_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess && cur_create(&s->big_ctx, ctx->device, s->big_stream, 0) != CUR_OK)
+    e = cudaErrorMemoryAllocation;
   if (e != cudaSuccess) {
     cudaGetLastError();
     cur_server_free(s);
@@ -411,6 +506,8 @@ void cur_server_free(cur_server* s) {
   if (s->st) cudaFree(s->st);
   for (cudaStream_t st : s->streams) cudaStreamDestroy(st);
   if (s->readback) cudaStreamDestroy(s->readback);
+  if (s->big_ctx) cur_free(s->big_ctx);
+  if (s->big_stream) cudaStreamDestroy(s->big_stream);
   cudaGetLastError();
   delete s;
 }
@@ -434,7 +531,9 @@ int cur_server_submit(cur_server* s, const cur_batch_job* job, int a_on_host, ui
   const int64_t mn = std::min(job->m, job->n);
   r->rmax = (job->max_rank <= 0 || job->max_rank > mn) ? mn : job->max_rank;
   const BatchDims d{job->m, job->n, c, job->block_size, r->rmax};
-  r->scratch_bytes = serve_job_scratch_bytes(d, s->team);
+  r->big = s->big_elements > 0 && job->m * job->n >= s->big_elements;
+  // a large request's scratch lives in the private context's workspace
+  r->scratch_bytes = r->big ? 0 : serve_job_scratch_bytes(d, s->team);
   const size_t rm = (size_t)r->rmax;
   r->out_bytes = 2 * al256(8 * rm) + al256(8 * rm * rm) +
                  al256(8 * (size_t)((r->rmax + job->block_size - 1) / job->block_size));

@@ -135,3 +135,35 @@ def test_serve_errors(ctx):
     S.close()
     with pytest.raises(cur.CurError):
         cur.Server(ctx, 1 << 30, "float32", team=9)
+
+
+def test_serve_large_requests_alone(ctx):
+    """Requests at or above the size threshold run alone through the
+    single-matrix path: the same result as cur_run on the caller's context,
+    with small requests served before and after them."""
+    import paper_2509_21963_gb300 as cur
+    specs, tols, mats = _requests(8, seed=31, lo=64, hi=300)
+    big = inputs.batch_matrix(dict(m=900, n=700, kind="exp20", r=0, seed=4)).astype(np.float32)
+    S = cur.Server(ctx, 2 << 30, "float32", team=2, streams=2, big_elements=500_000)
+    dev = [torch.from_numpy(A).cuda() for A in mats]
+    bd = torch.from_numpy(big).cuda()
+    tickets = [S.submit(A, t, 8, 8, seed=s["seed"]) for A, t, s in zip(dev[:4], tols, specs)]
+    tb = S.submit(bd, 1e-6, 50, 55, seed=9)
+    th = S.submit(big, 1e-6, 50, 55, seed=9)  # the same large request from host memory
+    tickets += [S.submit(A, t, 8, 8, seed=s["seed"]) for A, t, s in zip(dev[4:], tols[4:], specs[4:])]
+    S.drain()
+    ref_run = ctx.run(bd, 1e-6, 50, 55, 9)
+    for t in (tb, th):
+        got = S.result(t)
+        assert np.array_equal(got.I, ref_run.I) and np.array_equal(got.J, ref_run.J)
+        assert np.array_equal(got.U, ref_run.U) and got.rho == ref_run.rho
+        assert np.array_equal(got.rho_history, ref_run.rho_history)
+    big64 = big.astype(np.float64)
+    ref = oracle.run(big64, 1e-6, 50, 55, seed=9, mode=1)
+    _check_job(big64, ref_run, ref, 50, 1e-6)
+    for tk, A, t, s in zip(tickets, mats, tols, specs):
+        got = S.result(tk)
+        A64 = A.astype(np.float64)
+        _check_job(A64, got, oracle.run(A64, t, 8, 8, seed=s["seed"], mode=1), 8, t)
+    assert S.stats()["bytes_in_use"] == 0
+    S.close()
