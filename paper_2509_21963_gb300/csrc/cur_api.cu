@@ -247,7 +247,8 @@ int sketch_q(cur_ctx* ctx, int S, const double* G, int64_t c, const float* A, in
   LaunchEnv env = env_of(ctx);
   int ks = sketch_tc_plan_ks(env, m, n);
   TRY(ensure(ctx, scratch_id, sketch_tc_scratch_bytes(c, m, n, ks)));
-  const int64_t nparts_max = (c * n + 16383) / 16384;
+  // one partial per 256 columns and 16 rows of the reduction
+  const int64_t nparts_max = ((n + 255) / 256) * ((c + 15) / 16);
   TRY(ensure(ctx, parts_id, sizeof(double) * (size_t)nparts_max));
   int64_t nparts = 0;
   CK(launch_sketch_tc(env, S, G, c, A, lda, m, n, ctx->buf[scratch_id].p, ks, Y,

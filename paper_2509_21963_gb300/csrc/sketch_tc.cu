@@ -9,8 +9,9 @@
 //   * each column j of A (FP32) gets the scale 2^E_j with max_k |A(k,j)| < 2^E_j
 //     (colmax pre-pass), and every entry is written with S signed base-256
 //     digits d_s (|d_s| <= 256, exact in BF16): fix_S(x) = 2^(E_j-8S) sum d_s 256^s.
-//   * one MMA product is |q d| <= 127 * 256 < 2^15; a chunk of 256 rows sums to
-//     < 2^23, so the FP32 accumulator of each digit slice is an exact integer.
+//   * one MMA product is |q d| <= 127 * 256 = 32512; a chunk of 512 rows sums to
+//     at most 16646144 < 2^24, so the FP32 accumulator of each digit slice is an
+//     exact integer.
 //     Chunks are drained to int64 (exact) and combined over the K range; the
 //     FP64 result 2^(E_j-8S) sum_s 256^s D_s is exact as long as it fits 53
 //     bits (it does: < 2^47).
@@ -38,7 +39,7 @@ namespace {
 
 constexpr int kTileK = 64;        // rows of A per stage = MMA K per stage
 constexpr int kTileN = 128;       // columns of A per CTA tile = MMA M
-constexpr int kChunkTiles = 4;    // stages per exact accumulation chunk (256 rows)
+constexpr int kChunkTiles = 8;    // stages per exact accumulation chunk (512 rows)
 constexpr int kConvWarps = 8;
 constexpr int kThreads = (2 + kConvWarps) * 32;
 constexpr long long kWaitBudget = 4000000000LL;  // ~2 s at 2 GHz
@@ -133,11 +134,30 @@ __device__ __forceinline__ void fence_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
-// Exact rint for |y| < 2^22 (round to nearest even through the FP32 adder).
-__device__ __forceinline__ float rint_small(float y) {
-  const float magic = 12582912.0f;  // 1.5 * 2^23
-  return __fsub_rn(__fadd_rn(y, magic), magic);
+// Packed pairs of FP32 (Blackwell f32x2): each lane rounds like the scalar
+// instruction, so the digits below are bit-identical to scalar arithmetic.
+__device__ __forceinline__ uint64_t f2_add(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
 }
+__device__ __forceinline__ uint64_t f2_sub(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ uint64_t f2_mul(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ uint64_t f2_pack(float lo, float hi) {
+  return (uint64_t)__float_as_uint(lo) | ((uint64_t)__float_as_uint(hi) << 32);
+}
+// 1.5 * 2^23 in both lanes: (y + M) - M rounds |y| < 2^22 to the nearest
+// integer (ties to even) through the FP32 adder.
+constexpr uint64_t kMagic2 = 0x4B4000004B400000ull;
+constexpr uint64_t k256x2 = 0x4380000043800000ull;  // 256.0f in both lanes
 
 // FP32 accumulator holding an exact integer (|v| < 2^24) -> int32.
 __device__ __forceinline__ int f2i_exact(uint32_t bits) { return __float2int_rn(__uint_as_float(bits)); }
@@ -147,7 +167,7 @@ struct TcArgs {
   int c, c_pad;
   const int* colexp;       // E_j per column (pre-pass)
   unsigned long long* acc; // c x n int64 sums (two's complement), zeroed by the host
-  int64_t kunit;           // rows of A per work unit (multiple of 256)
+  int64_t kunit;           // rows of A per work unit (multiple of 512)
   int ks;                  // work units along K
   int64_t nstrips;         // column strips of 128
   int* err;                // device error word
@@ -314,6 +334,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int64_t jg = strip * kTileN + jl;
       const int E = jg < g.n ? g.colexp[jg] : 0;
       const float sc = ldexpf(1.0f, min(8 - E, 126));  // columns below 2^-118: digits lose range
+      const uint64_t sc2 = f2_pack(sc, sc);
       for (int i = 0; i < nt && ok; ++i, ++t) {
         const uint32_t sa = t % NA, so = t % NO;
         // the operand stage must be free of the MMAs that read it last time
@@ -331,14 +352,15 @@ __global__ void __launch_bounds__(kThreads, 1)
           uint32_t packed[S][4];
 #pragma unroll
           for (int e = 0; e < 8; e += 2) {
-            float y0 = At[(kg * 8 + e) * kTileN + jl] * sc;
-            float y1 = At[(kg * 8 + e + 1) * kTileN + jl] * sc;
+            // rows k, k+1 of column jl as one f32x2 pair, scaled by 2^(8 - E_j) (exact)
+            uint64_t y = f2_mul(f2_pack(At[(kg * 8 + e) * kTileN + jl],
+                                        At[(kg * 8 + e + 1) * kTileN + jl]), sc2);
 #pragma unroll
             for (int sl = S - 1; sl >= 0; --sl) {
-              float d0 = rint_small(y0), d1 = rint_small(y1);
-              packed[sl][e >> 1] = (__float_as_uint(d0) >> 16) | (__float_as_uint(d1) & 0xFFFF0000u);
-              y0 = __fmul_rn(__fsub_rn(y0, d0), 256.0f);
-              y1 = __fmul_rn(__fsub_rn(y1, d1), 256.0f);
+              const uint64_t d = f2_sub(f2_add(y, kMagic2), kMagic2);
+              // the two digits are integers |d| <= 256: their top halves are exact BF16
+              packed[sl][e >> 1] = __byte_perm((uint32_t)d, (uint32_t)(d >> 32), 0x7632);
+              if (sl > 0) y = f2_mul(f2_sub(y, d), k256x2);
             }
           }
           // K-major SW128: row jl, 16-byte chunk kg at (kg ^ (jl & 7))
@@ -417,8 +439,10 @@ __global__ void colmax_kernel(const float* __restrict__ A, int64_t lda, int64_t 
   atomicMax(&colmax_bits[j], mx);
 }
 
-__global__ void colexp_kernel(const unsigned* __restrict__ colmax_bits, int64_t n,
-                              int* __restrict__ colexp) {
+// E_j, and the scale 2^(E_j - 8S) that turns column j's integer sums into Y
+// (NaN for a column holding Inf/NaN).
+__global__ void colexp_kernel(const unsigned* __restrict__ colmax_bits, int64_t n, int S,
+                              int* __restrict__ colexp, double* __restrict__ colscale) {
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n) return;
   const unsigned b = colmax_bits[j];
@@ -426,23 +450,29 @@ __global__ void colexp_kernel(const unsigned* __restrict__ colmax_bits, int64_t 
   if (b >= 0x7F800000u) E = 1 << 20;          // Inf/NaN: flagged by the reduction
   else if (b != 0) frexpf(__uint_as_float(b), &E);
   colexp[j] = E;
+  colscale[j] = (E >= (1 << 20)) ? __longlong_as_double(0x7FF8000000000000LL)
+                                 : ldexp(1.0, E - 8 * S);
 }
 
-// Y[i, j] = 2^(E_j - 8S) acc[i][j] (exact: |acc| < 2^53), plus per-CTA sums of squares.
-__global__ void tc_reduce_kernel(const long long* __restrict__ acc, int64_t c, int64_t n, int S,
-                                 const int* __restrict__ colexp, double* __restrict__ Y,
-                                 double* __restrict__ sumsq_part, int64_t per_cta) {
+// Y[i, j] = 2^(E_j - 8S) acc[i][j] (exact: |acc| < 2^53 and the scale is a
+// power of two): one thread per column of a 256-column block and a group of
+// kReduceRows rows (blockIdx.y), plus per-CTA sums of squares.
+constexpr int kReduceRows = 16;
+
+__global__ void tc_reduce_kernel(const long long* __restrict__ acc, int64_t c, int64_t n,
+                                 const double* __restrict__ colscale, double* __restrict__ Y,
+                                 double* __restrict__ sumsq_part) {
   __shared__ double red[8];
-  const int64_t total = c * n;
-  const int64_t beg = (int64_t)blockIdx.x * per_cta, end = min(total, beg + per_cta);
+  const int64_t j = (int64_t)blockIdx.x * 256 + threadIdx.x;
+  const int64_t i0 = (int64_t)blockIdx.y * kReduceRows, i1 = min(c, i0 + kReduceRows);
   double ss = 0.0;
-  for (int64_t e = beg + threadIdx.x; e < end; e += 256) {
-    const int64_t j = e % n;
-    const int E = colexp[j];
-    double y = (E >= (1 << 20)) ? __longlong_as_double(0x7FF8000000000000LL)
-                                : ldexp((double)acc[e], E - 8 * S);
-    Y[e] = y;
-    ss = fma(y, y, ss);
+  if (j < n) {
+    const double sc = colscale[j];
+    for (int64_t i = i0; i < i1; ++i) {
+      const double y = (double)acc[i * n + j] * sc;
+      Y[i * n + j] = y;
+      ss = fma(y, y, ss);
+    }
   }
   for (int o = 16; o > 0; o >>= 1) ss += __shfl_down_sync(0xffffffffu, ss, o);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = ss;
@@ -450,7 +480,7 @@ __global__ void tc_reduce_kernel(const long long* __restrict__ acc, int64_t c, i
   if (threadIdx.x == 0) {
     double t = 0.0;
     for (int w = 0; w < 8; ++w) t += red[w];
-    sumsq_part[blockIdx.x] = t;
+    sumsq_part[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = t;
   }
 }
 
@@ -504,7 +534,7 @@ int sketch_tc_cpad(int c, int S) {
   int cp = (c + 15) / 16 * 16;
   if (cp < 16) cp = 16;
   // instantiated widths
-  const int widths[] = {16, 32, 48, 64, 80, 96, 128};
+  const int widths[] = {16, 32, 48, 64, 80, 96, 112, 128};
   for (int w : widths)
     if (w >= cp && 2 * S * w <= 512) return w;
   return -1;
@@ -517,6 +547,7 @@ size_t sketch_tc_scratch_bytes(int64_t c, int64_t m, int64_t n, int ks) {
   add(sizeof(uint16_t) * (size_t)(c * ldq));     // G_q
   add(sizeof(unsigned) * (size_t)n);             // column max bits
   add(sizeof(int) * (size_t)n);                  // column exponents
+  add(sizeof(double) * (size_t)n);               // column scales
   add(sizeof(long long) * (size_t)c * n);        // int64 sums
   return b;
 }
@@ -542,6 +573,7 @@ cudaError_t launch_sketch_tc(const LaunchEnv& env, int S, const double* G, int64
   uint16_t* Gq = (uint16_t*)take(sizeof(uint16_t) * (size_t)(c * ldq));
   unsigned* cmax = (unsigned*)take(sizeof(unsigned) * (size_t)n);
   int* cexp = (int*)take(sizeof(int) * (size_t)n);
+  double* cscale = (double*)take(sizeof(double) * (size_t)n);
   long long* acc64 = (long long*)take(sizeof(long long) * (size_t)c * n);
 
   // G_q (BF16, rows padded to a multiple of 64 so TMA strides are 16-byte multiples)
@@ -557,7 +589,7 @@ cudaError_t launch_sketch_tc(const LaunchEnv& env, int S, const double* G, int64
     int64_t rows_per = 512;
     dim3 grid((unsigned)((n + 255) / 256), (unsigned)((m + rows_per - 1) / rows_per));
     colmax_kernel<<<grid, 256, 0, env.stream>>>(A, lda, m, n, rows_per, cmax);
-    colexp_kernel<<<(unsigned)((n + 255) / 256), 256, 0, env.stream>>>(cmax, n, cexp);
+    colexp_kernel<<<(unsigned)((n + 255) / 256), 256, 0, env.stream>>>(cmax, n, S, cexp, cscale);
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -601,21 +633,18 @@ cudaError_t launch_sketch_tc(const LaunchEnv& env, int S, const double* G, int64
   if (S == SS && CP == CC) e = launch_tc<SS, CC>(env, mA, mG, a, grid); \
   else
   CUR_TC_CASE(1, 16) CUR_TC_CASE(1, 32) CUR_TC_CASE(1, 48) CUR_TC_CASE(1, 64)
-  CUR_TC_CASE(1, 80) CUR_TC_CASE(1, 96) CUR_TC_CASE(1, 128)
+  CUR_TC_CASE(1, 80) CUR_TC_CASE(1, 96) CUR_TC_CASE(1, 112) CUR_TC_CASE(1, 128)
   CUR_TC_CASE(2, 16) CUR_TC_CASE(2, 32) CUR_TC_CASE(2, 48) CUR_TC_CASE(2, 64)
-  CUR_TC_CASE(2, 80) CUR_TC_CASE(2, 96) CUR_TC_CASE(2, 128)
+  CUR_TC_CASE(2, 80) CUR_TC_CASE(2, 96) CUR_TC_CASE(2, 112) CUR_TC_CASE(2, 128)
   CUR_TC_CASE(3, 16) CUR_TC_CASE(3, 32) CUR_TC_CASE(3, 48) CUR_TC_CASE(3, 64)
   CUR_TC_CASE(3, 80)
   e = cudaErrorInvalidValue;
 #undef CUR_TC_CASE
   if (e != cudaSuccess) return e;
 
-  const int64_t total = c * n;
-  const int64_t per = 16384;
-  const int64_t nblk = (total + per - 1) / per;
-  tc_reduce_kernel<<<(unsigned)nblk, 256, 0, env.stream>>>(acc64, c, n, S, cexp, Y, sumsq_part,
-                                                           per);
-  *nparts = nblk;
+  const dim3 rgrid((unsigned)((n + 255) / 256), (unsigned)((c + kReduceRows - 1) / kReduceRows));
+  tc_reduce_kernel<<<rgrid, 256, 0, env.stream>>>(acc64, c, n, cscale, Y, sumsq_part);
+  *nparts = (int64_t)rgrid.x * rgrid.y;
   return cudaGetLastError();
 }
 

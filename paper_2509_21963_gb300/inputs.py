@@ -68,13 +68,16 @@ def explicit_sketch(c: int, m: int, seed: int) -> np.ndarray:
 
 
 def decay_matrix_torch(m: int, n: int, spectrum: str, seed: int, noise: float = 0.0,
-                       rank_cap: int = 2000, dtype=None, device="cuda"):
+                       rank_cap: int = 2000, dtype=None, device="cuda", factor_dtype=None):
     """Large A = U_k diag(s_1..s_k) V_k^T + noise * N(0,1), built with torch.
 
-    U_k, V_k: thin Q factors of seeded Gaussians (k = rank_cap columns).  The
-    factor product runs in FP32 (its rounding, ~1e-7 relative to |A|, sits far
-    below the noise term of the workloads that use this); the noise is drawn and
-    added in FP64 before the final cast to ``dtype``.
+    U_k, V_k: thin Q factors of seeded Gaussians (k = rank_cap columns).  By
+    default the factors and their product run in FP32 (rounding ~1e-7 per
+    operation, which accumulates to ~3e-5 of ||A|| over k = 4096 terms: far
+    below the noise term of the noisy workloads); factor_dtype=torch.float64
+    keeps the construction exact to FP64 for noise-free matrices whose small
+    tolerances must be reachable.  The noise is drawn and added in FP64 before
+    the final cast to ``dtype``.
     spectrum: "poly2" (i^-2), "exp200" (exp(-i/200)), "exp20" (exp(-i/20)),
               "poly1.5" (i^-1.5).
     """
@@ -94,13 +97,14 @@ def decay_matrix_torch(m: int, n: int, spectrum: str, seed: int, noise: float = 
         s = torch.exp(-i / 20.0)
     else:
         raise ValueError(spectrum)
-    U = torch.linalg.qr(torch.randn(m, k, device=device, generator=g, dtype=torch.float32))[0]
-    V = torch.linalg.qr(torch.randn(n, k, device=device, generator=g, dtype=torch.float32))[0]
+    fd = factor_dtype or torch.float32
+    U = torch.linalg.qr(torch.randn(m, k, device=device, generator=g, dtype=torch.float32).to(fd))[0]
+    V = torch.linalg.qr(torch.randn(n, k, device=device, generator=g, dtype=torch.float32).to(fd))[0]
     A = torch.empty(m, n, device=device, dtype=dtype)
     rows = max(1, (1 << 27) // max(n, 1))
     for r0 in range(0, m, rows):
         r1 = min(m, r0 + rows)
-        blk = ((U[r0:r1] * s.to(torch.float32)) @ V.T).to(torch.float64)
+        blk = ((U[r0:r1] * s.to(fd)) @ V.T).to(torch.float64)
         if noise > 0.0:
             blk += noise * torch.randn(r1 - r0, n, device=device, generator=g, dtype=torch.float64)
         A[r0:r1] = blk.to(dtype)
