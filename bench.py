@@ -32,7 +32,11 @@ sys.path.insert(0, ROOT)
 
 # dram bytes (read + write) of one sketch launch, from the committed ncu capture
 # summarised in profiles/; valid only while the kernel source is unchanged.
-TRAFFIC = {"sketch_simt.cu": {"sha1": None, "bytes_per_launch_full": None}}
+# profiles/sketch_f64_simt_8000x4000.md: 259.5 MB read + 65.8 MB written at 8000 x 4000
+# (split-K 50); at 20000^2 (split-K 12) reads scale with m*n (3244 MB) and the partial
+# writes with ks*c*n at the measured write ratio (79 MB).
+TRAFFIC = {"sketch_simt.cu": {"sha1": "7766d09d0424c94446f01a0e0d3665bda0fdd467",
+                              "bytes_per_launch_full": 3.323e9}}
 FP64_PEAK_TFLOPS = 1.25  # GB300 nominal FP64 rate (no FP64 entry in the measured peaks)
 HBM_GBS = 6685.5          # measured copy bandwidth of the GB300s (MEASURED_PEAKS.json)
 
@@ -62,12 +66,15 @@ def parse():
     p.add_argument("--paper-workload", action="store_true",
                    help="also time the Low-Rank matrix of Sec. 5.1 (30000^2 FP64, G1 G2^T of rank "
                         "2000, tol 1e-6, b = 250): the paper reports 12 s on a 48-core CPU")
-    p.add_argument("--workload", choices=["primary", "batch", "serve", "precision"],
+    p.add_argument("--workload", choices=["primary", "batch", "serve", "precision", "sketch"],
                    default="primary",
                    help="batch: 4096 independent FP32 matrices (m, n log-uniform in [64, 2048], "
                         "spectra exp(-i/20) / i^-1.5 / exact rank U[5,200]), tol 1e-4, b = c = 8, "
                         "all in one persistent launch; one step = the whole batch")
     p.add_argument("--batch-jobs", type=int, default=4096)
+    p.add_argument("--batch-uniform", type=int, default=0,
+                   help="every job N x N (with --batch-kind) instead of the mixed recipe")
+    p.add_argument("--batch-kind", choices=["exp20", "poly1.5", "rank"], default="poly1.5")
     p.add_argument("--serve-requests", type=int, default=300)
     p.add_argument("--serve-rate", type=float, default=200.0, help="Poisson arrival rate (1/s)")
     p.add_argument("--serve-min", type=int, default=512)
@@ -202,6 +209,21 @@ def oracle_sample(a, A_host_cols, frac_cols):
     return dt * 1000.0 * (a.n / A_host_cols.shape[1]), dt
 
 
+def adaptive_oracle_sample(a, A, target_s=12.0):
+    """Oracle on a column slab widened until one run takes about target_s
+    (the slab starts at n/64 and is rescaled from the measured time)."""
+    import numpy as np
+    import torch
+    ns = max(a.sketch + 1, a.n // 64)
+    while True:
+        slab = np.ascontiguousarray(A[:, :ns].to(torch.float64).cpu().numpy())
+        v, dt = oracle_sample(a, slab, ns)
+        if dt >= 0.5 * target_s or ns >= a.n // 2:
+            return v, dt, ns
+        grow = int(ns * min(8.0, target_s / max(dt, 1e-3)))
+        ns = min(a.n // 2, max(ns + 1, grow))
+
+
 def run_reference(a, ws, rank):
     if rank != 0:
         return 0
@@ -209,8 +231,8 @@ def run_reference(a, ws, rank):
     import torch
     dev = "cuda" if torch.cuda.is_available() else "cpu"
     dtype = torch.float64 if a.dtype == "f64" else torch.float32
-    ns = max(a.sketch + 1, a.n // 40)
     A = make_matrix(a, dev, dtype)
+    _, _, ns = adaptive_oracle_sample(a, A, target_s=8.0)
     slab = np.ascontiguousarray(A[:, :ns].to(torch.float64).cpu().numpy())
     del A
     for _ in range(a.warmup):
@@ -257,7 +279,18 @@ def batch_flops(m, n, r):
     return 2.0 * BATCH_C * m * n + (m + n) * r * r + (4.0 / 3.0 + 3.0) * r ** 3
 
 
+def batch_job_specs(a, seed):
+    from paper_2509_21963_gb300 import inputs
+    if a.batch_uniform:
+        return [dict(m=a.batch_uniform, n=a.batch_uniform, kind=a.batch_kind, r=100,
+                     seed=seed * 100003 + j) for j in range(a.batch_jobs)]
+    return inputs.batch_specs(a.batch_jobs, seed)
+
+
 def batch_workload_name(a):
+    if a.batch_uniform:
+        return (f"{a.batch_jobs} independent FP32 matrices of {a.batch_uniform} x {a.batch_uniform}, "
+                f"spectrum {a.batch_kind}, tol {BATCH_TOL:g}, b={BATCH_B}, c={BATCH_C}")
     return (f"{a.batch_jobs} independent FP32 matrices, m, n log-uniform in [64, 2048], spectra "
             f"exp(-i/20) / i^-1.5 / exact rank r~U[5,200] (one third each), tol {BATCH_TOL:g}, "
             f"b={BATCH_B}, c={BATCH_C}")
@@ -288,8 +321,7 @@ def batch_oracle_sample(specs, seconds, seed):
 def run_batch_reference(a, ws, rank):
     if rank != 0:
         return 0
-    from paper_2509_21963_gb300 import inputs
-    specs = inputs.batch_specs(a.batch_jobs, a.seed)
+    specs = batch_job_specs(a, a.seed)
     total = sum(batch_flops(s["m"], s["n"], batch_rank_model(s)) for s in specs)
     vals = []
     for k in range(a.warmup + a.steps):
@@ -322,7 +354,7 @@ def run_batch(a, ws, rank, local):
         dist.init_process_group("nccl")
     dev = f"cuda:{local}"
     log("batch: generating matrices")
-    specs = inputs.batch_specs(a.batch_jobs, a.seed + 1000 * rank)
+    specs = batch_job_specs(a, a.seed + 1000 * rank)
     mats = [inputs.batch_matrix_torch(s, device=dev) for s in specs]
     torch.cuda.synchronize()
     log("batch: matrices ready")
@@ -718,10 +750,16 @@ def run_precision(a, ws, rank, local):
             st, out = ctx.run_raw(A, tol, b, c, a.seed, **kw)
             e1.record(stream)
             torch.cuda.synchronize()
+            if st not in (cur.CUR_OK, cur.CUR_TOL_UNREACHED) or not out:
+                msg = ctx.last_error()
+                log(f"precision: tol {tol:g} mode {mode}: status {st}: {msg}")
+                forms.append({"tol": tol, "b": b, "c": c, "sketch_mode": mode, "status": int(st),
+                              "error": msg, "meets_tol": False})
+                continue
             res = cur._result_from(out)
             cur.lib().cur_result_free(out)
             err = true_rel_error(A, res.I, res.J, res.U) if res.rank else 1.0
-            sk = res.phase_ms["sketch"]
+            sk = max(res.phase_ms["sketch"], 1e-9)
             row = {"tol": tol, "b": b, "c": c,
                    "sketch": "FP64" if mode == 0 else f"tensor-core, {mode} digit(s)",
                    "time_to_tolerance_ms": e0.elapsed_time(e1), "rank": res.rank,
@@ -736,7 +774,7 @@ def run_precision(a, ws, rank, local):
             log(f"precision: tol {tol:g} mode {mode}: {row['time_to_tolerance_ms']:.1f} ms, "
                 f"rank {res.rank}, rho {res.rho:.2e}, true error {err:.2e}, status {st}")
     if rank == 0:
-        head = next(f for f in forms if f["tol"] == 1e-3 and f["sketch"].startswith("tensor-core, 2"))
+        head = next(f for f in forms if f["tol"] == 1e-3 and f.get("sketch", "").startswith("tensor-core, 2"))
         line = {"metric": "time-to-tolerance per CUR", "value": head["time_to_tolerance_ms"],
                 "unit": "ms", "n_gpus": ws, "steps": 1, "warmup": 1,
                 "ms_per_step": head["time_to_tolerance_ms"], "higher_is_better": False,
@@ -748,6 +786,49 @@ def run_precision(a, ws, rank, local):
                              "peak": HBM_GBS, "unit": "GB/s",
                              "frac": head["sketch_hbm_gbs_two_passes"] / HBM_GBS, "traffic": None,
                              "kernel": "sketch phase (column scales + tensor-core pass)"}}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# The sketch step alone (for kernel profiles)
+# ---------------------------------------------------------------------------
+def run_sketch_step(a, ws, rank, local):
+    """cur_step_sketch (FP64) or cur_step_sketch_q (digits) on a Gaussian A of
+    m x n, c = --sketch rows: W warm-up calls, then K timed calls."""
+    import torch
+    import paper_2509_21963_gb300 as cur
+    torch.cuda.set_device(local)
+    dtype = torch.float64 if a.dtype == "f64" else torch.float32
+    g = torch.Generator(device=f"cuda:{local}")
+    g.manual_seed(a.seed + 1)
+    A = torch.randn(a.m, a.n, device=f"cuda:{local}", generator=g, dtype=dtype)
+    ctx = cur.Context(local)
+    G = ctx.gaussian(a.seed, a.sketch, a.m)
+    call = (lambda: ctx.sketch(G, A)) if a.sketch_mode == 0 else \
+        (lambda: ctx.sketch_q(G, A, a.sketch_mode))
+    for _ in range(max(a.warmup, 3)):
+        call()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(a.steps):
+        call()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / a.steps
+    if rank == 0:
+        es = A.element_size()
+        line = {"metric": "sketch step time", "value": ms, "unit": "ms", "n_gpus": ws,
+                "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms,
+                "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+                "dtype": a.dtype if a.sketch_mode == 0 else f"bf16x{a.sketch_mode}",
+                "data": "synthetic",
+                "config": {"workload": f"sketch Y = G A, A {a.m}x{a.n} {a.dtype} Gaussian, c={a.sketch}"},
+                "one_pass_gbs": a.m * a.n * es / ms / 1e6,
+                "fp64_tflops": 2.0 * a.sketch * a.m * a.n / ms / 1e9}
         print(json.dumps(line), flush=True)
     ctx.close()
     return 0
@@ -765,6 +846,11 @@ def main():
         if a.impl == "reference":
             return run_batch_reference(a, ws, rank)
         return run_batch(a, ws, rank, local)
+    if a.workload == "sketch":
+        if a.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "kernel-profile mode only"}))
+            return 0
+        return run_sketch_step(a, ws, rank, local)
     if a.workload == "precision":
         if a.impl == "reference":
             print(json.dumps({"impl": "reference", "unavailable":
@@ -947,11 +1033,9 @@ def main():
 
     cpu = None
     if rank == 0 and ws == 1 and not a.no_cpu_baseline:
-        ns = max(a.sketch + 1, a.n // 20)
         log("cpu baseline: oracle on a column slab")
-        slab = np.ascontiguousarray(A[:, :ns].to(torch.float64).cpu().numpy())
-        v, dt = oracle_sample(a, slab, ns)
-        log(f"cpu baseline: {dt:.2f} s")
+        v, dt, ns = adaptive_oracle_sample(a, A)
+        log(f"cpu baseline: {dt:.2f} s on {ns} columns")
         cpu = {"value": v, "unit": "ms", "cores": 1, "kind": "oracle",
                "sample": f"one oracle run on the column slab A[:, :{ns}] ({dt:.1f} s), scaled by n/{ns}"}
 

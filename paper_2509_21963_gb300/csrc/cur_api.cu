@@ -70,12 +70,16 @@ int cur::ctx_fail_v(cur_ctx* ctx, int code, const char* msg) {
 
 namespace {
 
+// A failed call's error is also the runtime's pending error: clear it, so that
+// the next call on this context does not report it again.
 #define CK(expr)                                                                          \
   do {                                                                                    \
     cudaError_t e_ = (expr);                                                              \
-    if (e_ != cudaSuccess)                                                                \
+    if (e_ != cudaSuccess) {                                                              \
+      cudaGetLastError();                                                                 \
       return fail(ctx, CUR_ECUDA, "%s failed: %s (%d)", #expr, cudaGetErrorString(e_),    \
                   (int)e_);                                                               \
+    }                                                                                     \
   } while (0)
 
 #define TRY(expr)                   \

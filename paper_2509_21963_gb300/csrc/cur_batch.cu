@@ -58,9 +58,11 @@ int bfail(cur_ctx* ctx, int code, const char* fmt, ...) {
 #define BCK(expr)                                                                           \
   do {                                                                                      \
     cudaError_t e_ = (expr);                                                                \
-    if (e_ != cudaSuccess)                                                                  \
+    if (e_ != cudaSuccess) {                                                                \
+      cudaGetLastError();                                                                   \
       return bfail(ctx, CUR_ECUDA, "%s failed: %s (%d)", #expr, cudaGetErrorString(e_),     \
                    (int)e_);                                                                \
+    }                                                                                       \
   } while (0)
 
 size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }

@@ -252,7 +252,7 @@ cudaError_t launch_lupp(const LaunchEnv& env, const double* X, int64_t ldx, int6
   const int64_t per = (ncand + grid - 1) / grid;
   const size_t smem_res = sizeof(double) * ((size_t)nr * per + nr + per);
   if (smem_res <= kLuppSmemMax) {
-    if (smem_res > 48 * 1024) {
+    if (smem_res > 0) {  // static shared memory adds to it: always opt in
       e = cudaFuncSetAttribute((const void*)lupp_smem_kernel,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_res);
       if (e != cudaSuccess) return e;

@@ -605,7 +605,7 @@ cudaError_t launch_qrcp_pinv(const LaunchEnv& env, const double* M, int64_t p, i
   P.M = M; P.p = p; P.q = q; P.ldm = ldm; P.thr_mode = thr_mode; P.thr = thr;
   P.scale_dev = scale_dev; P.w = w; P.st = st;
   if (size_t ssm = qrcp_small_smem(p, q)) {
-    if (ssm > 48 * 1024) {
+    if (ssm > 0) {  // static shared memory adds to it: always opt in
       e = cudaFuncSetAttribute((const void*)qrcp_small_kernel,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm);
       if (e != cudaSuccess) return e;
@@ -615,7 +615,7 @@ cudaError_t launch_qrcp_pinv(const LaunchEnv& env, const double* M, int64_t p, i
   }
   const size_t csm = qrcp_coop_smem(p, q, grid);
   if (csm <= 200 * 1024) {
-    if (csm > 48 * 1024) {
+    if (csm > 0) {  // static shared memory adds to it: always opt in
       e = cudaFuncSetAttribute((const void*)qrcp_factor_smem_kernel,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm);
       if (e != cudaSuccess) return e;
@@ -626,7 +626,7 @@ cudaError_t launch_qrcp_pinv(const LaunchEnv& env, const double* M, int64_t p, i
                                     dim3(kThreads), args, csm, env.stream);
   } else {
     size_t smem = sizeof(double) * (size_t)p;
-    if (smem > 48 * 1024) {
+    if (smem > 0) {  // static shared memory adds to it: always opt in
       e = cudaFuncSetAttribute((const void*)qrcp_factor_kernel,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e != cudaSuccess) return e;
