@@ -51,7 +51,7 @@ def parse():
     p.add_argument("--n", type=int, default=20000)
     p.add_argument("--dtype", choices=["f64", "f32"], default="f64")
     p.add_argument("--sketch-mode", type=int, default=0,
-                   help="0 FP64 sketch; 1/2/3 tensor-core precision form with 1/2/3 digits (FP32 A)")
+                   help="0 FP64 sketch; 1-4 tensor-core precision form with 1-4 digits (FP32 A)")
     p.add_argument("--tol", type=float, default=1e-2)
     p.add_argument("--block", type=int, default=50)
     p.add_argument("--sketch", type=int, default=55)
@@ -695,14 +695,14 @@ PREC_M, PREC_N, PREC_RANK = 65536, 32768, 4096
 PREC_CASES = (  # (tol, b, c, sketch modes, rank cap); mode 0 = FP64 sketch, S = digits
     (1e-2, 100, 110, (0, 1), 2048),   # one digit: its sketch error (~0.1 here) bounds its reach
     (1e-3, 100, 110, (0, 2), 4096),
-    (1e-6, 72, 80, (0, 3), 6144),     # CUR needs ~1.4x the SVD rank on this spectrum
-)
+    (1e-6, 56, 62, (0, 3, 4), 6144),  # CUR needs ~1.4x the SVD rank on this spectrum;
+)                                     # c <= 64 for four digits
 
 
 def precision_workload_name():
     return (f"{PREC_M}x{PREC_N} FP32 A = U diag(exp(-i/200)) V^T (built in FP64, stored FP32), "
             f"U, V from QR of seeded Gaussian factors of rank {PREC_RANK}; tol 1e-2 and 1e-3 "
-            f"(b=100, c=110), 1e-6 (b=72, c=80); FP64 sketch vs tensor-core sketches with 1/2/3 "
+            f"(b=100, c=110), 1e-6 (b=56, c=62); FP64 sketch vs tensor-core sketches with 1/2/3/4 "
             f"base-256 digits")
 
 

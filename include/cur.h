@@ -53,14 +53,17 @@ typedef enum { CUR_F64 = 0, CUR_F32 = 1 } cur_dtype;
  * need an FP32 A with lda % 4 == 0 and a 16-byte aligned base; they use the
  * 8-bit sketch G_q = clamp(rint(16 G), -127, 127) and the S-digit fixed point
  * of each column (digits of 8 bits relative to a power-of-two column scale
- * 2^E_j > max |A(:,j)|), and compute Y = G_q fix_S(A) exactly:
+ * 2^E_j > max |A(:,j)|), and compute Y = G_q fix_S(A) exactly for S <= 3
+ * (for S = 4: the exact value rounded once to FP64):
  *   |fix_S(A)(k,j) - A(k,j)| <= 2^(E_j - 8S - 1).
- * c (rounded up to 16) must be <= 128, and <= 80 for S = 3. */
+ * c (rounded up to 16) must be <= 128, <= 80 for S = 3 and <= 64 for S = 4. */
 typedef enum {
   CUR_SKETCH_F64 = 0,   /* FP64 products and sums (the plain method)            */
   CUR_SKETCH_BF16 = 1,  /* S = 1: one BF16 digit per entry (2^-8 of column max)  */
   CUR_SKETCH_BF16X2 = 2,/* S = 2: hi + lo digits (2^-16)                         */
-  CUR_SKETCH_BF16X3 = 3 /* S = 3: hi + mid + lo digits (2^-24)                   */
+  CUR_SKETCH_BF16X3 = 3,/* S = 3: hi + mid + lo digits (2^-24)                   */
+  CUR_SKETCH_BF16X4 = 4 /* S = 4: four digits (2^-32; exact for FP32 entries
+                           within 2^-8 of their column's largest)               */
 } cur_sketch_mode;
 
 typedef struct cur_opts {

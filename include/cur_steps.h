@@ -36,7 +36,7 @@ int cur_step_sketch(cur_ctx *ctx, const double *G, int64_t c, const void *A,
 
 /* Precision form of the initial sketch on the tensor cores (see
  * cur_sketch_mode in cur.h): Y = G_q fix_S(A) exactly, with
- * G_q = clamp(rint(16 G), -127, 127) and S = digits in 1..3.
+ * G_q = clamp(rint(16 G), -127, 127) and S = digits in 1..4.
  *   G c x m FP64 (stride m); A m x n FP32 (stride lda, lda % 4 == 0, base
  *   16-byte aligned); Y c x n FP64; sumsq_host (may be NULL) receives ||Y||_F^2.
  *   Inf/NaN in a column of A turns that column of Y into NaN.

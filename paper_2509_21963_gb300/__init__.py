@@ -25,7 +25,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libcur.so")
 CUR_OK, CUR_EINVAL, CUR_ENONFINITE, CUR_ENOMEM, CUR_EBUDGET, CUR_ECUDA, CUR_ETIMEOUT, \
     CUR_TOL_UNREACHED = range(8)
 CUR_F64, CUR_F32 = 0, 1
-CUR_SKETCH_F64, CUR_SKETCH_BF16, CUR_SKETCH_BF16X2, CUR_SKETCH_BF16X3 = 0, 1, 2, 3
+CUR_SKETCH_F64, CUR_SKETCH_BF16, CUR_SKETCH_BF16X2, CUR_SKETCH_BF16X3, CUR_SKETCH_BF16X4 = 0, 1, 2, 3, 4
 PHASES = ("gaussian", "sketch", "lupp_col", "row_res", "lupp_row", "factors", "col_res", "core")
 
 _STATUS_NAMES = {0: "CUR_OK", 1: "CUR_EINVAL", 2: "CUR_ENONFINITE", 3: "CUR_ENOMEM",

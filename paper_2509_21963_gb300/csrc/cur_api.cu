@@ -263,12 +263,12 @@ int sketch_q(cur_ctx* ctx, int S, const double* G, int64_t c, const float* A, in
 }
 
 int check_precision_form(cur_ctx* ctx, int S, const void* A, int64_t lda, int dtype, int64_t c) {
-  if (S < 1 || S > 3) return fail(ctx, CUR_EINVAL, "unknown sketch_mode %d", S);
+  if (S < 1 || S > 4) return fail(ctx, CUR_EINVAL, "unknown sketch_mode %d", S);
   if (dtype != CUR_F32) return fail(ctx, CUR_EINVAL, "the precision forms of the sketch need FP32 A");
   if (lda % 4 != 0 || (reinterpret_cast<uintptr_t>(A) & 15) != 0)
     return fail(ctx, CUR_EINVAL, "the precision forms need lda %% 4 == 0 and a 16-byte aligned A");
   if (sketch_tc_cpad((int)c, S) < 0)
-    return fail(ctx, CUR_EINVAL, "sketch_size %lld too large for sketch_mode %d (c <= 128, <= 80 for S = 3)",
+    return fail(ctx, CUR_EINVAL, "sketch_size %lld too large for sketch_mode %d (c <= 128, <= 80 for S = 3, <= 64 for S = 4)",
                 (long long)c, S);
   return CUR_OK;
 }

@@ -84,7 +84,7 @@ cudaError_t launch_sketch_simt(const LaunchEnv& env, const SketchPlan& p, const 
 
 // ---- sketch_tc.cu ------------------------------------------------------------
 // Precision form of Y = G A on tcgen05 (BF16 digit slices, exact FP32/int64
-// accumulation): Y = G_q fix_S(A), G_q = clamp(rint(16 G), +-127), S in 1..3.
+// accumulation): Y = G_q fix_S(A), G_q = clamp(rint(16 G), +-127), S in 1..4.
 // A is FP32 with lda % 4 == 0 and a 16-byte aligned base.  Scratch layout is
 // owned by the launch (sketch_tc_scratch_bytes).  c_pad = sketch_tc_cpad(c, S)
 // must be > 0.  Writes *nparts sum-of-squares partials into sumsq_part.

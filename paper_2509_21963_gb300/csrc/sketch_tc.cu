@@ -14,9 +14,11 @@
 //     exact integer.
 //     Chunks are drained to int64 (exact) and combined over the K range; the
 //     FP64 result 2^(E_j-8S) sum_s 256^s D_s is exact as long as it fits 53
-//     bits (it does: < 2^47).
-// So Y = G_q fix_S(A) exactly; S = 1, 2, 3 are the "BF16", "hi+lo" and
-// "hi+mid+lo" forms, accurate to 2^-8S of each column's largest entry.
+//     bits (it does for S <= 3: < 2^47).
+// So Y = G_q fix_S(A) exactly for S = 1, 2, 3 (the "BF16", "hi+lo" and
+// "hi+mid+lo" forms, accurate to 2^-8S of each column's largest entry).  With
+// S = 4 the int64 sums are still exact but may exceed 2^53, so Y is the exact
+// value rounded once to FP64 (at most half an ulp).
 //
 // Kernel structure (one persistent CTA per SM, 10 warps):
 //   warp 0      TMA producer: A tile (64 rows x 128 columns FP32, no swizzle)
@@ -454,8 +456,8 @@ __global__ void colexp_kernel(const unsigned* __restrict__ colmax_bits, int64_t 
                                  : ldexp(1.0, E - 8 * S);
 }
 
-// Y[i, j] = 2^(E_j - 8S) acc[i][j] (exact: |acc| < 2^53 and the scale is a
-// power of two): one thread per column of a 256-column block and a group of
+// Y[i, j] = 2^(E_j - 8S) acc[i][j] (exact for S <= 3: |acc| < 2^53 and the
+// scale is a power of two; one rounding to FP64 for S = 4): one thread per column of a 256-column block and a group of
 // kReduceRows rows (blockIdx.y), plus per-CTA sums of squares.
 constexpr int kReduceRows = 16;
 
@@ -638,6 +640,7 @@ cudaError_t launch_sketch_tc(const LaunchEnv& env, int S, const double* G, int64
   CUR_TC_CASE(2, 80) CUR_TC_CASE(2, 96) CUR_TC_CASE(2, 112) CUR_TC_CASE(2, 128)
   CUR_TC_CASE(3, 16) CUR_TC_CASE(3, 32) CUR_TC_CASE(3, 48) CUR_TC_CASE(3, 64)
   CUR_TC_CASE(3, 80)
+  CUR_TC_CASE(4, 16) CUR_TC_CASE(4, 32) CUR_TC_CASE(4, 48) CUR_TC_CASE(4, 64)
   e = cudaErrorInvalidValue;
 #undef CUR_TC_CASE
   if (e != cudaSuccess) return e;
