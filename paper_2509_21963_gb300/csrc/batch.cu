@@ -257,15 +257,20 @@ __device__ bool team_qr_factor(const Team& tm, const QrWs& w, int64_t p, int64_t
 
   for (int64_t j = 0; j < kmax; ++j) {
     const double* slot = w.slots + (j & 1) * 2 * tm.T;
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32) {  // warp 0 reads the T candidates in parallel
       double bv = -1.0;
       int64_t bi = -1;
-      for (int r = 0; r < tm.T; ++r) {
+      for (int r = threadIdx.x; r < tm.T; r += 32) {
         double v = __ldcg(slot + 2 * r);
         int64_t i = (int64_t)__ldcg(slot + 2 * r + 1);
         if (better(v, i, bv, bi)) { bv = v; bi = i; }
       }
-      s_pc = bi;
+      for (int o = 16; o > 0; o >>= 1) {  // (value, index) max is order independent
+        double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        long long oi = __shfl_xor_sync(0xffffffffu, (long long)bi, o);
+        if (better(ov, oi, bv, bi)) { bv = ov; bi = oi; }
+      }
+      if (threadIdx.x == 0) s_pc = bi;
     }
     __syncthreads();
     const int64_t pc = s_pc;
@@ -752,6 +757,25 @@ __global__ void __launch_bounds__(256, 1) batch_kernel(BatchParams P) {
   }
 }
 
+// Whole-GPU core solve: U = A(I,J)^+ (or any p x q generalised inverse) by
+// one team made of the whole grid, for the single-matrix path's large cores.
+__global__ void __launch_bounds__(256, 1) core_qr_kernel(CoreQrParams P) {
+  Team tm;
+  tm.bar = P.bar;
+  tm.st = P.st;
+  tm.T = (int)gridDim.x;
+  tm.rank = (int)blockIdx.x;
+  tm.cluster = false;
+  double* vloc = P.vloc + (size_t)blockIdx.x * P.vloc_stride;
+  if (!team_qr_factor(tm, P.w, P.p, P.q, vloc)) return;
+  const int64_t k = qr_rank(P.w, P.p, P.q, P.thr, vloc);
+  if (P.p * kPanel * (int64_t)sizeof(double) <= (int64_t)P.panel_bytes)
+    team_qr_solve_panel(tm, P.w, P.p, P.q, k, P.X, P.ldx, dyn_smem(), vloc);
+  else
+    team_qr_solve(tm, P.w, P.p, P.q, k, P.X, P.ldx, vloc);
+  if (blockIdx.x == 0 && threadIdx.x == 0 && P.rank_out) *P.rank_out = k;
+}
+
 // Serving form: one thread-block cluster of T CTAs per job (blocks
 // [jid T, (jid + 1) T) along x), every job with its own workspace (team part,
 // T CTA parts), so launches of different waves can run concurrently.
@@ -880,6 +904,78 @@ cudaError_t launch_serve(const LaunchEnv& env, const BatchParams& P, int team, b
   cfg.numAttrs = 1;
   if (a_f32) return cudaLaunchKernelEx(&cfg, serve_kernel<float>, P);
   return cudaLaunchKernelEx(&cfg, serve_kernel<double>, P);
+}
+
+}  // namespace cur
+
+namespace cur {
+
+size_t core_qr_work_bytes(int64_t p, int64_t q, int T) {
+  const int64_t kmax = p < q ? p : q;
+  auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  size_t b = al(sizeof(double) * (size_t)(q * p));                       // Mc
+  b += al(sizeof(double) * (size_t)(kmax * p));                           // V
+  if (batch_panel_bytes(p) == 0) b += al(sizeof(double) * (size_t)(p * p));  // QT
+  b += 3 * al(sizeof(double) * (size_t)kmax) + al(8 * (size_t)kmax);      // tau, rdiag, perm
+  b += al((size_t)q) + al(sizeof(double) * (size_t)q);                   // used, norm2
+  b += al(sizeof(double) * 4 * (size_t)T);                                // slots
+  b += al(sizeof(double) * (size_t)(p > q ? p : q)) * (size_t)T;          // vloc per CTA
+  b += al(sizeof(GridBar)) + al(sizeof(long long));
+  return b;
+}
+
+int core_qr_grid(const LaunchEnv& env, int64_t p) {
+  const size_t panel = batch_panel_bytes(p);
+  if (cudaFuncSetAttribute(core_qr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)kBatchMaxPanelBytes) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, core_qr_kernel, 256, panel) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return per_sm >= 1 ? env.num_sms : 0;   // one CTA per SM
+}
+
+cudaError_t launch_core_qr(const LaunchEnv& env, double* Mc, int64_t p, int64_t q, double thr,
+                           double* X, int64_t ldx, void* work, int T, DevStatus* st,
+                           int64_t* rank_out) {
+  const int64_t kmax = p < q ? p : q;
+  auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  char* b = static_cast<char*>(work);
+  auto take = [&](size_t x) { char* r = b; b += al(x); return r; };
+  CoreQrParams P;
+  P.w.Mc = Mc;
+  (void)take(sizeof(double) * (size_t)(q * p));   // Mc lives at the start of the work area
+  P.w.V = reinterpret_cast<double*>(take(sizeof(double) * (size_t)(kmax * p)));
+  const size_t panel = batch_panel_bytes(p);
+  P.w.QT = panel ? nullptr : reinterpret_cast<double*>(take(sizeof(double) * (size_t)(p * p)));
+  P.w.tau = reinterpret_cast<double*>(take(sizeof(double) * (size_t)kmax));
+  P.w.rdiag = reinterpret_cast<double*>(take(sizeof(double) * (size_t)kmax));
+  (void)take(sizeof(double) * (size_t)kmax);
+  P.w.perm = reinterpret_cast<int64_t*>(take(8 * (size_t)kmax));
+  P.w.used = reinterpret_cast<uint8_t*>(take((size_t)q));
+  P.w.norm2 = reinterpret_cast<double*>(take(sizeof(double) * (size_t)q));
+  P.w.slots = reinterpret_cast<double*>(take(sizeof(double) * 4 * (size_t)T));
+  P.vloc_stride = al(sizeof(double) * (size_t)(p > q ? p : q)) / sizeof(double);
+  P.vloc = reinterpret_cast<double*>(take(sizeof(double) * P.vloc_stride * (size_t)T));
+  P.bar = reinterpret_cast<GridBar*>(take(sizeof(GridBar)));
+  P.p = p;
+  P.q = q;
+  P.thr = thr;
+  P.X = X;
+  P.ldx = ldx;
+  P.st = st;
+  P.panel_bytes = panel;
+  P.rank_out = rank_out;
+  cudaError_t e = cudaMemsetAsync(P.bar, 0, sizeof(GridBar), env.stream);
+  if (e != cudaSuccess) return e;
+  void* args[] = {&P};
+  return cudaLaunchCooperativeKernel((const void*)core_qr_kernel, dim3(T), dim3(256), args, panel,
+                                     env.stream);
 }
 
 }  // namespace cur

@@ -199,6 +199,30 @@ int batch_max_ctas(const LaunchEnv& env, int threads, bool a_f32, size_t dyn_sme
 // Panel bytes of the core solve for cores up to rmax (0 when it does not fit).
 size_t batch_panel_bytes(int64_t rmax);
 
+// Whole-GPU pivoted-QR generalised inverse (the team QR of the batch kernel
+// with one team made of every SM), X = P [R11^{-1} Q1^T; 0] (q x p, row stride
+// ldx) of the p x q matrix Mc (column-major, overwritten; Mc must be the start
+// of `work`, which holds core_qr_work_bytes(p, q, T) bytes).  thr < 0: rank
+// threshold max(p,q) 2^-52 |R_00|.  core_qr_grid returns T (0: not runnable).
+struct CoreQrParams {
+  QrWs w;
+  double* vloc;
+  size_t vloc_stride;
+  GridBar* bar;
+  DevStatus* st;
+  int64_t p, q;
+  double thr;
+  double* X;
+  int64_t ldx;
+  size_t panel_bytes;
+  int64_t* rank_out;
+};
+size_t core_qr_work_bytes(int64_t p, int64_t q, int T);
+int core_qr_grid(const LaunchEnv& env, int64_t p);
+cudaError_t launch_core_qr(const LaunchEnv& env, double* Mc, int64_t p, int64_t q, double thr,
+                           double* X, int64_t ldx, void* work, int T, DevStatus* st,
+                           int64_t* rank_out);
+
 // Serving form (one cluster of `team` CTAs per job, per-job workspaces).
 size_t serve_job_scratch_bytes(const BatchDims& d, int team);
 int serve_max_clusters(const LaunchEnv& env, int team, bool a_f32, size_t panel);

@@ -26,6 +26,7 @@
 #include "../../include/cur_steps.h"
 #include "cur_internal.cuh"
 #include "ctx.cuh"
+#include "batch.cuh"
 
 using namespace cur;
 
@@ -208,6 +209,29 @@ int gather(cur_ctx* ctx, const void* X, bool f32, int64_t ldx, bool trans, const
   CK(launch_gather2d(env_of(ctx), X, f32, ldx, trans, ridx, cidx, rows, cols, rlim, clim, out, ldo));
   ctx->launches += 1;
   return CUR_OK;
+}
+
+// Cores of at least this rank are factored by the whole-GPU team QR
+// (batch.cu), smaller ones by the single-CTA or cooperative kernels of qrcp.cu.
+constexpr int64_t kTeamCoreMin = 1024;
+
+// Line 12: U = A(I,J)^+ (r x r), relative rank threshold max(p,q) 2^-52 |R_00|.
+// Mc: an r x r scratch for the small-core path.
+int core_solve(cur_ctx* ctx, const void* A, bool f32, int64_t lda, int64_t m, int64_t n,
+               const int64_t* I, const int64_t* J, int64_t r, double* Mc, double* U) {
+  LaunchEnv env = env_of(ctx);
+  const int T = r >= kTeamCoreMin ? core_qr_grid(env, r) : 0;
+  if (T > 0) {
+    TRY(ensure(ctx, B_TEAMCORE, core_qr_work_bytes(r, r, T)));
+    double* W = bp<double>(ctx, B_TEAMCORE);
+    // column-major A(I,J): W[col * r + i] = A(I[i], J[col])
+    TRY(gather(ctx, A, f32, lda, true, J, I, r, r, n, m, W, r));
+    CK(launch_core_qr(env, W, r, r, -1.0, U, r, W, T, dstat(ctx), nullptr));
+    ctx->launches += 1;
+    return CUR_OK;
+  }
+  TRY(gather(ctx, A, f32, lda, false, I, J, r, r, m, n, Mc, r));
+  return pinv_call(ctx, B_QRBIG, Mc, r, r, r, 0, 0.0, nullptr, U, r);
 }
 
 int sum_parts(cur_ctx* ctx, const double* parts, int64_t n, double* out) {
@@ -497,11 +521,7 @@ int run_device(cur_ctx* ctx, const void* A, int64_t m, int64_t n, int64_t lda, i
     if ((st = ensure(ctx, B_CORE, sizeof(double) * (size_t)(r * r))) != CUR_OK) { cur_result_free(res); return st; }
     double* Mc = bp<double>(ctx, B_CORE);
     tick(ctx, CUR_PHASE_CORE);
-    if ((st = gather(ctx, A, f32, lda, false, res->I, res->J, r, r, m, n, Mc, r)) != CUR_OK) {
-      cur_result_free(res);
-      return st;
-    }
-    if ((st = pinv_call(ctx, B_QRBIG, Mc, r, r, r, 0, 0.0, nullptr, res->U, r)) != CUR_OK) {
+    if ((st = core_solve(ctx, A, f32, lda, m, n, res->I, res->J, r, Mc, res->U)) != CUR_OK) {
       cur_result_free(res);
       return st;
     }
