@@ -73,7 +73,7 @@ int cur_step_pinv(cur_ctx *ctx, const double *M, int64_t p, int64_t q,
  * and stay caller-owned.
  *   Scratch: a fixed 16 MiB device array inside the library (held by every GPU
  *   that loads the library until the process exits) that must hold
- *   nr * ncand + 2 * G * (nr + 2) doubles plus 256 bytes, G <= the SM count
+ *   nr * ncand + 2 * G * max(nr + 2, 34) doubles plus 256 bytes, G <= the SM count
  *   (e.g. 55 x 20000 fits); larger problems and nr > 6144 return CUR_EINVAL
  *   with a message in err.  The call allocates nothing (no cudaMalloc,
  *   cudaFree or allocating library routine).

@@ -175,7 +175,7 @@ int lupp_call(cur_ctx* ctx, BufId wid, const double* X, int64_t ldx, int64_t nr,
   LuppWork w;
   w.W = bp<double>(ctx, wid);
   w.slot_val = w.W + (size_t)nr * ncand;
-  w.bar = reinterpret_cast<GridBar*>(w.slot_val + 2 * (size_t)grid * (nr + 2));
+  w.bar = reinterpret_cast<GridBar*>(w.slot_val + 2 * (size_t)grid * (size_t)lupp_slot_stride(nr));
   w.max_grid = grid;
   CK(launch_lupp(env, X, ldx, nr, ncand, steps, mask, piv, w, grid, dstat(ctx)));
   ctx->launches += 1;

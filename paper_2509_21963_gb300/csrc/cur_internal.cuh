@@ -108,11 +108,19 @@ cudaError_t launch_gather2d(const LaunchEnv& env, const void* X, bool x_is_f32, 
 // ---- lupp.cu --------------------------------------------------------------
 struct LuppWork {
   double* W;          // nr * ncand working copy
-  double* slot_val;   // 2 * max_grid * (nr + 2)
+  double* slot_val;   // 2 * max_grid * lupp_slot_stride(nr)
   GridBar* bar;
   int max_grid;
 };
 size_t lupp_work_doubles(int64_t nr, int64_t ncand, int max_grid);
+// Feature panel of the blocked selector; doubles per CTA and step parity in
+// LuppWork::slot_val (2 * max_grid of them): the unblocked record (|value|,
+// index, nr column values) or the blocked one (|value|, index, panel column,
+// multipliers).
+constexpr int kLuppPanel = 16;
+__host__ __device__ inline int64_t lupp_slot_stride(int64_t nr) {
+  return nr + 2 > 2 + 2 * kLuppPanel ? nr + 2 : 2 + 2 * kLuppPanel;
+}
 int lupp_grid(const LaunchEnv& env, int64_t nr, int64_t ncand);
 cudaError_t launch_lupp(const LaunchEnv& env, const double* X, int64_t ldx, int64_t nr,
                         int64_t ncand, int64_t steps, uint8_t* mask, int64_t* piv,

@@ -43,7 +43,7 @@ struct LuppParams {
   const double* X; int64_t ldx; int nr; int64_t ncand; int steps;
   uint8_t* mask; int64_t* piv;
   double* W;
-  double* slots;  // [2][grid][nr + 2]: abs, index bits, column values
+  double* slots;  // [2][grid][stride]: abs, index bits, column values (stride: lupp_slot_stride)
   GridBar* bar; DevStatus* st;
 };
 
@@ -57,7 +57,7 @@ __global__ void __launch_bounds__(kThreads) lupp_kernel(LuppParams p) {
   const int64_t per = (p.ncand + G - 1) / G;
   const int64_t lo = (int64_t)cta * per, hi = min(p.ncand, lo + per);
   const int64_t ldw = p.ncand;
-  const int stride = p.nr + 2;
+  const int stride = (int)lupp_slot_stride(p.nr);
 
   for (int rr = 0; rr < p.nr; ++rr)
     for (int64_t i = lo + tid; i < hi; i += kThreads) p.W[rr * ldw + i] = p.X[rr * p.ldx + i];
@@ -132,6 +132,158 @@ __global__ void __launch_bounds__(kThreads) lupp_kernel(LuppParams p) {
   }
 }
 
+// Blocked form of lupp_kernel for slices too large for shared memory: the
+// features are taken in panels of KB rows.  Within a panel each CTA keeps its
+// candidates' panel rows (Pn) and their multipliers (Lm) in shared memory and
+// runs the steps there (one grid barrier per step, as above); the features
+// below the panel are updated once per panel: the pivot candidates' trailing
+// values follow by forward substitution, prow_s = W(:,p_s) - sum_{s'<s}
+// l_{s',p_s} prow_{s'}, and every eligible candidate i then takes
+// W(u,i) -= sum_s l_{s,i} prow_s(u).  Same pivots and arithmetic as the
+// unblocked kernel up to the order of the trailing sums; W makes one L2 round
+// trip per panel instead of one per step.
+// Shared memory: Pn, Lm [KB][per]; prow [KB][nr]; pv [KB]; PL [KB][KB].
+constexpr int kLuppKB = kLuppPanel;
+
+__global__ void __launch_bounds__(kThreads) lupp_blocked_kernel(LuppParams p, int per, int KB) {
+  extern __shared__ double sh[];
+  double* Pn = sh;                                   // KB * per
+  double* Lm = Pn + (size_t)KB * per;                // KB * per
+  double* prow = Lm + (size_t)KB * per;              // KB * nr
+  double* pv = prow + (size_t)KB * p.nr;             // KB
+  double* PL = pv + KB;                              // KB * KB: PL[s * KB + s'] = l_{s', p_s}
+  __shared__ Best red[kThreads / 32];
+  __shared__ Best s_win;
+  __shared__ int s_wcta;
+  __shared__ long long s_piv[kLuppKB];
+  const int G = gridDim.x, cta = blockIdx.x, tid = threadIdx.x;
+  const int lane = tid & 31, wid = tid >> 5;
+  const int64_t lo = (int64_t)cta * per, hi = min(p.ncand, lo + per);
+  const int own = (int)max((int64_t)0, hi - lo);
+  const int64_t ldw = p.ncand;
+  const int stride = (int)lupp_slot_stride(p.nr);  // >= 2 + 2 KB: abs, index, panel column, multipliers
+
+  for (int rr = 0; rr < p.nr; ++rr)
+    for (int64_t i = lo + tid; i < hi; i += kThreads) p.W[rr * ldw + i] = p.X[rr * p.ldx + i];
+  __syncthreads();
+
+  for (int t0 = 0; t0 < p.steps; t0 += KB) {
+    const int nb = min(KB, p.nr - t0);          // rows of this panel
+    const int ns = min(KB, p.steps - t0);       // steps of this panel
+    for (int e = tid; e < nb * own; e += kThreads) {
+      const int u = e / own, li = e - u * own;
+      Pn[u * per + li] = p.W[(int64_t)(t0 + u) * ldw + lo + li];
+      Lm[u * per + li] = 0.0;
+    }
+    __syncthreads();
+    for (int s = 0; s < ns; ++s) {
+      const int t = t0 + s;
+      double* slot = p.slots + ((size_t)(t & 1) * G) * stride;
+      Best b{-1.0, LLONG_MAX};
+      for (int li = tid; li < own; li += kThreads) {
+        if (p.mask[lo + li]) continue;
+        const double a = fabs(Pn[s * per + li]);
+        if (better(a, lo + li, b)) { b.a = a; b.i = lo + li; }
+      }
+      b = warp_best(b);
+      if (lane == 0) red[wid] = b;
+      __syncthreads();
+      if (wid == 0) {
+        Best c = lane < kThreads / 32 ? red[lane] : Best{-1.0, LLONG_MAX};
+        c = warp_best(c);
+        if (lane == 0) s_win = c;
+      }
+      __syncthreads();
+      const Best mine = s_win;
+      double* my = slot + (size_t)cta * stride;
+      if (tid == 0) { my[0] = mine.a; my[1] = __longlong_as_double(mine.i); }
+      if (mine.i != LLONG_MAX) {
+        const int lw = (int)(mine.i - lo);
+        for (int u = s + tid; u < nb; u += kThreads) my[2 + u] = Pn[u * per + lw];
+        for (int q = tid; q < s; q += kThreads) my[2 + KB + q] = Lm[q * per + lw];
+      }
+      __threadfence();
+      if (!grid_barrier(p.bar, p.st)) return;
+      if (wid == 0) {
+        Best c{-1.0, LLONG_MAX};
+        int ccta = -1;
+        for (int g = lane; g < G; g += 32) {
+          const double* sg = slot + (size_t)g * stride;
+          const double a = __ldcg(sg);
+          const long long i = __double_as_longlong(__ldcg(sg + 1));
+          if (better(a, i, c)) { c.a = a; c.i = i; ccta = g; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          double oa = __shfl_down_sync(0xffffffffu, c.a, o);
+          long long oi = __shfl_down_sync(0xffffffffu, c.i, o);
+          int oc = __shfl_down_sync(0xffffffffu, ccta, o);
+          if (better(oa, oi, c)) { c.a = oa; c.i = oi; ccta = oc; }
+        }
+        if (lane == 0) { s_win = c; s_wcta = ccta; }
+      }
+      __syncthreads();
+      const Best w = s_win;
+      if (w.i == LLONG_MAX) {
+        if (tid == 0) dev_set_err(p.st, kDevNoCandidate);
+        return;
+      }
+      const double* wsl = slot + (size_t)s_wcta * stride;
+      for (int u = s + tid; u < nb; u += kThreads) pv[u] = __ldcg(wsl + 2 + u);
+      for (int q = tid; q < KB; q += kThreads) PL[s * KB + q] = q < s ? __ldcg(wsl + 2 + KB + q) : 0.0;
+      if (tid == 0) {
+        s_piv[s] = w.i;
+        if (cta == 0) p.piv[t] = w.i;
+        if (w.i >= lo && w.i < hi) p.mask[w.i] = 1;
+      }
+      __syncthreads();
+      if (w.a > 0.0) {
+        const double rp = 1.0 / pv[s];
+        for (int li = tid; li < own; li += kThreads) {
+          if (p.mask[lo + li]) continue;
+          const double l = Pn[s * per + li] * rp;
+          Lm[s * per + li] = l;
+          for (int u = s + 1; u < nb; ++u) Pn[u * per + li] = fma(-l, pv[u], Pn[u * per + li]);
+        }
+      }
+      __syncthreads();
+    }
+    // write the panel rows back (later panels and the caller see W)
+    for (int e = tid; e < nb * own; e += kThreads) {
+      const int u = e / own, li = e - u * own;
+      p.W[(int64_t)(t0 + u) * ldw + lo + li] = Pn[u * per + li];
+    }
+    const int r0 = t0 + nb;  // first trailing feature
+    if (r0 < p.nr && t0 + ns < p.steps) {
+      // pivot rows' trailing values: prow_s = W(:, p_s) - sum_{s' < s} l_{s', p_s} prow_{s'}
+      for (int u = r0 + tid; u < p.nr; u += kThreads) {
+        for (int s = 0; s < ns; ++s) {
+          double v = __ldcg(p.W + (int64_t)u * ldw + s_piv[s]);
+          for (int q = 0; q < s; ++q) v = fma(-PL[s * KB + q], prow[q * p.nr + u], v);
+          prow[s * p.nr + u] = v;
+        }
+      }
+      __syncthreads();
+      // rank-ns update of the owned eligible candidates' trailing features
+      for (int li = tid; li < own; li += kThreads) {
+        if (p.mask[lo + li]) continue;
+        double l[kLuppKB];
+#pragma unroll
+        for (int s = 0; s < kLuppKB; ++s) l[s] = s < ns ? Lm[s * per + li] : 0.0;
+        for (int u = r0; u < p.nr; ++u) {
+          double* wp = p.W + (int64_t)u * ldw + lo + li;
+          double acc = *wp;
+#pragma unroll
+          for (int s = 0; s < kLuppKB; ++s)
+            if (s < ns) acc = fma(-l[s], prow[s * p.nr + u], acc);
+          *wp = acc;
+        }
+      }
+    }
+    __threadfence();
+    __syncthreads();
+  }
+}
+
 // Same selection with each CTA's candidate slice resident in shared memory:
 // Wsh[rr * per + li] for candidate lo + li.  Used whenever the slice fits.
 // The elimination of a step is spread over (row, candidate) pairs so that all
@@ -148,7 +300,7 @@ __global__ void __launch_bounds__(kThreads) lupp_smem_kernel(LuppParams p, int p
   const int lane = tid & 31, wid = tid >> 5;
   const int64_t lo = (int64_t)cta * per;
   const int own = (int)max((int64_t)0, min((int64_t)per, p.ncand - lo));
-  const int stride = p.nr + 2;
+  const int stride = (int)lupp_slot_stride(p.nr);
 
   for (int e = tid; e < p.nr * own; e += kThreads) {
     int rr = e / own, li = e - rr * own;
@@ -226,7 +378,7 @@ __global__ void __launch_bounds__(kThreads) lupp_smem_kernel(LuppParams p, int p
 }  // namespace
 
 size_t lupp_work_doubles(int64_t nr, int64_t ncand, int max_grid) {
-  return (size_t)nr * ncand + 2 * (size_t)max_grid * (nr + 2);
+  return (size_t)nr * ncand + 2 * (size_t)max_grid * (size_t)lupp_slot_stride(nr);
 }
 
 // Largest dynamic shared memory the resident-slice variant may use per CTA.
@@ -262,8 +414,23 @@ cudaError_t launch_lupp(const LaunchEnv& env, const double* X, int64_t ldx, int6
     return cudaLaunchCooperativeKernel((const void*)lupp_smem_kernel, dim3(grid), dim3(kThreads),
                                        args, smem_res, env.stream);
   }
+  const int KB = kLuppKB;
+  const size_t smem_blk =
+      sizeof(double) * ((size_t)2 * KB * per + (size_t)KB * nr + KB + (size_t)KB * KB);
+  if (smem_blk <= kLuppSmemMax) {
+    e = cudaFuncSetAttribute((const void*)lupp_blocked_kernel,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_blk);
+    if (e != cudaSuccess) return e;
+    int per_i = (int)per, kb = KB;
+    void* args[] = {&p, &per_i, &kb};
+    return cudaLaunchCooperativeKernel((const void*)lupp_blocked_kernel, dim3(grid),
+                                       dim3(kThreads), args, smem_blk, env.stream);
+  }
   void* args[] = {&p};
   size_t smem = sizeof(double) * (size_t)(nr > 0 ? nr : 1);
+  e = cudaFuncSetAttribute((const void*)lupp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem);
+  if (e != cudaSuccess) return e;
   return cudaLaunchCooperativeKernel((const void*)lupp_kernel, dim3(grid), dim3(kThreads), args,
                                      smem, env.stream);
 }

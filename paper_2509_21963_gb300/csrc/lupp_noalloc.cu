@@ -18,7 +18,7 @@
 #include "cur_internal.cuh"
 
 // Scratch capacity: 16 MiB.  It holds nr * ncand doubles of working copy plus
-// 2 * grid * (nr + 2) doubles of slots, e.g. 55 x 20000 or 50 x 20000.
+// 2 * grid * lupp_slot_stride(nr) doubles of slots, e.g. 55 x 20000 or 50 x 20000.
 constexpr size_t kNoAllocBytes = 16u << 20;
 
 // The scratch itself: shared by every call on a device, keeps the last call's
@@ -77,7 +77,8 @@ extern "C" int cur_step_lupp_noalloc(int device, void* cuda_stream, const double
     return CUR_ECUDA;
   }
   const int grid = lupp_grid(env, nr, ncand);
-  const size_t slot_bytes = round_up(sizeof(double) * 2 * (size_t)grid * (size_t)(nr + 2));
+  const size_t slot_bytes =
+      round_up(sizeof(double) * 2 * (size_t)grid * (size_t)lupp_slot_stride(nr));
   const size_t w_bytes = round_up(sizeof(double) * (size_t)nr * (size_t)ncand);
   if (kHeaderBytes + slot_bytes + w_bytes > kNoAllocBytes) {
     char msg[256];

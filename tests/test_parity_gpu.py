@@ -93,7 +93,12 @@ def test_sketch_strided_unaligned(ctx):
 
 
 @pytest.mark.parametrize("nr,ncand,steps", [(30, 800, 10), (55, 20000, 50), (7, 1001, 7),
-                                            (50, 20000, 50), (12, 40, 12)])
+                                            (50, 20000, 50), (12, 40, 12),
+                                            # slices too large for shared memory: the
+                                            # blocked selector (16-feature panels) ...
+                                            (120, 40000, 110), (275, 30000, 250),
+                                            # ... and the unblocked global one
+                                            (20, 300000, 20)])
 def test_lupp_pivots_exact(ctx, nr, ncand, steps):
     rng = np.random.default_rng(nr * ncand)
     X = rng.standard_normal((nr, ncand))
