@@ -311,21 +311,52 @@ __device__ bool team_qr_factor(const Team& tm, const QrWs& w, int64_t p, int64_t
       if (w.used[col]) continue;
       double* x = w.Mc + col * p;
       double f = 0.0;
+      // four independent L2 loads in flight per lane (the loops are latency bound)
       if (tau != 0.0) {
-        double d = 0.0;
-        for (int64_t i = j + lane; i < p; i += 32) d += vloc[i] * __ldcg(x + i);
+        double d0 = 0.0, d1 = 0.0, d2 = 0.0, d3 = 0.0;
+        int64_t i = j + lane;
+        for (; i + 96 < p; i += 128) {
+          const double a0 = __ldcg(x + i), a1 = __ldcg(x + i + 32), a2 = __ldcg(x + i + 64),
+                       a3 = __ldcg(x + i + 96);
+          d0 += vloc[i] * a0;
+          d1 += vloc[i + 32] * a1;
+          d2 += vloc[i + 64] * a2;
+          d3 += vloc[i + 96] * a3;
+        }
+        for (; i < p; i += 32) d0 += vloc[i] * __ldcg(x + i);
+        double d = (d0 + d1) + (d2 + d3);
         for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
         f = tau * d;
       }
-      double s = 0.0;
-      for (int64_t i = j + lane; i < p; i += 32) {
+      double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+      int64_t i = j + lane;
+      for (; i + 96 < p; i += 128) {
+        double y0 = __ldcg(x + i), y1 = __ldcg(x + i + 32), y2 = __ldcg(x + i + 64),
+               y3 = __ldcg(x + i + 96);
+        if (tau != 0.0) {
+          y0 = y0 - f * vloc[i];
+          y1 = y1 - f * vloc[i + 32];
+          y2 = y2 - f * vloc[i + 64];
+          y3 = y3 - f * vloc[i + 96];
+          x[i] = y0;
+          x[i + 32] = y1;
+          x[i + 64] = y2;
+          x[i + 96] = y3;
+        }
+        s0 += (i > j) ? y0 * y0 : 0.0;  // only the row i = j (lane 0, first block) is excluded
+        s1 += y1 * y1;
+        s2 += y2 * y2;
+        s3 += y3 * y3;
+      }
+      for (; i < p; i += 32) {
         double y = __ldcg(x + i);
         if (tau != 0.0) {
           y = y - f * vloc[i];
           x[i] = y;
         }
-        if (i > j) s += y * y;
+        if (i > j) s0 += y * y;
       }
+      double s = (s0 + s1) + (s2 + s3);
       for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
       if (lane == 0) w.norm2[col] = s;
     }
@@ -393,6 +424,9 @@ __device__ void team_qr_solve(const Team& tm, const QrWs& w, int64_t p, int64_t 
 // block barriers; the back substitution runs column-oriented (R's column
 // perm[i] is contiguous in Mc) with one block barrier per row.
 constexpr int kPanel = 8;
+constexpr int kPanelRows = 10;  // rows per thread (256 threads): cores up to 2560
+static_assert((size_t)kPanelRows * 256 * kPanel * sizeof(double) >= kBatchMaxPanelBytes,
+              "every core that fits the panel has at most kPanelRows rows per thread");
 
 __device__ void team_qr_solve_panel(const Team& tm, const QrWs& w, int64_t p, int64_t q, int64_t k,
                                     double* X, int64_t ldx, double* Zs, const double* rinv) {
@@ -422,13 +456,22 @@ __device__ void team_qr_solve_panel(const Team& tm, const QrWs& w, int64_t p, in
       for (int c = 0; c < kPanel; ++c) acc[c] = 0.0;
       // rows stay with thread i % NT for every reflector, so each row of the
       // panel is only ever touched by one thread (no barrier between the
-      // update of H_jj and the dot of H_jj+1)
+      // update of H_jj and the dot of H_jj+1); the reflector's entries of this
+      // thread's rows are loaded once (all in flight together) and reused by
+      // the update
       const int64_t i0 = (jj / NT) * NT + tid;
-      for (int64_t i = i0; i < p; i += NT) {
-        if (i < jj) continue;
-        const double vi = __ldcg(v + i);
+      double vr[kPanelRows];
 #pragma unroll
-        for (int c = 0; c < kPanel; ++c) acc[c] += vi * Zs[c * p + i];
+      for (int q = 0; q < kPanelRows; ++q) {
+        const int64_t i = i0 + (int64_t)q * NT;
+        vr[q] = (i >= jj && i < p) ? __ldcg(v + i) : 0.0;
+      }
+#pragma unroll
+      for (int q = 0; q < kPanelRows; ++q) {
+        const int64_t i = i0 + (int64_t)q * NT;
+        if (i < jj || i >= p) continue;
+#pragma unroll
+        for (int c = 0; c < kPanel; ++c) acc[c] += vr[q] * Zs[c * p + i];
       }
 #pragma unroll
       for (int c = 0; c < kPanel; ++c)
@@ -443,11 +486,12 @@ __device__ void team_qr_solve_panel(const Team& tm, const QrWs& w, int64_t p, in
         s_d[tid] = t * sum;
       }
       __syncthreads();
-      for (int64_t i = i0; i < p; i += NT) {
-        if (i < jj) continue;
-        const double vi = __ldcg(v + i);
 #pragma unroll
-        for (int c = 0; c < kPanel; ++c) Zs[c * p + i] -= s_d[c] * vi;
+      for (int q = 0; q < kPanelRows; ++q) {
+        const int64_t i = i0 + (int64_t)q * NT;
+        if (i < jj || i >= p) continue;
+#pragma unroll
+        for (int c = 0; c < kPanel; ++c) Zs[c * p + i] -= s_d[c] * vr[q];
       }
     }
     for (int64_t i = k - 1; i >= 0; --i) {

@@ -211,6 +211,8 @@ constexpr int64_t kReducePerCta = 8192;
 
 }  // namespace
 
+// The one-thread-per-column kernel for up to 256 output rows (b = 50 and
+// b = 250 both measured faster than the 64 x 64 tiles on GB300).
 static bool use_skinny(const GemmArgs& g) {
   return !g.transB && !g.b_is_f32 && g.ksplit <= 1 && g.M <= 256;
 }
