@@ -126,7 +126,11 @@ int cur_run_opts(cur_ctx *ctx, const void *A, int64_t m, int64_t n,
 
 /* End-to-end form: A is a HOST buffer (m x n, stride lda).  The call copies A
  * to the device (a context-owned buffer, grown as needed), runs, and copies
- * I, J, U and rho back into the result's host mirrors before returning. */
+ * I, J, U and rho back into the result's host mirrors before returning.  With
+ * the FP64 sketch the copy goes in row blocks on a second stream and the
+ * sketch of each block starts when its copy lands (the copy overlaps the
+ * sketch); the precision forms copy A whole first.  A_host is read until the
+ * call returns (pinned memory makes the copies asynchronous). */
 int cur_run_host(cur_ctx *ctx, const void *A_host, int64_t m, int64_t n,
                  int64_t lda, int dtype, double tol, int block_size,
                  int sketch_size, uint64_t seed, const cur_opts *opts,

@@ -34,6 +34,9 @@ struct cur_ctx {
   std::vector<int> ev_phase;      // phase that starts at event i (-1: none)
   bool timing = false;
   int64_t launches = 0;           // kernel launches of the current run
+  // host-input runs: a copy stream and per-row-block events (created on demand)
+  cudaStream_t copy_stream = nullptr;
+  std::vector<cudaEvent_t> copy_ev;
 };
 
 namespace cur {

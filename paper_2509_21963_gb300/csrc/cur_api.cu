@@ -269,6 +269,63 @@ int sketch_f64(cur_ctx* ctx, const double* G, int64_t c, const void* A, bool a_f
   return CUR_OK;
 }
 
+// Y = G A with A arriving from host memory: A is copied to A_dev in row blocks
+// on the context's copy stream, and the sketch of each block starts as soon
+// as its copy lands, so the copy of block k+1 overlaps the sketch of block k;
+// the blocks' split-K slices are summed in one fixed-order reduction.
+int sketch_f64_from_host(cur_ctx* ctx, const double* G, int64_t c, const void* A_host,
+                         int64_t lda_host, void* A_dev, bool a_f32, int64_t m, int64_t n,
+                         double* Y, int slot, BufId parts_id) {
+  LaunchEnv env = env_of(ctx);
+  const int nb = m >= 8192 ? 8 : (m >= 2048 ? 4 : 1);
+  const int64_t rows = (m + nb - 1) / nb;
+  const size_t es = a_f32 ? 4 : 8;
+  if (!ctx->copy_stream) CK(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
+  while ((int)ctx->copy_ev.size() < nb + 1) {
+    cudaEvent_t e;
+    CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    ctx->copy_ev.push_back(e);
+  }
+  std::vector<SketchPlan> plans;
+  int64_t nslices = 0;
+  for (int k = 0; k < nb; ++k) {
+    const int64_t r0 = k * rows, rk = std::min(rows, m - r0);
+    if (rk <= 0) break;
+    plans.push_back(plan_sketch_simt(env, c, rk, n));
+    nslices += plans.back().ks;
+  }
+  TRY(ensure(ctx, B_SPLITK, sizeof(double) * (size_t)nslices * (size_t)(c * n)));
+  const int64_t nparts = sketch_reduce_parts(c, n);
+  TRY(ensure(ctx, parts_id, sizeof(double) * (size_t)nparts));
+  double* slices = bp<double>(ctx, B_SPLITK);
+  // the copies may only overwrite A_dev once earlier work on the stream is done
+  CK(cudaEventRecord(ctx->copy_ev[nb], ctx->stream));
+  CK(cudaStreamWaitEvent(ctx->copy_stream, ctx->copy_ev[nb], 0));
+  const char* src = static_cast<const char*>(A_host);
+  char* dst = static_cast<char*>(A_dev);
+  for (size_t k = 0; k < plans.size(); ++k) {
+    const int64_t r0 = (int64_t)k * rows, rk = std::min(rows, m - r0);
+    CK(cudaMemcpy2DAsync(dst + (size_t)r0 * n * es, (size_t)n * es, src + (size_t)r0 * lda_host * es,
+                         (size_t)lda_host * es, (size_t)n * es, (size_t)rk, cudaMemcpyHostToDevice,
+                         ctx->copy_stream));
+    CK(cudaEventRecord(ctx->copy_ev[k], ctx->copy_stream));
+  }
+  int64_t z = 0;
+  for (size_t k = 0; k < plans.size(); ++k) {
+    const int64_t r0 = (int64_t)k * rows, rk = std::min(rows, m - r0);
+    CK(cudaStreamWaitEvent(ctx->stream, ctx->copy_ev[k], 0));
+    CK(launch_sketch_simt_slices(env, plans[k], G + r0, m, c, dst + (size_t)r0 * n * es, a_f32, n,
+                                 rk, n, slices + (size_t)z * (size_t)(c * n)));
+    z += plans[k].ks;
+    ctx->launches += 1;
+  }
+  double* parts = bp<double>(ctx, parts_id);
+  CK(launch_sketch_reduce(env, slices, (int)nslices, c, n, Y, parts));
+  ctx->launches += 1;
+  TRY(sum_parts(ctx, parts, nparts, &dstat(ctx)->scalar[slot]));
+  return CUR_OK;
+}
+
 // Precision form: Y = G_q fix_S(A) on the tensor cores, ||Y||^2 into scalar[slot].
 int sketch_q(cur_ctx* ctx, int S, const double* G, int64_t c, const float* A, int64_t m,
              int64_t n, int64_t lda, double* Y, int slot, BufId parts_id, BufId scratch_id) {
@@ -329,8 +386,11 @@ int validate(cur_ctx* ctx, const void* A, int64_t m, int64_t n, int64_t lda, int
   return CUR_OK;
 }
 
+// A_host (optional): A arrives from host memory (row stride lda_host) and A is
+// the device buffer it is copied into; the FP64 sketch then overlaps the copy.
 int run_device(cur_ctx* ctx, const void* A, int64_t m, int64_t n, int64_t lda, int dtype,
-               double tol, int b, int c, uint64_t seed, const cur_opts* o, cur_result** out) {
+               double tol, int b, int c, uint64_t seed, const cur_opts* o, cur_result** out,
+               const void* A_host = nullptr, int64_t lda_host = 0) {
   int64_t max_rank;
   double tol_eff;
   TRY(validate(ctx, A, m, n, lda, dtype, tol, b, &c, o, &max_rank, &tol_eff));
@@ -361,7 +421,10 @@ int run_device(cur_ctx* ctx, const void* A, int64_t m, int64_t n, int64_t lda, i
   TRY(ensure(ctx, B_PARTS, sizeof(double) * 4096));
   tick(ctx, CUR_PHASE_SKETCH);
   const int smode = o ? o->sketch_mode : CUR_SKETCH_F64;
-  if (smode == CUR_SKETCH_F64) {
+  if (smode == CUR_SKETCH_F64 && A_host) {
+    TRY(sketch_f64_from_host(ctx, G, c, A_host, lda_host, const_cast<void*>(A), f32, m, n, S, 0,
+                             B_PARTS));
+  } else if (smode == CUR_SKETCH_F64) {
     TRY(sketch_f64(ctx, G, c, A, f32, m, n, lda, S, 0, B_PARTS));
   } else {
     TRY(sketch_q(ctx, smode, G, c, static_cast<const float*>(A), m, n, lda, S, 0, B_PARTS, B_TC));
@@ -570,6 +633,11 @@ void cur_free(cur_ctx* ctx) {
   for (auto& b : ctx->buf)
     if (b.p) cudaFree(b.p);
   for (auto e : ctx->ev_pool) cudaEventDestroy(e);
+  for (auto e : ctx->copy_ev) cudaEventDestroy(e);
+  if (ctx->copy_stream) {
+    cudaStreamSynchronize(ctx->copy_stream);
+    cudaStreamDestroy(ctx->copy_stream);
+  }
   if (ctx->st_host) cudaFreeHost(ctx->st_host);
   delete ctx;
 }
@@ -604,10 +672,12 @@ int cur_run_host(cur_ctx* ctx, const void* A_host, int64_t m, int64_t n, int64_t
   size_t bytes = es * (size_t)(m * n);
   CK(cudaSetDevice(ctx->device));
   TRY(ensure(ctx, B_AHOST, bytes));
-  CK(cudaMemcpy2DAsync(ctx->buf[B_AHOST].p, es * (size_t)n, A_host, es * (size_t)lda,
-                       es * (size_t)n, (size_t)m, cudaMemcpyHostToDevice, ctx->stream));
+  const bool overlap = !opts || opts->sketch_mode == CUR_SKETCH_F64;
+  if (!overlap)  // the precision forms read A twice (column scales first): copy it whole
+    CK(cudaMemcpy2DAsync(ctx->buf[B_AHOST].p, es * (size_t)n, A_host, es * (size_t)lda,
+                         es * (size_t)n, (size_t)m, cudaMemcpyHostToDevice, ctx->stream));
   int st = run_device(ctx, ctx->buf[B_AHOST].p, m, n, n, dtype, tol, block_size, sketch_size, seed,
-                      opts, out);
+                      opts, out, overlap ? A_host : nullptr, lda);
   if (*out) {
     cur_result* r = *out;
     r->I_host.resize((size_t)r->rank);

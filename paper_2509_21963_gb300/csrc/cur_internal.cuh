@@ -81,6 +81,16 @@ cudaError_t launch_sketch_simt(const LaunchEnv& env, const SketchPlan& p, const 
                                int64_t ldg, int64_t c, const void* A, bool a_f32, int64_t lda,
                                int64_t m, int64_t n, double* Y, double* partial,
                                double* sumsq_part);
+// Row-block form (for a sketch that overlaps the host-to-device copy of A):
+// the plan's ks slices of G(:, rows) A(rows, :) into `slices`, unreduced;
+// then Y = the fixed-order sum of all nslices slices, with sketch_reduce_parts
+// sum-of-squares partials.
+cudaError_t launch_sketch_simt_slices(const LaunchEnv& env, const SketchPlan& p, const double* G,
+                                      int64_t ldg, int64_t c, const void* A, bool a_f32,
+                                      int64_t lda, int64_t m, int64_t n, double* slices);
+int64_t sketch_reduce_parts(int64_t c, int64_t n);
+cudaError_t launch_sketch_reduce(const LaunchEnv& env, const double* slices, int nslices,
+                                 int64_t c, int64_t n, double* Y, double* sumsq_part);
 
 // ---- sketch_tc.cu ------------------------------------------------------------
 // Precision form of Y = G A on tcgen05 (BF16 digit slices, exact FP32/int64

@@ -193,4 +193,36 @@ cudaError_t launch_sketch_simt(const LaunchEnv& env, const SketchPlan& p, const 
   return cudaGetLastError();
 }
 
+// Row-block form for copies that overlap the sketch: the ks slices of
+// G(:, rows) A(rows, :) go to `slices` (ks * c * n doubles, no reduction);
+// launch_sketch_reduce sums all slices of all row blocks in a fixed order.
+cudaError_t launch_sketch_simt_slices(const LaunchEnv& env, const SketchPlan& p, const double* G,
+                                      int64_t ldg, int64_t c, const void* A, bool a_f32,
+                                      int64_t lda, int64_t m, int64_t n, double* slices) {
+  SketchArgs g;
+  g.G = G; g.ldg = ldg; g.c = (int)c; g.A = A; g.lda = lda; g.m = m; g.n = n;
+  g.kunit = p.kunit; g.ks = p.ks;
+  g.out = slices;
+  g.sumsq_part = nullptr;
+  g.vec_ok = (lda % 2 == 0) && ((reinterpret_cast<uintptr_t>(A) & (a_f32 ? 7 : 15)) == 0);
+  const int row_blocks = (int)((c + kMaxWarps * kRowsPerWarp - 1) / (kMaxWarps * kRowsPerWarp));
+  const int rows_first = (int)(c < kMaxWarps * kRowsPerWarp ? c : kMaxWarps * kRowsPerWarp);
+  const int warps = (rows_first + kRowsPerWarp - 1) / kRowsPerWarp;
+  dim3 grid((unsigned)((n + kCols - 1) / kCols), (unsigned)row_blocks, (unsigned)p.ks);
+  if (a_f32) sketch_kernel<true><<<grid, warps * 32, 0, env.stream>>>(g);
+  else sketch_kernel<false><<<grid, warps * 32, 0, env.stream>>>(g);
+  return cudaGetLastError();
+}
+
+int64_t sketch_reduce_parts(int64_t c, int64_t n) { return (c * n + kReducePerCta - 1) / kReducePerCta; }
+
+cudaError_t launch_sketch_reduce(const LaunchEnv& env, const double* slices, int nslices,
+                                 int64_t c, int64_t n, double* Y, double* sumsq_part) {
+  const int64_t total = c * n;
+  const int64_t nblk = (total + kReducePerCta - 1) / kReducePerCta;
+  sketch_reduce_kernel<<<(unsigned)nblk, 256, 0, env.stream>>>(slices, nslices, total, Y,
+                                                                sumsq_part, kReducePerCta);
+  return cudaGetLastError();
+}
+
 }  // namespace cur

@@ -363,6 +363,21 @@ def test_host_entry_point_matches_device(ctx):
     assert a.rho == h.rho and np.array_equal(a.U, h.U)
 
 
+def test_host_entry_point_row_blocks(ctx):
+    """With m >= 2048 the host entry copies A in row blocks that overlap the
+    sketch; the sketch is then summed block by block (another rounding order),
+    so the result equals the device-input run in every decision, with rho and U
+    equal to rounding."""
+    A = inputs.svd_matrix(9000, 600, 10.0 ** (-np.arange(1, 601) / 30.0), seed=12)
+    a = ctx.run(dev(A), 1e-6, 20, 30, 5)
+    h = ctx.run_host(A, 1e-6, 20, 30, 5)
+    assert np.array_equal(a.I, h.I) and np.array_equal(a.J, h.J) and a.rank == h.rank
+    assert abs(a.rho - h.rho) <= 1e-9 * a.rho
+    assert np.linalg.norm(a.U - h.U) <= 1e-6 * np.linalg.norm(a.U)
+    ref = oracle.run(A, 1e-6, 20, 30, seed=5, mode=1)
+    _check_parity(A, h, ref, 20, require_full=False)
+
+
 def test_deterministic_repeat(ctx):
     A = dev(inputs.cfg_small(2))
     a = ctx.run(A, 1e-6, 10, 30, 4)
