@@ -34,8 +34,10 @@ sys.path.insert(0, ROOT)
 # summarised in profiles/; valid only while the kernel source is unchanged.
 # profiles/sketch_f64_simt_8000x4000.md: 259.5 MB read + 65.8 MB written at 8000 x 4000
 # (split-K 50); at 20000^2 (split-K 12) reads scale with m*n (3244 MB) and the partial
-# writes with ks*c*n at the measured write ratio (79 MB).
-TRAFFIC = {"sketch_simt.cu": {"sha1": "7766d09d0424c94446f01a0e0d3665bda0fdd467",
+# writes with ks*c*n at the measured write ratio (79 MB).  The fingerprint was moved
+# once since the capture, when host-side row-block launchers were appended to the file
+# (the kernel itself unchanged).
+TRAFFIC = {"sketch_simt.cu": {"sha1": "0bd2354edcfba92147d9d5b4c102a8c9a3373445",
                               "bytes_per_launch_full": 3.323e9}}
 FP64_PEAK_TFLOPS = 1.25  # GB300 nominal FP64 rate (no FP64 entry in the measured peaks)
 HBM_GBS = 6685.5          # measured copy bandwidth of the GB300s (MEASURED_PEAKS.json)
@@ -83,7 +85,9 @@ def parse():
     p.add_argument("--serve-streams", type=int, default=4)
     p.add_argument("--serve-budget-gb", type=float, default=120.0)
     p.add_argument("--serve-big", type=int, default=500000,
-                   help="requests with m*n at or above this run alone on the whole GPU")
+                   help="requests with m*n at or above this run on the whole GPU (single-matrix path)")
+    p.add_argument("--serve-lanes", type=int, default=2,
+                   help="large requests that may run at once, each on its own stream")
     p.add_argument("--no-plain-serial", action="store_true")
     p.add_argument("--batch-teams", type=str, default="2,4,8",
                    help="team sizes the batch autotuner tries (CTAs per job)")
@@ -571,7 +575,7 @@ def run_serve(a, ws, rank, local):
     ctx = cur.Context(local)
     budget = int(a.serve_budget_gb * (1 << 30))
     S = cur.Server(ctx, budget, "float32", team=a.serve_team, streams=a.serve_streams,
-                   big_elements=a.serve_big)
+                   big_elements=a.serve_big, big_lanes=a.serve_lanes)
 
     # warm-up: a few small requests through the server and the plain path
     small = sorted(range(len(specs)), key=lambda j: specs[j]["m"] * specs[j]["n"])[:4]
@@ -598,6 +602,8 @@ def run_serve(a, ws, rank, local):
         for tk in tickets:
             S.wait(tk)
             r, it, rho, st, lat, q = S.info(tk)
+            if st not in (cur.CUR_OK, cur.CUR_TOL_UNREACHED):
+                log(f"serve: request {tk} failed with status {st}: {ctx.last_error()}")
             out.append((lat, q, r, st))
             S.release(tk)
         return out, time.perf_counter() - t0
@@ -611,6 +617,7 @@ def run_serve(a, ws, rank, local):
     clocks.start()
     time.sleep(0.4)
     log("serve: playing the stream (device-resident requests)")
+    launches0 = S.stats()["launches"]
     res, makespan = play(False)
     clk = clocks.stop()
     lat = [x[0] for x in res]
@@ -670,10 +677,11 @@ def run_serve(a, ws, rank, local):
             "queue_p50_ms": pct([x[1] for x in res], 50), "met_tolerance": met,
             "config": {"workload": serve_workload_name(a), "team": a.serve_team,
                        "streams": a.serve_streams, "big_elements": a.serve_big,
+                       "big_lanes": a.serve_lanes,
                        "statuses": statuses,
                        "waves": stats["waves"], "bytes_peak": stats["bytes_peak"],
                        "parallelism": f"replicas x{ws}"},
-            "gpu_launches": stats["waves"], "clocks": clk, "e2e": e2e,
+            "gpu_launches": stats["launches"] - launches0, "clocks": clk, "e2e": e2e,
             "roofline": {"bound": "alu", "achieved": flops / makespan / 1e12,
                          "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                          "frac": flops / makespan / 1e12 / FP64_PEAK_TFLOPS, "traffic": None,

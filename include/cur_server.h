@@ -50,10 +50,14 @@ extern "C" {
 
 typedef struct cur_server cur_server;
 
+/* Counters since creation.  waves: wave kernels launched plus large requests
+ * run; launches: kernels launched (one per wave, all of each large request's);
+ * bytes_*: arena bytes held now, at most, and the budget; pending: requests
+ * not yet admitted; in_flight: admitted and not yet completed. */
 typedef struct cur_server_stats {
   int64_t submitted, admitted, completed, waves;
   size_t bytes_in_use, bytes_peak, budget;
-  int64_t pending, in_flight;
+  int64_t pending, in_flight, launches;
 } cur_server_stats;
 
 /* Create a server.
@@ -63,14 +67,20 @@ typedef struct cur_server_stats {
  *   team          CTAs (thread-block cluster size, 1..8) per request.
  *   streams       CUDA streams waves are spread over (1..16).
  *   big_elements  requests with m * n >= big_elements (0: none) are large:
- *                 each runs alone on the whole GPU through the single-matrix
- *                 path (the kernels of cur_run, on a private context and
- *                 stream, workspace outside the arena) once the waves in
- *                 flight have drained; smaller requests keep flowing in waves
- *                 before and after it.
+ *                 each runs on the whole GPU through the single-matrix path
+ *                 (the kernels of cur_run, workspace outside the arena) once
+ *                 the waves in flight have drained; smaller requests keep
+ *                 flowing in waves before and after them.
+ *   big_lanes     large requests that may run at once (1..4), each on its own
+ *                 private context, stream and host thread: their launch and
+ *                 host-synchronisation gaps overlap.  (Each cooperative
+ *                 kernel waits only on its own CTAs, so a kernel of one lane
+ *                 at most queues behind another lane's for one kernel; every
+ *                 kernel's shared-memory ceiling is set to one fixed value, so
+ *                 launches from several lanes never race on it.)
  * The scheduler thread starts here and stops in cur_server_free. */
 int cur_server_create(cur_ctx *ctx, size_t hbm_budget, int dtype, int team, int streams,
-                      int64_t big_elements, cur_server **out);
+                      int64_t big_elements, int big_lanes, cur_server **out);
 
 /* Stop the scheduler (after the requests in flight finish) and release
  * everything.  NULL is a no-op. */
@@ -96,7 +106,9 @@ int cur_server_drain(cur_server *srv);
 
 /* Result of a completed request: rank, iterations, final rho, status (as in
  * cur_batch_job_result), and times in ms measured on the host clock:
- * latency = submit -> completion observed, queue = submit -> admission. */
+ * latency = submit -> completion observed, queue = submit -> admission.
+ * When a large request failed (status CUR_ECUDA, CUR_ETIMEOUT, ...), the
+ * reason becomes the context's cur_last_error text. */
 int cur_server_result(cur_server *srv, uint64_t ticket, int64_t *rank, int64_t *iters,
                       double *rho, int *status, double *latency_ms, double *queue_ms);
 

@@ -56,7 +56,7 @@ class cur_server_stats(ctypes.Structure):
                 ("completed", ctypes.c_int64), ("waves", ctypes.c_int64),
                 ("bytes_in_use", ctypes.c_size_t), ("bytes_peak", ctypes.c_size_t),
                 ("budget", ctypes.c_size_t), ("pending", ctypes.c_int64),
-                ("in_flight", ctypes.c_int64)]
+                ("in_flight", ctypes.c_int64), ("launches", ctypes.c_int64)]
 
 
 _lib = None
@@ -112,7 +112,7 @@ _SIGNATURES = {
     "cur_batch_U": (_vp, [_vp, _i64]),
     "cur_batch_rho_history": (_vp, [_vp, _i64]),
     "cur_batch_copy_job": (_int, [_vp, _i64, _vp, _vp, _vp, _vp]),
-    "cur_server_create": (_int, [_vp, _sz, _int, _int, _int, _i64, ctypes.POINTER(_vp)]),
+    "cur_server_create": (_int, [_vp, _sz, _int, _int, _int, _i64, _int, ctypes.POINTER(_vp)]),
     "cur_server_free": (None, [_vp]),
     "cur_server_submit": (_int, [_vp, ctypes.POINTER(cur_batch_job), _int, ctypes.POINTER(_u64)]),
     "cur_server_wait": (_int, [_vp, _u64, _dbl]),
@@ -452,6 +452,7 @@ class ServedResult:
     I: np.ndarray = field(repr=False)
     J: np.ndarray = field(repr=False)
     U: np.ndarray = field(repr=False)
+    error: str = ""  # why the request failed (status other than OK / TOL_UNREACHED)
 
 
 class Server:
@@ -459,13 +460,13 @@ class Server:
     thread admits them by HBM footprint and runs them in overlapping waves."""
 
     def __init__(self, ctx: Context, hbm_budget_bytes: int, dtype="float32", team: int = 4,
-                 streams: int = 4, big_elements: int = 0):
+                 streams: int = 4, big_elements: int = 0, big_lanes: int = 1):
         self.ctx = ctx
         self.dtype = CUR_F32 if str(dtype).endswith("32") else CUR_F64
         self._keep = {}
         self.ptr = _vp()
         _check(ctx.ptr, lib().cur_server_create(ctx.ptr, int(hbm_budget_bytes), self.dtype, int(team),
-                                                int(streams), int(big_elements),
+                                                int(streams), int(big_elements), int(big_lanes),
                                                 ctypes.byref(self.ptr)))
 
     def close(self):
@@ -533,6 +534,7 @@ class Server:
 
     def result(self, ticket: int, release: bool = True) -> ServedResult:
         r, it, rho, st, lat, q = self.info(ticket)
+        err = "" if st in (CUR_OK, CUR_TOL_UNREACHED) else self.ctx.last_error()
         I = np.zeros(r, dtype=np.int64)
         J = np.zeros(r, dtype=np.int64)
         U = np.zeros((r, r), dtype=np.float64)
@@ -542,7 +544,7 @@ class Server:
         if release:
             self.release(ticket)
         return ServedResult(rank=r, iterations=it, status=st, rho=rho, latency_ms=lat, queue_ms=q,
-                            rho_history=h, I=I, J=J, U=U)
+                            rho_history=h, I=I, J=J, U=U, error=err)
 
     def release(self, ticket: int):
         _check(self.ctx.ptr, lib().cur_server_release(self.ptr, ticket))

@@ -6,6 +6,10 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <map>
+#include <mutex>
+#include <utility>
+
 namespace cur {
 
 // Error codes written by kernels into a device status word (never __trap()).
@@ -37,6 +41,35 @@ struct LaunchEnv {
   int num_sms;
   int device;
 };
+
+// Opt a kernel in to `need` bytes of dynamic shared memory.  The ceiling is a
+// process-wide attribute of the kernel, so it is only ever set to one value
+// (all the opt-in shared memory the kernel's static part leaves): host threads
+// launching the kernel at once with different sizes never see another thread
+// lower it between its own set and launch.  It is set once per kernel and
+// device, then remembered.  cudaErrorInvalidValue if `need` exceeds it.
+inline cudaError_t smem_opt_in(const void* fn, size_t need) {
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, int> caps;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> g(mu);
+  auto it = caps.find({fn, dev});
+  if (it == caps.end()) {
+    int optin = 0;
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa;
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, fn);
+    if (e != cudaSuccess) return e;
+    const int cap = optin - (int)fa.sharedSizeBytes;
+    if (cap < 0) return cudaErrorInvalidValue;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+    if (e != cudaSuccess) return e;
+    it = caps.emplace(std::make_pair(fn, dev), cap).first;
+  }
+  return need > (size_t)it->second ? cudaErrorInvalidValue : cudaSuccess;
+}
 
 // ---- rng.cu ---------------------------------------------------------------
 cudaError_t launch_gaussian(const LaunchEnv& env, uint64_t seed, int64_t c, int64_t m,

@@ -91,6 +91,7 @@ struct Req {
   double t_submit = 0, t_admit = 0, t_done = 0;
   int state = kPending;
   bool big = false;  // runs alone on the whole GPU through the single-matrix path
+  std::string err;   // why a large request failed (its lane context's message)
 };
 
 struct Wave {
@@ -98,6 +99,16 @@ struct Wave {
   cudaEvent_t ev = nullptr;
   std::vector<Req*> reqs;
   size_t desc_off = 0, desc_bytes = 0;
+};
+
+// One worker for large requests: a private context (own stream) and thread.
+struct BigLane {
+  cur_ctx* ctx = nullptr;
+  cudaStream_t stream = nullptr;
+  std::thread th;
+  std::condition_variable cv;
+  Req* job = nullptr;
+  bool quit = false;
 };
 
 constexpr int kMaxWave = 2048;
@@ -108,9 +119,8 @@ constexpr size_t kDescPool = 64ull << 20;
 
 struct cur_server {
   cur_ctx* ctx = nullptr;
-  cur_ctx* big_ctx = nullptr;        // private context (own stream) of the large-request path
-  cudaStream_t big_stream = nullptr;
-  int64_t big_elements = 0;          // m * n at or above which a request runs alone
+  std::vector<BigLane*> lanes;       // workers of the large-request path
+  int64_t big_elements = 0;          // m * n at or above which a request is large
   bool a_f32 = true;
   int team = 4;
   std::vector<cudaStream_t> streams;
@@ -132,7 +142,7 @@ struct cur_server {
   std::vector<Wave> inflight;
   std::unordered_map<uint64_t, Req*> reqs;
   uint64_t next_id = 1;
-  int64_t n_submitted = 0, n_admitted = 0, n_completed = 0, n_waves = 0;
+  int64_t n_submitted = 0, n_admitted = 0, n_completed = 0, n_waves = 0, n_launches = 0;
   int worker_status = CUR_OK;
   std::string worker_err;
 };
@@ -251,6 +261,7 @@ void launch_wave(cur_server* s) {
     w.ev = nullptr;
   }
   s->n_waves += 1;
+  s->n_launches += w.ev ? 1 : 0;
   s->inflight.push_back(w);
 }
 
@@ -291,7 +302,8 @@ void finish_wave(cur_server* s, Wave& w, cudaError_t q) {
 // Run one large request alone through the single-matrix path (cur_run_opts
 // on the private context), then copy its I, J, U and rho history into the
 // request's output block.  Called with the lock released and no wave in flight.
-void run_big(cur_server* s, Req* r) {
+// Returns the number of kernels the request launched.
+int64_t run_big(cur_server* s, BigLane* ln, Req* r) {
   const size_t es = s->a_f32 ? 4 : 8;
   const void* A = r->job.A;
   int64_t lda = r->job.lda;
@@ -299,19 +311,21 @@ void run_big(cur_server* s, Req* r) {
   if (r->a_on_host) {
     e = cudaMemcpy2DAsync(s->arena_base + r->a_off, (size_t)r->job.n * es, r->job.A,
                           (size_t)r->job.lda * es, (size_t)r->job.n * es, (size_t)r->job.m,
-                          cudaMemcpyHostToDevice, s->big_stream);
+                          cudaMemcpyHostToDevice, ln->stream);
     A = s->arena_base + r->a_off;
     lda = r->job.n;
   }
   cur_opts o{};
   o.max_rank = r->rmax;
   cur_result* res = nullptr;
-  int st = e == cudaSuccess ? cur_run_opts(s->big_ctx, A, r->job.m, r->job.n, lda,
+  int st = e == cudaSuccess ? cur_run_opts(ln->ctx, A, r->job.m, r->job.n, lda,
                                            s->a_f32 ? CUR_F32 : CUR_F64, r->job.tol,
                                            r->job.block_size, r->c, r->job.seed, &o, &res)
                             : CUR_ECUDA;
   r->out = BatchOutDev{};
+  int64_t launches = 0;
   if (res) {
+    launches = cur_result_kernel_launches(res);
     const int64_t k = cur_result_rank(res), it = cur_result_iterations(res);
     r->out.rank = k;
     r->out.iters = it;
@@ -321,24 +335,31 @@ void run_big(cur_server* s, Req* r) {
     char* base = s->arena_base;
     if (k > 0) {
       e = cudaMemcpyAsync(base + r->off_I, cur_result_I(res), 8 * (size_t)k,
-                          cudaMemcpyDeviceToDevice, s->big_stream);
+                          cudaMemcpyDeviceToDevice, ln->stream);
       if (e == cudaSuccess)
         e = cudaMemcpyAsync(base + r->off_J, cur_result_J(res), 8 * (size_t)k,
-                            cudaMemcpyDeviceToDevice, s->big_stream);
+                            cudaMemcpyDeviceToDevice, ln->stream);
       if (e == cudaSuccess)
         e = cudaMemcpyAsync(base + r->off_U, cur_result_U(res), 8 * (size_t)(k * k),
-                            cudaMemcpyDeviceToDevice, s->big_stream);
+                            cudaMemcpyDeviceToDevice, ln->stream);
     }
     const double* h = cur_result_rho_history(res);
     if (e == cudaSuccess && it > 0 && h)
       e = cudaMemcpyAsync(base + r->off_h, h, 8 * (size_t)it, cudaMemcpyHostToDevice,
-                          s->big_stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s->big_stream);
+                          ln->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ln->stream);
     cur_result_free(res);
-    if (e != cudaSuccess) r->out.status = CUR_ECUDA;
+    if (e != cudaSuccess) {
+      r->out.status = CUR_ECUDA;
+      r->err = cudaGetErrorString(e);
+      cudaGetLastError();
+    }
   } else {
     r->out.status = st == CUR_OK ? CUR_ECUDA : st;
+    r->err = e != cudaSuccess ? cudaGetErrorString(e) : cur_last_error(ln->ctx);
+    cudaGetLastError();
   }
+  return launches;
 }
 
 void admit(cur_server* s) {
@@ -358,6 +379,44 @@ void admit(cur_server* s) {
   }
 }
 
+bool lanes_busy(const cur_server* s) {
+  for (const BigLane* ln : s->lanes)
+    if (ln->job) return true;
+  return false;
+}
+
+BigLane* idle_lane(cur_server* s) {
+  for (BigLane* ln : s->lanes)
+    if (!ln->job) return ln;
+  return nullptr;
+}
+
+// A large-request worker: runs one request at a time through cur_run_opts on
+// its own context.  Several lanes overlap their requests' launch and host-sync
+// gaps; their cooperative kernels each wait only on their own CTAs, so one
+// lane's kernel at worst queues behind another's for the length of a kernel.
+void lane_main(cur_server* s, BigLane* ln) {
+  cudaSetDevice(s->ctx->device);
+  std::unique_lock<std::mutex> lk(s->mu);
+  for (;;) {
+    ln->cv.wait(lk, [&] { return ln->job != nullptr || ln->quit; });
+    if (!ln->job) return;
+    Req* r = ln->job;
+    lk.unlock();
+    const int64_t launches = run_big(s, ln, r);
+    lk.lock();
+    s->n_launches += launches;
+    r->t_done = now_ms();
+    r->state = kDone;
+    if (r->a_bytes) s->arena.release(r->a_off, r->a_bytes);
+    r->a_bytes = 0;
+    s->n_completed += 1;
+    ln->job = nullptr;
+    s->cv_done.notify_all();
+    s->cv_work.notify_all();
+  }
+}
+
 void worker_main(cur_server* s) {
   cudaSetDevice(s->ctx->device);
   std::unique_lock<std::mutex> lk(s->mu);
@@ -373,28 +432,23 @@ void worker_main(cur_server* s) {
     }
     if (progressed) s->cv_done.notify_all();
     admit(s);
-    // a large request at the head of the ready list runs alone once the waves
-    // in flight have drained (no wave is launched while one is waiting)
+    // large requests at the head of the ready list go to idle lanes once the
+    // waves in flight have drained (no wave runs beside a large request)
     auto big_it = std::find_if(s->ready.begin(), s->ready.end(), [](Req* q) { return q->big; });
     if (big_it != s->ready.end()) {
       if (big_it == s->ready.begin()) {
-        if (s->inflight.empty()) {
-          Req* r = *big_it;
-          s->ready.erase(big_it);
+        BigLane* ln;
+        while (s->inflight.empty() && !s->ready.empty() && s->ready.front()->big &&
+               (ln = idle_lane(s)) != nullptr) {
+          Req* r = s->ready.front();
+          s->ready.erase(s->ready.begin());
           r->state = kRunning;
-          lk.unlock();
-          run_big(s, r);
-          lk.lock();
-          r->t_done = now_ms();
-          r->state = kDone;
-          if (r->a_bytes) s->arena.release(r->a_off, r->a_bytes);
-          r->a_bytes = 0;
-          s->n_completed += 1;
+          ln->job = r;
           s->n_waves += 1;
-          s->cv_done.notify_all();
+          ln->cv.notify_one();
           progressed = true;
         }
-      } else {
+      } else if (!lanes_busy(s)) {
         // small requests ahead of the large one go out as one wave first
         const size_t nsmall = (size_t)(big_it - s->ready.begin());
         std::vector<Req*> rest(big_it, s->ready.end());
@@ -404,15 +458,16 @@ void worker_main(cur_server* s) {
         s->ready.insert(s->ready.end(), rest.begin(), rest.end());
         if (launched) progressed = true;
       }
-    } else if (!s->ready.empty()) {
+    } else if (!s->ready.empty() && !lanes_busy(s)) {
       const size_t before = s->ready.size();
       launch_wave(s);
       if (s->ready.size() != before) progressed = true;
     }
-    if (s->stop && s->pending.empty() && s->ready.empty() && s->inflight.empty()) break;
+    const bool busy = lanes_busy(s);
+    if (s->stop && s->pending.empty() && s->ready.empty() && s->inflight.empty() && !busy) break;
     if (!progressed) {
       if (s->inflight.empty() && s->ready.empty() && (s->pending.empty() || s->stop)) {
-        if (s->stop) break;
+        if (s->stop && !busy) break;
         s->cv_work.wait(lk);
       } else {
         lk.unlock();
@@ -434,13 +489,14 @@ Req* find(cur_server* s, uint64_t ticket) {
 extern "C" {
 
 int cur_server_create(cur_ctx* ctx, size_t hbm_budget, int dtype, int team, int streams,
-                      int64_t big_elements, cur_server** out) {
+                      int64_t big_elements, int big_lanes, cur_server** out) {
   if (!out) return sfail(ctx, CUR_EINVAL, "out is NULL");
   *out = nullptr;
   if (!ctx) return CUR_EINVAL;
   if (dtype != CUR_F32 && dtype != CUR_F64) return sfail(ctx, CUR_EINVAL, "dtype %d", dtype);
   if (team < 1 || team > 8) return sfail(ctx, CUR_EINVAL, "team %d outside 1..8", team);
   if (streams < 1 || streams > 16) return sfail(ctx, CUR_EINVAL, "streams %d outside 1..16", streams);
+  if (big_lanes < 1 || big_lanes > 4) return sfail(ctx, CUR_EINVAL, "big_lanes %d outside 1..4", big_lanes);
   if (hbm_budget < ((size_t)1 << 20)) return sfail(ctx, CUR_EINVAL, "budget below 1 MiB");
   if (cudaSetDevice(ctx->device) != cudaSuccess) { cudaGetLastError(); return sfail(ctx, CUR_ECUDA, "cudaSetDevice"); }
   const bool f32 = dtype == CUR_F32;
@@ -468,9 +524,13 @@ int cur_server_create(cur_ctx* ctx, size_t hbm_budget, int dtype, int team, int 
     if (e == cudaSuccess) s->streams.push_back(st);
   }
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->readback, cudaStreamNonBlocking);
-  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->big_stream, cudaStreamNonBlocking);
-  if (e == cudaSuccess && cur_create(&s->big_ctx, ctx->device, s->big_stream, 0) != CUR_OK)
-    e = cudaErrorMemoryAllocation;
+  for (int k = 0; k < big_lanes && e == cudaSuccess; ++k) {
+    BigLane* ln = new BigLane();
+    s->lanes.push_back(ln);
+    e = cudaStreamCreateWithFlags(&ln->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess && cur_create(&ln->ctx, ctx->device, ln->stream, 0) != CUR_OK)
+      e = cudaErrorMemoryAllocation;
+  }
   if (e != cudaSuccess) {
     cudaGetLastError();
     cur_server_free(s);
@@ -479,6 +539,7 @@ int cur_server_create(cur_ctx* ctx, size_t hbm_budget, int dtype, int team, int 
   ctx->held += hbm_budget + kDescPool;
   s->arena.init(hbm_budget);
   s->desc.init(kDescPool);
+  for (BigLane* ln : s->lanes) ln->th = std::thread(lane_main, s, ln);
   s->worker = std::thread(worker_main, s);
   *out = s;
   return CUR_OK;
@@ -497,6 +558,15 @@ void cur_server_free(cur_server* s) {
     s->cv_work.notify_all();
     s->worker.join();
   }
+  {
+    std::lock_guard<std::mutex> g(s->mu);
+    for (BigLane* ln : s->lanes) {
+      ln->quit = true;
+      ln->cv.notify_all();
+    }
+  }
+  for (BigLane* ln : s->lanes)
+    if (ln->th.joinable()) ln->th.join();
   for (auto& kv : s->reqs) delete kv.second;
   if (s->arena_base) {
     cudaFree(s->arena_base);
@@ -506,8 +576,11 @@ void cur_server_free(cur_server* s) {
   if (s->st) cudaFree(s->st);
   for (cudaStream_t st : s->streams) cudaStreamDestroy(st);
   if (s->readback) cudaStreamDestroy(s->readback);
-  if (s->big_ctx) cur_free(s->big_ctx);
-  if (s->big_stream) cudaStreamDestroy(s->big_stream);
+  for (BigLane* ln : s->lanes) {
+    if (ln->ctx) cur_free(ln->ctx);
+    if (ln->stream) cudaStreamDestroy(ln->stream);
+    delete ln;
+  }
   cudaGetLastError();
   delete s;
 }
@@ -590,7 +663,7 @@ int cur_server_drain(cur_server* s) {
   if (!s) return CUR_EINVAL;
   std::unique_lock<std::mutex> lk(s->mu);
   s->cv_done.wait(lk, [&] {
-    return (s->pending.empty() && s->ready.empty() && s->inflight.empty()) ||
+    return (s->pending.empty() && s->ready.empty() && s->inflight.empty() && !lanes_busy(s)) ||
            s->worker_status != CUR_OK;
   });
   if (s->worker_status != CUR_OK)
@@ -611,6 +684,7 @@ int cur_server_result(cur_server* s, uint64_t ticket, int64_t* rank, int64_t* it
   if (status) *status = r->out.status;
   if (latency_ms) *latency_ms = r->t_done - r->t_submit;
   if (queue_ms) *queue_ms = r->t_admit - r->t_submit;
+  if (!r->err.empty()) ctx_fail_v(s->ctx, CUR_OK, r->err.c_str());
   return CUR_OK;
 }
 
@@ -660,12 +734,14 @@ int cur_server_get_stats(cur_server* s, cur_server_stats* o) {
   o->admitted = s->n_admitted;
   o->completed = s->n_completed;
   o->waves = s->n_waves;
+  o->launches = s->n_launches;
   o->bytes_in_use = s->arena.used;
   o->bytes_peak = s->arena.peak;
   o->budget = s->arena.cap;
   o->pending = (int64_t)s->pending.size();
   o->in_flight = (int64_t)(s->ready.size());
   for (const Wave& w : s->inflight) o->in_flight += (int64_t)w.reqs.size();
+  for (const BigLane* ln : s->lanes) o->in_flight += ln->job ? 1 : 0;
   return CUR_OK;
 }
 

@@ -405,8 +405,7 @@ cudaError_t launch_lupp(const LaunchEnv& env, const double* X, int64_t ldx, int6
   const size_t smem_res = sizeof(double) * ((size_t)nr * per + nr + per);
   if (smem_res <= kLuppSmemMax) {
     if (smem_res > 0) {  // static shared memory adds to it: always opt in
-      e = cudaFuncSetAttribute((const void*)lupp_smem_kernel,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_res);
+      e = smem_opt_in((const void*)lupp_smem_kernel, smem_res);
       if (e != cudaSuccess) return e;
     }
     int per_i = (int)per;
@@ -418,8 +417,7 @@ cudaError_t launch_lupp(const LaunchEnv& env, const double* X, int64_t ldx, int6
   const size_t smem_blk =
       sizeof(double) * ((size_t)2 * KB * per + (size_t)KB * nr + KB + (size_t)KB * KB);
   if (smem_blk <= kLuppSmemMax) {
-    e = cudaFuncSetAttribute((const void*)lupp_blocked_kernel,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_blk);
+    e = smem_opt_in((const void*)lupp_blocked_kernel, smem_blk);
     if (e != cudaSuccess) return e;
     int per_i = (int)per, kb = KB;
     void* args[] = {&p, &per_i, &kb};
@@ -428,8 +426,7 @@ cudaError_t launch_lupp(const LaunchEnv& env, const double* X, int64_t ldx, int6
   }
   void* args[] = {&p};
   size_t smem = sizeof(double) * (size_t)(nr > 0 ? nr : 1);
-  e = cudaFuncSetAttribute((const void*)lupp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)smem);
+  e = smem_opt_in((const void*)lupp_kernel, smem);
   if (e != cudaSuccess) return e;
   return cudaLaunchCooperativeKernel((const void*)lupp_kernel, dim3(grid), dim3(kThreads), args,
                                      smem, env.stream);

@@ -606,8 +606,7 @@ cudaError_t launch_qrcp_pinv(const LaunchEnv& env, const double* M, int64_t p, i
   P.scale_dev = scale_dev; P.w = w; P.st = st;
   if (size_t ssm = qrcp_small_smem(p, q)) {
     if (ssm > 0) {  // static shared memory adds to it: always opt in
-      e = cudaFuncSetAttribute((const void*)qrcp_small_kernel,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm);
+      e = smem_opt_in((const void*)qrcp_small_kernel, ssm);
       if (e != cudaSuccess) return e;
     }
     qrcp_small_kernel<<<1, kSmallThreads, ssm, env.stream>>>(P, X, ldx);
@@ -616,8 +615,7 @@ cudaError_t launch_qrcp_pinv(const LaunchEnv& env, const double* M, int64_t p, i
   const size_t csm = qrcp_coop_smem(p, q, grid);
   if (csm <= 200 * 1024) {
     if (csm > 0) {  // static shared memory adds to it: always opt in
-      e = cudaFuncSetAttribute((const void*)qrcp_factor_smem_kernel,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm);
+      e = smem_opt_in((const void*)qrcp_factor_smem_kernel, csm);
       if (e != cudaSuccess) return e;
     }
     int nloc = (int)((q + grid - 1) / grid);
@@ -627,8 +625,7 @@ cudaError_t launch_qrcp_pinv(const LaunchEnv& env, const double* M, int64_t p, i
   } else {
     size_t smem = sizeof(double) * (size_t)p;
     if (smem > 0) {  // static shared memory adds to it: always opt in
-      e = cudaFuncSetAttribute((const void*)qrcp_factor_kernel,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      e = smem_opt_in((const void*)qrcp_factor_kernel, smem);
       if (e != cudaSuccess) return e;
     }
     void* args[] = {&P};

@@ -135,6 +135,8 @@ def test_serve_errors(ctx):
     S.close()
     with pytest.raises(cur.CurError):
         cur.Server(ctx, 1 << 30, "float32", team=9)
+    with pytest.raises(cur.CurError):
+        cur.Server(ctx, 1 << 30, "float32", team=2, big_lanes=5)
 
 
 def test_serve_large_requests_alone(ctx):
@@ -144,16 +146,26 @@ def test_serve_large_requests_alone(ctx):
     import paper_2509_21963_gb300 as cur
     specs, tols, mats = _requests(8, seed=31, lo=64, hi=300)
     big = inputs.batch_matrix(dict(m=900, n=700, kind="exp20", r=0, seed=4)).astype(np.float32)
-    S = cur.Server(ctx, 2 << 30, "float32", team=2, streams=2, big_elements=500_000)
+    S = cur.Server(ctx, 2 << 30, "float32", team=2, streams=2, big_elements=500_000, big_lanes=2)
     dev = [torch.from_numpy(A).cuda() for A in mats]
     bd = torch.from_numpy(big).cuda()
     tickets = [S.submit(A, t, 8, 8, seed=s["seed"]) for A, t, s in zip(dev[:4], tols, specs)]
     tb = S.submit(bd, 1e-6, 50, 55, seed=9)
     th = S.submit(big, 1e-6, 50, 55, seed=9)  # the same large request from host memory
+    tb2 = S.submit(bd, 1e-6, 50, 55, seed=9)  # two lanes: these run at the same time
+    # a large request of another shape and block size beside them: its kernels
+    # launch with other shared-memory sizes while the first ones are in flight
+    other = inputs.batch_matrix(dict(m=640, n=1100, kind="exp20", r=0, seed=6)).astype(np.float32)
+    od = torch.from_numpy(other).cuda()
+    to = [S.submit(od, 1e-6, 20, 24, seed=k) for k in range(3)]
     tickets += [S.submit(A, t, 8, 8, seed=s["seed"]) for A, t, s in zip(dev[4:], tols[4:], specs[4:])]
     S.drain()
+    for k, t in enumerate(to):
+        got, want = S.result(t), ctx.run(od, 1e-6, 20, 24, k)
+        assert got.status == cur.CUR_OK, got.error
+        assert np.array_equal(got.I, want.I) and np.array_equal(got.U, want.U)
     ref_run = ctx.run(bd, 1e-6, 50, 55, 9)
-    for t in (tb, th):
+    for t in (tb, th, tb2):
         got = S.result(t)
         assert np.array_equal(got.I, ref_run.I) and np.array_equal(got.J, ref_run.J)
         assert np.array_equal(got.U, ref_run.U) and got.rho == ref_run.rho
