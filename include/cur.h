@@ -82,14 +82,14 @@ typedef struct cur_opts {
 
 /* Phases of one run, for cur_result_phase_ms (device time, milliseconds). */
 typedef enum {
-  CUR_PHASE_GAUSSIAN = 0,  /* G from the seed (Algorithm 1 line 1)              */
-  CUR_PHASE_SKETCH = 1,    /* Y = G A and ||Y||_F (line 3): the pass over A     */
-  CUR_PHASE_LUPP_COL = 2,  /* J_k (line 7)                                      */
-  CUR_PHASE_ROW_RES = 3,   /* S^row (line 8)                                    */
-  CUR_PHASE_LUPP_ROW = 4,  /* I_k (line 10)                                     */
+  CUR_PHASE_GAUSSIAN = 0,  /* G from the seed (Algorithm 1's sketch matrix)     */
+  CUR_PHASE_SKETCH = 1,    /* Y = G A and ||Y||_F: the pass over A              */
+  CUR_PHASE_LUPP_COL = 2,  /* J_k, column selection                             */
+  CUR_PHASE_ROW_RES = 3,   /* S^row, row residual                               */
+  CUR_PHASE_LUPP_ROW = 4,  /* I_k, row selection                                */
   CUR_PHASE_FACTORS = 5,   /* Rt_k, N_k^+, L_k (Lemma 1 factors)                */
-  CUR_PHASE_COL_RES = 6,   /* S^col update and ||S^col||_F (lines 13-15)        */
-  CUR_PHASE_CORE = 7,      /* U = A(I,J)^+ at exit (line 12)                    */
+  CUR_PHASE_COL_RES = 6,   /* S^col update and ||S^col||_F (rho_k)              */
+  CUR_PHASE_CORE = 7,      /* U = A(I,J)^+ at exit                              */
   CUR_PHASE_COUNT = 8
 } cur_phase;
 

@@ -26,7 +26,7 @@ extern "C" {
  * G has row stride m.  Errors: CUR_EINVAL if c < 1 or m < 1. */
 int cur_step_gaussian(cur_ctx *ctx, uint64_t seed, int64_t c, int64_t m, double *G);
 
-/* Initial sketch S_0^col = Y = G A (Algorithm 1 line 3) in FP64 arithmetic.
+/* Initial sketch S_0^col = Y = G A (Algorithm 1) in FP64 arithmetic.
  *   G  c x m FP64 (stride m); A m x n (stride lda, dtype FP64 or FP32);
  *   Y  c x n FP64 output (stride n);
  *   sumsq_host (may be NULL) receives ||Y||_F^2 (synchronises the stream). */

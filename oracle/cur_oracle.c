@@ -366,12 +366,12 @@ int cur_oracle_run_sketched(const double *A, const double *Asketch, int64_t m, i
   out->rank = 0; out->iters = 0; out->rho = 1.0; out->status = 0;
   if (m <= 0 || n <= 0 || b <= 0 || c < b || !(tol > 0.0)) { out->status = -1; return -1; }
 
-  /* line 1: sketch matrix G (c x m) */
+  /* sketch matrix G (c x m) */
   double *G = (double *)malloc(sizeof(double) * (size_t)(c * m));
   if (Gin) memcpy(G, Gin, sizeof(double) * (size_t)(c * m));
   else cur_oracle_gaussian_sketch(seed, c, m, G);
 
-  /* lines 3-4: S_0 = G A, rho_0 = ||S_0|| / ||G A|| = 1 */
+  /* initial sketch S_0 = G A, rho_0 = ||S_0|| / ||G A|| = 1 */
   double *Y = (double *)malloc(sizeof(double) * (size_t)(c * n));
   if (Asketch) cur_oracle_sketch(G, c, Asketch, m, n, n, Y);
   else cur_oracle_sketch(G, c, A, m, n, lda, Y);
@@ -406,14 +406,14 @@ int cur_oracle_run_sketched(const double *A, const double *Asketch, int64_t m, i
   double thr_scale = -1.0;
   int64_t r = 0, k = 0;
 
-  while (rho > tol && r < max_rank) { /* line 6 */
+  while (rho > tol && r < max_rank) { /* loop while rho exceeds tol */
     int64_t bk = b < max_rank - r ? b : max_rank - r;
-    /* line 7: J_k = LUPP on the sketched residual (candidates = columns) */
+    /* column selection: J_k = LUPP on the sketched residual (candidates = columns) */
     for (int64_t j = 0; j < n; ++j)
       for (int64_t i = 0; i < c; ++i) ST[j * c + i] = S[i * n + j];
     double gap_c = INFINITY, gap_r = INFINITY;
     cur_oracle_lupp(ST, n, c, c, bk, excl_col, J + r, &gap_c);
-    /* line 8: S^row_k = A(:,J_k) - C U R(:,J_k) with the previous C, U, R */
+    /* row residual: S^row_k = A(:,J_k) - C U R(:,J_k) with the previous C, U, R */
     if (mode == 0) {
       row_residual(A, m, lda, I, J, r, U, J + r, bk, Srow);
     } else {
@@ -422,14 +422,14 @@ int cur_oracle_run_sketched(const double *A, const double *Asketch, int64_t m, i
           Srow[i * bk + t] = lemma_residual_entry(A, lda, L, max_rank, Rt, n, r, i, J[r + t]);
     }
     double srow_scale = maxabs(Srow, m * bk);
-    /* line 10: I_k = LUPP on the row residual (candidates = rows) */
+    /* row selection: I_k = LUPP on the row residual (candidates = rows) */
     cur_oracle_lupp(Srow, m, bk, bk, bk, excl_row, I + r, &gap_r);
-    /* lines 9, 11: J = [J, J_k], I = [I, I_k] */
+    /* index updates: J = [J, J_k], I = [I, I_k] */
     int64_t rn = r + bk;
     if (mode == 0) {
-      /* line 12: U = A(I,J)^+ by pivoted QR, recomputed */
+      /* core: U = A(I,J)^+ by pivoted QR, recomputed */
       core_by_qrcp(A, lda, I, J, rn, U);
-      /* lines 13-14: S^col = G A - (G C) U R, G C = (G A)(:,J) */
+      /* column residual: S^col = G A - (G C) U R, G C = (G A)(:,J) */
       col_residual(Y, c, n, A, lda, I, J, rn, U, S);
     } else {
       /* Lemma 1 with I+ = I_k, J+ = J_k: S_k = S_{k-1} - S(:,J_k) N^+ S(I_k,:),
@@ -470,12 +470,12 @@ int cur_oracle_run_sketched(const double *A, const double *Asketch, int64_t m, i
         }
     }
     r = rn;
-    /* line 15 */
+    /* rho_k = ||S^col|| / ||G A|| */
     rho = frob(S, c * n) / nY;
     record(out, k, rho, gap_c, gap_r, srow_scale);
     ++k;
   }
-  /* line 12 at exit (Lemma 1 mode): the core of the returned CUR */
+  /* core at exit (Lemma 1 mode): U of the returned CUR */
   if (mode == 1 && r > 0) core_by_qrcp(A, lda, I, J, r, U);
   out->rank = r;
   out->iters = k;

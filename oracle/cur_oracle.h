@@ -88,8 +88,9 @@ typedef struct cur_oracle_out {
  *   A m x n (stride lda); tol = epsilon; b = block size; c = sketch rows;
  *   G = explicit c x m sketch or NULL (then generated from seed as above);
  *   max_rank <= min(m, n) (0 selects min(m, n));
- *   mode 0: lines 8 and 13-14 literally: U = A(I,J)^+ recomputed by QRCP every
- *           iteration, S^row = A(:,J_k) - C U R(:,J_k), S^col = GA - (GC) U R;
+ *   mode 0: the row and column residuals as Algorithm 1 states them, with
+ *           U = A(I,J)^+ recomputed by QRCP every iteration,
+ *           S^row = A(:,J_k) - C U R(:,J_k), S^col = GA - (GC) U R;
  *   mode 1: the same residuals through Lemma 1, S_k = S_{k-1} - S(:,J_k)
  *           N_k^+ S(I_k,:) with N_k = S_{k-1}(I_k,J_k) (N_k^+ by QRCP with the
  *           absolute threshold |I| * 2^-52 * |R_00(N_1)|), and U = A(I,J)^+ by

@@ -172,7 +172,7 @@ struct PhaseClock {
 };
 
 // ---------------------------------------------------------------------------
-// LUPP (Algorithm 1 lines 7 and 10) in one CTA, on a private copy.
+// LUPP (both selections of Algorithm 1) in one CTA, on a private copy.
 // W holds nf feature rows of ncand candidates (W[t * ldw + i]); mask marks
 // excluded candidates and receives the chosen ones.  Step t takes the
 // eligible candidate of largest |W[t][i]| (ties: smallest index; all zero:
@@ -541,7 +541,7 @@ __device__ void run_job(const BatchParams& P, const Team& tm, const BatchJobDev&
   for (int64_t i = tid; i < n; i += NT) cw.maskc[i] = 0;
   for (int64_t i = tid; i < m; i += NT) cw.maskr[i] = 0;
 
-  // ---- line 1: G (c x m), Philox blocks of four entries --------------------
+  // ---- sketch matrix G (c x m), Philox blocks of four entries -------------
   const int64_t bpr = (m + 3) / 4;
   for (int64_t g = tm.gtid(); g < c * bpr; g += tm.gsize()) {
     const int64_t i = g / bpr, qb = g - i * bpr;
@@ -553,7 +553,7 @@ __device__ void run_job(const BatchParams& P, const Team& tm, const BatchJobDev&
   }
   if (!tm.sync()) return;
 
-  // ---- lines 3-4: S = Y = G A, ||Y||_F ---------------------------------------
+  // ---- initial sketch S = Y = G A, ||Y||_F ---------------------------------
   double ss = 0.0;
   for (int64_t j0 = (int64_t)tm.rank * NT; j0 < n; j0 += tm.gsize()) {
     const int64_t j = j0 + tid;
@@ -603,10 +603,10 @@ __device__ void run_job(const BatchParams& P, const Team& tm, const BatchJobDev&
     rho = 0.0;
   }
 
-  // ---- lines 6-15 ---------------------------------------------------------------
+  // ---- the loop of Algorithm 1 --------------------------------------------------
   while (status == 0 && rho > jb.tol && r < rmax) {
     const int bk = (int)min(b, rmax - r);
-    // line 7: J_k = LUPP(S), privately
+    // column selection: J_k = LUPP(S), privately
     for (int64_t e = tid; e < c * n; e += NT) cw.W[e] = __ldcg(S + e);
     __syncthreads();
     if (!cta_lupp(cw.W, n, (int)c, n, bk, cw.maskc, s_Jk, s_prow)) { status = 5; break; }
@@ -617,7 +617,7 @@ __device__ void run_job(const BatchParams& P, const Team& tm, const BatchJobDev&
       cw.SJ[e] = __ldcg(S + qq * n + s_Jk[t]);
     }
     pc.lap(1);
-    // line 8: S^row = A(:,J_k) - L Rt(:,J_k), rows over the team
+    // row residual: S^row = A(:,J_k) - L Rt(:,J_k), rows over the team
     for (int64_t i0 = (int64_t)tm.rank * NT; i0 < m; i0 += tm.gsize()) {
       const int64_t i = i0 + tid;
       for (int t0 = 0; t0 < bk; t0 += kTB) {
@@ -649,7 +649,7 @@ __device__ void run_job(const BatchParams& P, const Team& tm, const BatchJobDev&
     if (!tm.sync()) { status = 6; break; }
     pc.lap(2);
 
-    // line 10: I_k = LUPP(S^row), privately
+    // row selection: I_k = LUPP(S^row), privately
     for (int64_t e = tid; e < (int64_t)bk * m; e += NT) cw.W[e] = __ldcg(SrowT + e);
     __syncthreads();
     if (!cta_lupp(cw.W, m, bk, m, bk, cw.maskr, s_Ik, s_prow)) { status = 5; break; }
@@ -742,7 +742,7 @@ __device__ void run_job(const BatchParams& P, const Team& tm, const BatchJobDev&
       P.rho_hist[jb.off_hist + iters - 1] = rho;
   }
 
-  // ---- line 12 at exit: U = A(I,J)^+ -----------------------------------------------
+  // ---- core at exit: U = A(I,J)^+ -------------------------------------------------
   if (status == 0 && r > 0) {
     for (int64_t e = tm.gtid(); e < r * r; e += tm.gsize()) {
       const int64_t col = e / r, i = e - col * r;

@@ -2,7 +2,7 @@
 // 2509.21963, Algorithm 1) on one GPU.
 //
 // Per run:  G (seeded Gaussian, c x m)  ->  S = Y = G A, ||Y||_F   (one pass of A)
-// Per iteration k (Algorithm 1 lines 7-15, residuals through Lemma 1):
+// Per iteration k (the loop of Algorithm 1, residuals through Lemma 1):
 //   J_k  = LUPP(S^col)                       cooperative selection kernel
 //   S^row = A(:,J_k) - L Rt(:,J_k)           gather + FP64 GEMM   (m x b)
 //   I_k  = LUPP(S^row)
@@ -11,9 +11,9 @@
 //   L_k  = S^row N^+                         FP64 GEMM            (m x b)
 //   S^col -= (S^col(:,J_k) N^+) Rt_k, ||S^col||_F   fused GEMM + sum of squares
 //   rho = ||S^col||_F / ||Y||_F              8-byte read-back, host decides
-// At exit U = A(I,J)^+ by pivoted QR (line 12, "default QR").
+// At exit U = A(I,J)^+ by pivoted QR (the paper's default QR).
 // Lemma 1 gives S_k = A - sum_l L_l Rt_l with L_l = S_{l-1}(:,J_l) N_l^+ and
-// Rt_l = S_{l-1}(I_l,:): the same residuals as lines 8 and 13-14, without an
+// Rt_l = S_{l-1}(I_l,:): the same row and column residuals, without an
 // explicit U inside the loop.
 #include <cmath>
 #include <cstdarg>
@@ -215,7 +215,7 @@ int gather(cur_ctx* ctx, const void* X, bool f32, int64_t ldx, bool trans, const
 // (batch.cu), smaller ones by the single-CTA or cooperative kernels of qrcp.cu.
 constexpr int64_t kTeamCoreMin = 1024;
 
-// Line 12: U = A(I,J)^+ (r x r), relative rank threshold max(p,q) 2^-52 |R_00|.
+// Core: U = A(I,J)^+ (r x r), relative rank threshold max(p,q) 2^-52 |R_00|.
 // Mc: an r x r scratch for the small-core path.
 int core_solve(cur_ctx* ctx, const void* A, bool f32, int64_t lda, int64_t m, int64_t n,
                const int64_t* I, const int64_t* J, int64_t r, double* Mc, double* U) {
@@ -407,7 +407,7 @@ int run_device(cur_ctx* ctx, const void* A, int64_t m, int64_t n, int64_t lda, i
   double minus1 = -1.0;
   CK(cudaMemcpyAsync(&dstat(ctx)->scalar[2], &minus1, sizeof(double), cudaMemcpyHostToDevice, s));
 
-  // line 1: G; line 3: S_0 = Y = G A and ||Y||_F (the one full pass over A)
+  // sketch matrix G; initial sketch S_0 = Y = G A and ||Y||_F (the one full pass over A)
   const double* G = o ? o->omega : nullptr;
   if (!G) {
     TRY(ensure(ctx, B_OMEGA, sizeof(double) * (size_t)(c * m)));
@@ -478,7 +478,7 @@ int run_device(cur_ctx* ctx, const void* A, int64_t m, int64_t n, int64_t lda, i
 
   double rho = 1.0;
   int64_t r = 0;
-  while (rho > tol_eff && r < max_rank) {  // Algorithm 1 line 6
+  while (rho > tol_eff && r < max_rank) {  // Algorithm 1's loop test
     const int64_t bk = (int64_t)b < max_rank - r ? (int64_t)b : max_rank - r;
     if (r + bk > rcap) {  // grow the Lemma 1 factors, keeping their content
       int64_t nc = rcap * 2 > r + bk ? rcap * 2 : r + bk;
@@ -493,10 +493,10 @@ int run_device(cur_ctx* ctx, const void* A, int64_t m, int64_t n, int64_t lda, i
     int64_t* Jk = Jd + r;
     int64_t* Ik = Id + r;
 
-    // line 7: J_k = LUPP on S^col (candidates: the n columns)
+    // column selection: J_k = LUPP on S^col (candidates: the n columns)
     tick(ctx, CUR_PHASE_LUPP_COL);
     if ((st = lupp_call(ctx, B_LUPPW, S, n, c, n, bk, maskc, Jk)) != CUR_OK) return fail_res(st);
-    // line 8: S^row^T = A(:,J_k)^T - Rt(:,J_k)^T L^T   (bk x m)
+    // row residual: S^row^T = A(:,J_k)^T - Rt(:,J_k)^T L^T   (bk x m)
     tick(ctx, CUR_PHASE_ROW_RES);
     if ((st = gather(ctx, A, f32, lda, true, Jk, nullptr, bk, m, n, m, SrowT, m)) != CUR_OK)
       return fail_res(st);
@@ -508,7 +508,7 @@ int run_device(cur_ctx* ctx, const void* A, int64_t m, int64_t n, int64_t lda, i
       if ((st = gemm(ctx, gargs(bk, m, r, -1.0, G1, bk, true, LT, m, false, false, 1.0, SrowT, m,
                                 SrowT, m))) != CUR_OK) return fail_res(st);
     }
-    // line 10: I_k = LUPP on S^row (candidates: the m rows)
+    // row selection: I_k = LUPP on S^row (candidates: the m rows)
     tick(ctx, CUR_PHASE_LUPP_ROW);
     if ((st = lupp_call(ctx, B_LUPPW, SrowT, m, bk, m, bk, maskr, Ik)) != CUR_OK) return fail_res(st);
     // N = S^row(I_k, :) = S_{k-1}(I_k, J_k)
@@ -535,7 +535,7 @@ int run_device(cur_ctx* ctx, const void* A, int64_t m, int64_t n, int64_t lda, i
     // L_k^T = (S^row N^+)^T = N^+^T S^row^T   (bk x m)
     if ((st = gemm(ctx, gargs(bk, m, bk, 1.0, Np, bk, true, SrowT, m, false, false, 0.0, nullptr, 0,
                               LT + (size_t)r * m, m))) != CUR_OK) return fail_res(st);
-    // lines 13-14 (Lemma 1): S^col -= (S^col(:,J_k) N^+) Rt_k, fused ||S^col||^2
+    // column residual (Lemma 1): S^col -= (S^col(:,J_k) N^+) Rt_k, fused ||S^col||^2
     tick(ctx, CUR_PHASE_COL_RES);
     double* SJk = bp<double>(ctx, B_SJK);
     double* T1 = bp<double>(ctx, B_T1);
@@ -552,7 +552,7 @@ int run_device(cur_ctx* ctx, const void* A, int64_t m, int64_t n, int64_t lda, i
       if ((st = sum_parts(ctx, g.sumsq_part, np, &dstat(ctx)->scalar[1])) != CUR_OK)
         return fail_res(st);
     }
-    // line 15: rho_k (the host needs it to decide line 6)
+    // rho_k (the host needs it for the loop test)
     tick(ctx, -1);
     if ((st = read_status(ctx)) != CUR_OK) return fail_res(st);
     r += bk;
@@ -560,7 +560,7 @@ int run_device(cur_ctx* ctx, const void* A, int64_t m, int64_t n, int64_t lda, i
     res->rho_hist.push_back(rho);
   }
 
-  // line 12 for the returned CUR: U = A(I,J)^+ by pivoted QR
+  // core of the returned CUR: U = A(I,J)^+ by pivoted QR
   res->rank = r;
   res->iters = (int64_t)res->rho_hist.size();
   res->rho = rho;

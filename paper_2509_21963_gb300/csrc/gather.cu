@@ -1,6 +1,6 @@
 // gather.cu -- index gathers of IterativeCUR (arXiv 2509.21963): C_k = A(:,J_k)
-// and R_k = A(I_k,:) (Algorithm 1 line 13), the residual entries S(:,J_k),
-// S(I_k,:), N_k = S(I_k,J_k) of Lemma 1, and the core A(I,J) (line 12).
+// and R_k = A(I_k,:) (Algorithm 1's column residual), the residual entries
+// S(:,J_k), S(I_k,:), N_k = S(I_k,J_k) of Lemma 1, and the core A(I,J).
 //
 // One kernel covers every case: out[a, t] = X(r(a), c(t)) with optional row /
 // column index lists and an optional transpose, converting FP32 sources to

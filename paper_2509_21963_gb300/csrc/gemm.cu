@@ -1,12 +1,12 @@
 // gemm.cu -- FP64 general matrix product with fused sum of squares, used by
-// the residual updates of IterativeCUR (arXiv 2509.21963, Algorithm 1 lines 8,
-// 13-15 in the Lemma 1 form) and by the FP64 sketch Y = G A (line 3).
+// the residual updates of IterativeCUR (arXiv 2509.21963, Algorithm 1's row
+// and column residuals in the Lemma 1 form) and by the FP64 sketch Y = G A.
 //
 // All of these products are FP64; GB300 executes FP64 on a reduced-rate
 // pipe, so a plain register-tiled SIMT kernel (64x64 tile, 4x4 per thread)
 // already saturates it and sits far above its memory roofline.  The epilogue
 // fuses beta*C and the per-tile sum of squares that the stopping test
-// ||S^col||_F needs (Algorithm 1 line 15); partial sums are reduced in a fixed
+// ||S^col||_F needs (Algorithm 1's rho_k); partial sums are reduced in a fixed
 // order so results are deterministic.
 #include "cur_internal.cuh"
 

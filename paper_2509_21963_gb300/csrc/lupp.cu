@@ -1,6 +1,6 @@
 // lupp.cu -- LU with partial pivoting as the index selector of IterativeCUR
 // (arXiv 2509.21963, Sec. 3.2.1 column selection on the sketched residual
-// S^col, Sec. 3.2.2 row selection on S^row; Algorithm 1 lines 7 and 10).
+// S^col, Sec. 3.2.2 row selection on S^row; both selections of Algorithm 1).
 //
 // The candidates (columns of S^col, rows of A for S^row) are the ncand
 // columns of an nr x ncand matrix X.  One cooperative launch performs all

@@ -1,5 +1,5 @@
-// qrcp.cu -- core solve of IterativeCUR (arXiv 2509.21963, Algorithm 1
-// line 12, "U = A(I,J)^+, default QR"): generalised inverse of a p x q matrix
+// qrcp.cu -- core solve of IterativeCUR (arXiv 2509.21963, Algorithm 1: the
+// core U = A(I,J)^+ by the paper's default QR): generalised inverse of a p x q matrix
 // by Householder QR with column pivoting (Businger & Golub 1965),
 //   M P = Q R,  k = #{|R_ii| > thr},  X = P [R_11^{-1} Q_1^T ; 0]   (q x p).
 // Also used for N_k^+ of Lemma 1, N_k = S(I_k, J_k).

@@ -1,5 +1,5 @@
 // sketch_simt.cu -- the initial sketch Y = G A of IterativeCUR (arXiv
-// 2509.21963, Algorithm 1 line 3) in FP64 arithmetic on the SIMT FP64 pipe.
+// 2509.21963, Algorithm 1) in FP64 arithmetic on the SIMT FP64 pipe.
 //
 // GB300 runs FP64 at about 2 DFMA/clk/SM, so this pass is bound by that pipe,
 // not by HBM: the design goal is to keep the pipe busy on every SM for the

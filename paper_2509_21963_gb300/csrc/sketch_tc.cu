@@ -1,5 +1,5 @@
 // sketch_tc.cu -- precision form of the initial sketch Y = G A of IterativeCUR
-// (arXiv 2509.21963, Algorithm 1 line 3; Sec. 3.4 names the sketch as a primary
+// (arXiv 2509.21963, Algorithm 1; Sec. 3.4 names the sketch as a primary
 // cost) on the 5th-generation tensor cores (tcgen05, kind::f16, BF16 operands,
 // FP32 accumulators in tensor memory).
 //
