@@ -58,9 +58,12 @@ int cur_step_lupp(cur_ctx *ctx, const double *X, int64_t ldx, int64_t nr,
 /* Generalised inverse X = M^+ (q x p, stride p) of M (p x q, stride ldm) by
  * Householder QR with column pivoting (Businger-Golub): M P = Q R,
  * k = #{|R_ii| > thr}, X = P [R_11^{-1} Q_1^T; 0].  This is the core solve
- * "U = A(I,J)^+, default QR" of Algorithm 1.  thr < 0 selects
+ * U = A(I,J)^+ of Algorithm 1 (the paper's default QR).  thr < 0 selects
  * thr = max(p,q) 2^-52 |R_00|.  rank_host (may be NULL) receives k
- * (synchronises the stream). */
+ * (synchronises the stream).  The kernels are those cur_run uses for a core
+ * of this size: one CTA, a cooperative grid holding M in shared memory, or
+ * (square M too large for that, p <= 10240) the whole-GPU team QR with a
+ * shared-memory solve panel. */
 int cur_step_pinv(cur_ctx *ctx, const double *M, int64_t p, int64_t q,
                   int64_t ldm, double thr, double *X, int64_t *rank_host);
 

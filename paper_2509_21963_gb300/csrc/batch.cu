@@ -418,27 +418,38 @@ __device__ void team_qr_solve(const Team& tm, const QrWs& w, int64_t p, int64_t 
   }
 }
 
-// The same solve with kPanel right-hand sides of X resident in shared memory
-// (Zs: kPanel columns of length p, column-major), panels spread over the
-// team's CTAs.  Each reflector is read once per panel and applied with two
-// block barriers; the back substitution runs column-oriented (R's column
-// perm[i] is contiguous in Mc) with one block barrier per row.
-constexpr int kPanel = 8;
-constexpr int kPanelRows = 10;  // rows per thread (256 threads): cores up to 2560
-static_assert((size_t)kPanelRows * 256 * kPanel * sizeof(double) >= kBatchMaxPanelBytes,
-              "every core that fits the panel has at most kPanelRows rows per thread");
+// The same solve with PW right-hand sides of X resident in shared memory
+// (Zs: PW columns of length p, column-major), panels spread over the team's
+// CTAs.  Each reflector is read once per panel and applied with two block
+// barriers; the back substitution runs column-oriented (R's column perm[i] is
+// contiguous in Mc) with one block barrier per row.  Each of the block's
+// threads owns at most PR rows (p <= PR * blockDim.x).
+// Panel widths: the widest that fits the dynamic shared memory, with the rows
+// per thread that 160 KB of panel gives 256 threads at that width.
+__host__ __device__ inline int panel_rows(int pw) { return pw == 8 ? 10 : pw == 4 ? 20 : 40; }
+__host__ __device__ inline int panel_width(int64_t p, size_t bytes, int threads) {
+  for (int pw = 8; pw >= 2; pw >>= 1)
+    if ((size_t)p * pw * sizeof(double) <= bytes && p <= (int64_t)panel_rows(pw) * threads)
+      return pw;
+  return 0;
+}
+static_assert((size_t)10 * 256 * 8 * sizeof(double) >= kBatchMaxPanelBytes &&
+                  (size_t)20 * 256 * 4 * sizeof(double) >= kBatchMaxPanelBytes &&
+                  (size_t)40 * 256 * 2 * sizeof(double) >= kBatchMaxPanelBytes,
+              "at each width, every core that fits the panel has at most panel_rows rows per thread");
 
+template <int PW, int PR>
 __device__ void team_qr_solve_panel(const Team& tm, const QrWs& w, int64_t p, int64_t q, int64_t k,
                                     double* X, int64_t ldx, double* Zs, const double* rinv) {
-  __shared__ double s_red[kMaxWarps][kPanel];
-  __shared__ double s_d[kPanel];
+  __shared__ double s_red[kMaxWarps][PW];
+  __shared__ double s_d[PW];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
   const int NT = blockDim.x;
-  const int64_t npanel = (p + kPanel - 1) / kPanel;
+  const int64_t npanel = (p + PW - 1) / PW;
   for (int64_t g = tm.rank; g < npanel; g += tm.T) {
-    const int64_t c0 = g * kPanel;
-    const int wc = (int)min((int64_t)kPanel, p - c0);
-    for (int64_t e = tid; e < p * kPanel; e += NT) {
+    const int64_t c0 = g * PW;
+    const int wc = (int)min((int64_t)PW, p - c0);
+    for (int64_t e = tid; e < p * PW; e += NT) {
       const int64_t c = e / p, i = e - c * p;
       Zs[e] = (c < wc && i == c0 + c) ? 1.0 : 0.0;
     }
@@ -451,66 +462,78 @@ __device__ void team_qr_solve_panel(const Team& tm, const QrWs& w, int64_t p, in
       const double t = __ldcg(w.tau + jj);
       if (t == 0.0) continue;
       const double* v = w.V + jj * p;
-      double acc[kPanel];
+      double acc[PW];
 #pragma unroll
-      for (int c = 0; c < kPanel; ++c) acc[c] = 0.0;
+      for (int c = 0; c < PW; ++c) acc[c] = 0.0;
       // rows stay with thread i % NT for every reflector, so each row of the
       // panel is only ever touched by one thread (no barrier between the
       // update of H_jj and the dot of H_jj+1); the reflector's entries of this
       // thread's rows are loaded once (all in flight together) and reused by
       // the update
       const int64_t i0 = (jj / NT) * NT + tid;
-      double vr[kPanelRows];
+      double vr[PR];
 #pragma unroll
-      for (int q = 0; q < kPanelRows; ++q) {
+      for (int q = 0; q < PR; ++q) {
         const int64_t i = i0 + (int64_t)q * NT;
         vr[q] = (i >= jj && i < p) ? __ldcg(v + i) : 0.0;
       }
 #pragma unroll
-      for (int q = 0; q < kPanelRows; ++q) {
+      for (int q = 0; q < PR; ++q) {
         const int64_t i = i0 + (int64_t)q * NT;
         if (i < jj || i >= p) continue;
 #pragma unroll
-        for (int c = 0; c < kPanel; ++c) acc[c] += vr[q] * Zs[c * p + i];
+        for (int c = 0; c < PW; ++c) acc[c] += vr[q] * Zs[c * p + i];
       }
 #pragma unroll
-      for (int c = 0; c < kPanel; ++c)
+      for (int c = 0; c < PW; ++c)
         for (int o = 16; o > 0; o >>= 1) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o);
       if (lane == 0)
 #pragma unroll
-        for (int c = 0; c < kPanel; ++c) s_red[wid][c] = acc[c];
+        for (int c = 0; c < PW; ++c) s_red[wid][c] = acc[c];
       __syncthreads();
-      if (tid < kPanel) {
+      if (tid < PW) {
         double sum = 0.0;
         for (int w2 = 0; w2 < nw; ++w2) sum += s_red[w2][tid];
         s_d[tid] = t * sum;
       }
       __syncthreads();
 #pragma unroll
-      for (int q = 0; q < kPanelRows; ++q) {
+      for (int q = 0; q < PR; ++q) {
         const int64_t i = i0 + (int64_t)q * NT;
         if (i < jj || i >= p) continue;
 #pragma unroll
-        for (int c = 0; c < kPanel; ++c) Zs[c * p + i] -= s_d[c] * vr[q];
+        for (int c = 0; c < PW; ++c) Zs[c * p + i] -= s_d[c] * vr[q];
       }
     }
     for (int64_t i = k - 1; i >= 0; --i) {
       __syncthreads();
       const double ri = rinv[i];
       const int64_t pi = __ldcg(w.perm + i);
-      double zi[kPanel];
+      double zi[PW];
 #pragma unroll
-      for (int c = 0; c < kPanel; ++c) zi[c] = Zs[c * p + i] * ri;
+      for (int c = 0; c < PW; ++c) zi[c] = Zs[c * p + i] * ri;
       const double* Rcol = w.Mc + pi * p;  // R(l, i) for l < i
       for (int64_t l = tid; l < i; l += NT) {
         const double rl = __ldcg(Rcol + l);
 #pragma unroll
-        for (int c = 0; c < kPanel; ++c) Zs[c * p + l] -= rl * zi[c];
+        for (int c = 0; c < PW; ++c) Zs[c * p + l] -= rl * zi[c];
       }
       if (tid == 0)
         for (int c = 0; c < wc; ++c) X[pi * ldx + c0 + c] = zi[c];
     }
     __syncthreads();
+  }
+}
+
+// Solve with the widest shared-memory panel that fits `panel_bytes`, else the
+// unpanelled solve (which needs the p x p QT scratch).
+__device__ void team_qr_solve_best(const Team& tm, const QrWs& w, int64_t p, int64_t q, int64_t k,
+                                   double* X, int64_t ldx, size_t panel_bytes, const double* rinv) {
+  switch (panel_width(p, panel_bytes, (int)blockDim.x)) {
+    case 8: team_qr_solve_panel<8, 10>(tm, w, p, q, k, X, ldx, dyn_smem(), rinv); break;
+    case 4: team_qr_solve_panel<4, 20>(tm, w, p, q, k, X, ldx, dyn_smem(), rinv); break;
+    case 2: team_qr_solve_panel<2, 40>(tm, w, p, q, k, X, ldx, dyn_smem(), rinv); break;
+    default: team_qr_solve(tm, w, p, q, k, X, ldx, rinv);
   }
 }
 
@@ -753,10 +776,7 @@ __device__ void run_job(const BatchParams& P, const Team& tm, const BatchJobDev&
     pc.lap(5);
     if (status == 0) {
       const int64_t k = qr_rank(tw.qr, r, r, -1.0, cw.vloc);
-      if (r * kPanel * (int64_t)sizeof(double) <= P.panel_bytes)
-        team_qr_solve_panel(tm, tw.qr, r, r, k, Uout, r, dyn_smem(), cw.vloc);
-      else
-        team_qr_solve(tm, tw.qr, r, r, k, Uout, r, cw.vloc);
+      team_qr_solve_best(tm, tw.qr, r, r, k, Uout, r, P.panel_bytes, cw.vloc);
     }
   }
   if (status == 0 && rho > jb.tol) status = 7;  // CUR_TOL_UNREACHED
@@ -813,10 +833,7 @@ __global__ void __launch_bounds__(256, 1) core_qr_kernel(CoreQrParams P) {
   double* vloc = P.vloc + (size_t)blockIdx.x * P.vloc_stride;
   if (!team_qr_factor(tm, P.w, P.p, P.q, vloc)) return;
   const int64_t k = qr_rank(P.w, P.p, P.q, P.thr, vloc);
-  if (P.p * kPanel * (int64_t)sizeof(double) <= (int64_t)P.panel_bytes)
-    team_qr_solve_panel(tm, P.w, P.p, P.q, k, P.X, P.ldx, dyn_smem(), vloc);
-  else
-    team_qr_solve(tm, P.w, P.p, P.q, k, P.X, P.ldx, vloc);
+  team_qr_solve_best(tm, P.w, P.p, P.q, k, P.X, P.ldx, P.panel_bytes, vloc);
   if (blockIdx.x == 0 && threadIdx.x == 0 && P.rank_out) *P.rank_out = k;
 }
 
@@ -870,8 +887,8 @@ int batch_max_ctas(const LaunchEnv& env, int threads, bool a_f32, size_t dyn_sme
 }
 
 size_t batch_panel_bytes(int64_t rmax) {
-  const size_t need = (size_t)rmax * kPanel * sizeof(double);
-  return need <= kBatchMaxPanelBytes ? need : 0;
+  const int pw = panel_width(rmax, kBatchMaxPanelBytes, 256);
+  return (size_t)rmax * pw * sizeof(double);
 }
 
 cudaError_t launch_batch(const LaunchEnv& env, const BatchParams& P, int grid, int threads,

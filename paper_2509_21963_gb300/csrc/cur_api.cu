@@ -211,16 +211,19 @@ int gather(cur_ctx* ctx, const void* X, bool f32, int64_t ldx, bool trans, const
   return CUR_OK;
 }
 
-// Cores of at least this rank are factored by the whole-GPU team QR
-// (batch.cu), smaller ones by the single-CTA or cooperative kernels of qrcp.cu.
-constexpr int64_t kTeamCoreMin = 1024;
+// Square cores whose pivoted QR no longer fits the shared-memory kernels of
+// qrcp.cu (rank above ~1800 on 152 SMs) are factored by the whole-GPU team QR
+// of batch.cu when its solve panel fits (rank up to 10240); the rest by qrcp.cu.
+bool team_core(const LaunchEnv& env, int64_t p, int64_t q) {
+  return p == q && !qrcp_resident(env, p, q) && batch_panel_bytes(p) > 0;
+}
 
 // Core: U = A(I,J)^+ (r x r), relative rank threshold max(p,q) 2^-52 |R_00|.
 // Mc: an r x r scratch for the small-core path.
 int core_solve(cur_ctx* ctx, const void* A, bool f32, int64_t lda, int64_t m, int64_t n,
                const int64_t* I, const int64_t* J, int64_t r, double* Mc, double* U) {
   LaunchEnv env = env_of(ctx);
-  const int T = r >= kTeamCoreMin ? core_qr_grid(env, r) : 0;
+  const int T = team_core(env, r, r) ? core_qr_grid(env, r) : 0;
   if (T > 0) {
     TRY(ensure(ctx, B_TEAMCORE, core_qr_work_bytes(r, r, T)));
     double* W = bp<double>(ctx, B_TEAMCORE);
@@ -802,11 +805,25 @@ int cur_step_pinv(cur_ctx* ctx, const double* M, int64_t p, int64_t q, int64_t l
   CK(cudaSetDevice(ctx->device));
   TRY(ensure(ctx, B_STATUS, sizeof(DevStatus)));
   CK(cudaMemsetAsync(ctx->buf[B_STATUS].p, 0, sizeof(DevStatus), ctx->stream));
+  LaunchEnv env = env_of(ctx);
+  const int T = team_core(env, p, q) ? core_qr_grid(env, p) : 0;
+  if (T > 0) {  // the same kernels as the core of cur_run at this size
+    const size_t wb = core_qr_work_bytes(p, q, T);
+    TRY(ensure(ctx, B_TEAMCORE, wb + 256));
+    double* W = bp<double>(ctx, B_TEAMCORE);
+    int64_t* rk = reinterpret_cast<int64_t*>(reinterpret_cast<char*>(W) + wb);
+    // column-major M: W[col * p + i] = M(i, col)
+    TRY(gather(ctx, M, false, ldm, true, nullptr, nullptr, q, p, q, p, W, p));
+    CK(launch_core_qr(env, W, p, q, thr < 0 ? -1.0 : thr, X, p, W, T, dstat(ctx), rk));
+    ctx->launches += 1;
+    TRY(read_status(ctx));
+    if (rank_host) CK(cudaMemcpy(rank_host, rk, sizeof(int64_t), cudaMemcpyDeviceToHost));
+    return CUR_OK;
+  }
   TRY(pinv_call(ctx, B_STEP_QR, M, p, q, ldm, thr < 0 ? 0 : 1, thr, nullptr, X, p));
   TRY(read_status(ctx));
   if (rank_host) {
     QrcpWork w;
-    LaunchEnv env = env_of(ctx);
     qrcp_carve(ctx->buf[B_STEP_QR].p, p, q, qrcp_grid(env, p, q), &w);
     CK(cudaMemcpy(rank_host, w.rank, sizeof(int64_t), cudaMemcpyDeviceToHost));
   }

@@ -186,6 +186,9 @@ struct QrcpWork {
 size_t qrcp_work_bytes(int64_t p, int64_t q, int max_grid);
 void qrcp_carve(void* base, int64_t p, int64_t q, int max_grid, QrcpWork* w);
 int qrcp_grid(const LaunchEnv& env, int64_t p, int64_t q);
+// True when the factorisation keeps M in shared memory (one CTA, or each CTA of
+// the cooperative grid holding its columns); false: the global-memory kernel.
+bool qrcp_resident(const LaunchEnv& env, int64_t p, int64_t q);
 // thr_mode: 0 relative (max(p,q) 2^-52 |R_00|); 1 absolute `thr`; 2 absolute
 // thr * (*scale_dev), where *scale_dev (if *scale_dev < 0) is first set to
 // 2^-52 |R_00| of this factorisation.

@@ -586,6 +586,10 @@ static size_t qrcp_coop_smem(int64_t p, int64_t q, int g) {
   return sizeof(double) * (size_t)(nloc * p + p) + sizeof(int) * (size_t)nloc;
 }
 
+bool qrcp_resident(const LaunchEnv& env, int64_t p, int64_t q) {
+  return qrcp_small_smem(p, q) > 0 || qrcp_coop_smem(p, q, qrcp_grid(env, p, q)) <= 200 * 1024;
+}
+
 int qrcp_grid(const LaunchEnv& env, int64_t p, int64_t q) {
   if (q <= 128) return 1;
   int64_t g = (q + 7) / 8;   // about 8 columns (one per warp) per CTA

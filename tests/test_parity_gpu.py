@@ -136,6 +136,53 @@ def test_pinv_matches_oracle(ctx, p, seed):
     assert np.linalg.norm(M @ Xg - np.eye(p)) <= 10 * p * kappa * U_RND
 
 
+def test_pinv_team_matches_oracle(ctx):
+    """A square core too large for the shared-memory QR kernels (p = 1900)
+    runs on the whole-GPU team QR with a panel of 8 right-hand sides: against
+    the oracle, with the bounds above."""
+    p = 1900
+    M = np.random.default_rng(6).standard_normal((p, p))
+    Xo, ko, _, _ = oracle.qrcp_pinv(M)
+    Xg, kg = ctx.pinv(dev(M))
+    Xg = Xg.cpu().numpy()
+    assert kg == ko == p
+    kappa = np.linalg.cond(M)
+    assert np.linalg.norm(Xg - Xo) / np.linalg.norm(Xo) <= 10 * p * kappa * U_RND
+    assert np.linalg.norm(M @ Xg - np.eye(p)) <= 10 * p * kappa * U_RND
+
+
+@pytest.mark.parametrize("p", [3001, 6000])
+def test_pinv_team_wide_cores(ctx, p):
+    """Team QR cores with solve panels of 4 (p = 3001, ragged against the 256
+    threads) and 2 (p = 6000) right-hand sides, beyond the oracle's seconds:
+    Householder QR's backward stability, ||M X - I||_F <= 10 p u ||M||_F ||X||_F
+    (||M||_F ||X||_F bounds kappa_2 from above); a wrong reflector, pivot or
+    row leaves a residual of order one."""
+    Md = torch.from_numpy(np.random.default_rng(p).standard_normal((p, p))).cuda()
+    Xd, k = ctx.pinv(Md)
+    assert k == p
+    res = torch.linalg.matrix_norm(Md @ Xd - torch.eye(p, dtype=torch.float64, device="cuda")).item()
+    bound = 10 * p * U_RND * torch.linalg.matrix_norm(Md).item() * torch.linalg.matrix_norm(Xd).item()
+    assert res <= bound, (res, bound)
+    assert res <= 1e-6
+
+
+def test_run_team_core_wide_panel(ctx):
+    """A whole run whose core (rank 2700 at full rank) takes the team QR with a
+    4-wide solve panel: the returned U inverts A(I,J) to the same backward
+    bound, and the run ends at full rank with rho at noise level."""
+    m, n = 3000, 2700
+    A = inputs.svd_matrix(m, n, 0.9995 ** np.arange(n), seed=12)
+    got = ctx.run(dev(A), 1e-8, 50, 55, 3)
+    assert got.status == 0 and got.rank == n and got.rho <= 1e-9
+    assert len(set(got.I)) == n and len(set(got.J)) == n
+    Md = dev(A)[torch.from_numpy(got.I).cuda()][:, torch.from_numpy(got.J).cuda()]
+    Ud = torch.from_numpy(got.U).cuda()
+    res = torch.linalg.matrix_norm(Ud @ Md - torch.eye(n, dtype=torch.float64, device="cuda")).item()
+    bound = 10 * n * U_RND * torch.linalg.matrix_norm(Md).item() * torch.linalg.matrix_norm(Ud).item()
+    assert res <= bound, (res, bound)
+
+
 def test_pinv_rank_deficient(ctx):
     rng = np.random.default_rng(5)
     M = rng.standard_normal((40, 10)) @ rng.standard_normal((10, 40))
