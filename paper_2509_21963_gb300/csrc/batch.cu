@@ -50,7 +50,8 @@ struct Team {
   bool cluster;     // the team is a thread-block cluster (hardware barrier)
   __device__ int64_t gtid() const { return (int64_t)rank * blockDim.x + threadIdx.x; }
   __device__ int64_t gsize() const { return (int64_t)T * blockDim.x; }
-  // All threads of all CTAs of the team; false on timeout / earlier error.
+  // All threads of all CTAs of the team; false on timeout, or when another CTA
+  // recorded an error while this one waited.
   __device__ bool sync() const {
     if (T == 1) {
       __syncthreads();
@@ -63,27 +64,7 @@ struct Team {
     }
     __shared__ int s_ok;
     __syncthreads();
-    if (threadIdx.x == 0) {
-      int ok = 1;
-      volatile unsigned* vgen = &bar->gen;
-      unsigned g = *vgen;
-      __threadfence();
-      unsigned prev = atomicAdd(&bar->count, 1u);
-      if (prev == (unsigned)T - 1) {
-        atomicExch(&bar->count, 0u);
-        __threadfence();
-        atomicAdd(&bar->gen, 1u);
-      } else {
-        long long t0 = clock64();
-        while (*vgen == g) {
-          if (clock64() - t0 > kBarrierBudget) { ok = 0; dev_set_err(st, kDevTimeout); break; }
-          __nanosleep(32);
-        }
-      }
-      __threadfence();
-      if (*((volatile int*)&st->err) != 0) ok = 0;
-      s_ok = ok;
-    }
+    if (threadIdx.x == 0) s_ok = bar_arrive_wait(bar, (unsigned)T, st) ? 1 : 0;
     __syncthreads();
     return s_ok != 0;
   }

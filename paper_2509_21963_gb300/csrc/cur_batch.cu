@@ -130,7 +130,8 @@ int plan_schedule(cur_batch* b, int team) {
     b->cta_alloc = need_c;
   }
   // barriers start at zero; every team's header is re-zeroed here and stays
-  // consistent across launches (each barrier returns its counter to zero)
+  // consistent across launches (a completed barrier leaves its counter at a
+  // multiple of the team size)
   BCK(cudaMemsetAsync(b->team_scratch, 0, need_t, b->bstream));
   BCK(cudaStreamSynchronize(b->bstream));
   b->team = team;

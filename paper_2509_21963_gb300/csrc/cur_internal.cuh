@@ -26,10 +26,11 @@ struct DevStatus {
   double scalar[6];  // [0] sumsq of Y, [1] sumsq of S, [2] pinv rank-scale, ...
 };
 
-// Bounded software grid barrier for cooperative launches.
-struct GridBar {
-  unsigned count;
-  unsigned gen;
+// Bounded software barrier for co-resident CTAs (cooperative launches, software
+// teams): one 64-bit arrival counter that only grows (gridbar.cuh).  Zeroed
+// before a launch; a completed barrier leaves it at a multiple of its CTA count.
+struct alignas(8) GridBar {
+  unsigned long long count;
 };
 
 // Cycle budget of one barrier wait (~2 s at 2 GHz): far above any legitimate
