@@ -217,6 +217,96 @@ __device__ void qr_local_best(const Team& tm, const QrWs& w, int64_t q, double* 
 // Factorisation; false on a team barrier failure.  Every read of Mc goes
 // through L2 (__ldcg): the team's scratch is reused by jobs of other shapes,
 // so a line cached in this SM's L1 may hold another CTA's older data.
+// Apply H_j = I - tau v v^T (v = vloc, rows j..p-1) to one column x of the
+// trailing matrix with one warp, and return the column's squared norm over
+// rows j+1..p-1 (the next pivot search needs it).  Columns of at most 32 R rows
+// stay in registers between the dot product and the update (one pass over L2);
+// longer ones take two passes with eight loads in flight per lane.
+template <int R>
+__device__ __forceinline__ double qr_col_apply_reg(double* x, const double* vloc, int64_t j,
+                                                   int64_t p, double tau, int lane) {
+  double y[R], v[R];
+#pragma unroll
+  for (int t = 0; t < R; ++t) {
+    const int64_t i = j + lane + 32 * t;
+    y[t] = i < p ? __ldcg(x + i) : 0.0;
+    v[t] = i < p ? vloc[i] : 0.0;
+  }
+  if (tau != 0.0) {
+    double d = 0.0;
+#pragma unroll
+    for (int t = 0; t < R; ++t) d += v[t] * y[t];
+    for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+    const double f = tau * d;
+#pragma unroll
+    for (int t = 0; t < R; ++t) {
+      const int64_t i = j + lane + 32 * t;
+      y[t] = y[t] - f * v[t];
+      if (i < p) x[i] = y[t];
+    }
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int t = 0; t < R; ++t) {
+    const int64_t i = j + lane + 32 * t;
+    if (i > j && i < p) s += y[t] * y[t];
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  return s;
+}
+
+__device__ __forceinline__ double qr_col_apply_l2(double* x, const double* vloc, int64_t j,
+                                                  int64_t p, double tau, int lane) {
+  double f = 0.0;
+  if (tau != 0.0) {
+    double d[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) d[u] = 0.0;
+    int64_t i = j + lane;
+    for (; i + 224 < p; i += 256) {
+      double a[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) a[u] = __ldcg(x + i + 32 * u);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) d[u] += vloc[i + 32 * u] * a[u];
+    }
+    for (; i < p; i += 32) d[0] += vloc[i] * __ldcg(x + i);
+    double dd = ((d[0] + d[1]) + (d[2] + d[3])) + ((d[4] + d[5]) + (d[6] + d[7]));
+    for (int o = 16; o > 0; o >>= 1) dd += __shfl_xor_sync(0xffffffffu, dd, o);
+    f = tau * dd;
+  }
+  double sq[8];
+#pragma unroll
+  for (int u = 0; u < 8; ++u) sq[u] = 0.0;
+  int64_t i = j + lane;
+  for (; i + 224 < p; i += 256) {
+    double y[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) y[u] = __ldcg(x + i + 32 * u);
+    if (tau != 0.0) {
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        y[u] = y[u] - f * vloc[i + 32 * u];
+        x[i + 32 * u] = y[u];
+      }
+    }
+    sq[0] += (i > j) ? y[0] * y[0] : 0.0;  // only the row i = j (lane 0, first block) is excluded
+#pragma unroll
+    for (int u = 1; u < 8; ++u) sq[u] += y[u] * y[u];
+  }
+  for (; i < p; i += 32) {
+    double y = __ldcg(x + i);
+    if (tau != 0.0) {
+      y = y - f * vloc[i];
+      x[i] = y;
+    }
+    if (i > j) sq[0] += y * y;
+  }
+  double s = ((sq[0] + sq[1]) + (sq[2] + sq[3])) + ((sq[4] + sq[5]) + (sq[6] + sq[7]));
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  return s;
+}
+
 __device__ bool team_qr_factor(const Team& tm, const QrWs& w, int64_t p, int64_t q, double* vloc) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int64_t kmax = p < q ? p : q;
@@ -291,54 +381,12 @@ __device__ bool team_qr_factor(const Team& tm, const QrWs& w, int64_t p, int64_t
     for (int64_t col = tm.rank + (int64_t)tm.T * wid; col < q; col += (int64_t)tm.T * nw) {
       if (w.used[col]) continue;
       double* x = w.Mc + col * p;
-      double f = 0.0;
-      // four independent L2 loads in flight per lane (the loops are latency bound)
-      if (tau != 0.0) {
-        double d0 = 0.0, d1 = 0.0, d2 = 0.0, d3 = 0.0;
-        int64_t i = j + lane;
-        for (; i + 96 < p; i += 128) {
-          const double a0 = __ldcg(x + i), a1 = __ldcg(x + i + 32), a2 = __ldcg(x + i + 64),
-                       a3 = __ldcg(x + i + 96);
-          d0 += vloc[i] * a0;
-          d1 += vloc[i + 32] * a1;
-          d2 += vloc[i + 64] * a2;
-          d3 += vloc[i + 96] * a3;
-        }
-        for (; i < p; i += 32) d0 += vloc[i] * __ldcg(x + i);
-        double d = (d0 + d1) + (d2 + d3);
-        for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
-        f = tau * d;
-      }
-      double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-      int64_t i = j + lane;
-      for (; i + 96 < p; i += 128) {
-        double y0 = __ldcg(x + i), y1 = __ldcg(x + i + 32), y2 = __ldcg(x + i + 64),
-               y3 = __ldcg(x + i + 96);
-        if (tau != 0.0) {
-          y0 = y0 - f * vloc[i];
-          y1 = y1 - f * vloc[i + 32];
-          y2 = y2 - f * vloc[i + 64];
-          y3 = y3 - f * vloc[i + 96];
-          x[i] = y0;
-          x[i + 32] = y1;
-          x[i + 64] = y2;
-          x[i + 96] = y3;
-        }
-        s0 += (i > j) ? y0 * y0 : 0.0;  // only the row i = j (lane 0, first block) is excluded
-        s1 += y1 * y1;
-        s2 += y2 * y2;
-        s3 += y3 * y3;
-      }
-      for (; i < p; i += 32) {
-        double y = __ldcg(x + i);
-        if (tau != 0.0) {
-          y = y - f * vloc[i];
-          x[i] = y;
-        }
-        if (i > j) s0 += y * y;
-      }
-      double s = (s0 + s1) + (s2 + s3);
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      const int64_t len = p - j;
+      double s;
+      if (len <= 4 * 32) s = qr_col_apply_reg<4>(x, vloc, j, p, tau, lane);
+      else if (len <= 8 * 32) s = qr_col_apply_reg<8>(x, vloc, j, p, tau, lane);
+      else if (len <= 24 * 32) s = qr_col_apply_reg<24>(x, vloc, j, p, tau, lane);
+      else s = qr_col_apply_l2(x, vloc, j, p, tau, lane);
       if (lane == 0) w.norm2[col] = s;
     }
     __syncthreads();
