@@ -467,6 +467,43 @@ static_assert((size_t)10 * 256 * 8 * sizeof(double) >= kBatchMaxPanelBytes &&
                   (size_t)40 * 256 * 2 * sizeof(double) >= kBatchMaxPanelBytes,
               "at each width, every core that fits the panel has at most panel_rows rows per thread");
 
+// Warp sums of PW values at once by a reduce-scatter butterfly: at each of the
+// first log2(PW) levels a lane keeps half of its values and adds its partner's
+// other half, then the single remaining value is summed over the lanes left;
+// PW - 1 + log2(32 / PW) shuffle-adds instead of 5 PW (the FP64 adds share the
+// narrow FP64 pipe with the solve's FMAs).  Every lane returns the warp total
+// of component scatter_component<PW>(lane).
+template <int PW>
+__device__ __forceinline__ double warp_sum_scatter(double (&v)[PW], int lane) {
+  int off = 16;
+#pragma unroll
+  for (int w = PW; w > 1; w >>= 1) {
+    const int h = w >> 1;
+    const bool hi = (lane & off) != 0;
+#pragma unroll
+    for (int k = 0; k < h; ++k) {
+      const double keep = hi ? v[h + k] : v[k];
+      const double give = hi ? v[k] : v[h + k];
+      v[k] = keep + __shfl_xor_sync(0xffffffffu, give, off);
+    }
+    off >>= 1;
+  }
+  double s = v[0];
+  for (; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  return s;
+}
+
+template <int PW>
+__device__ __forceinline__ int scatter_component(int lane) {
+  int c = 0, off = 16;
+#pragma unroll
+  for (int w = PW; w > 1; w >>= 1) {
+    if (lane & off) c += w >> 1;
+    off >>= 1;
+  }
+  return c;
+}
+
 template <int PW, int PR>
 __device__ void team_qr_solve_panel(const Team& tm, const QrWs& w, int64_t p, int64_t q, int64_t k,
                                     double* X, int64_t ldx, double* Zs, const double* rinv) {
@@ -513,12 +550,8 @@ __device__ void team_qr_solve_panel(const Team& tm, const QrWs& w, int64_t p, in
 #pragma unroll
         for (int c = 0; c < PW; ++c) acc[c] += vr[q] * Zs[c * p + i];
       }
-#pragma unroll
-      for (int c = 0; c < PW; ++c)
-        for (int o = 16; o > 0; o >>= 1) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o);
-      if (lane == 0)
-#pragma unroll
-        for (int c = 0; c < PW; ++c) s_red[wid][c] = acc[c];
+      const double tot = warp_sum_scatter<PW>(acc, lane);
+      if ((lane & (32 / PW - 1)) == 0) s_red[wid][scatter_component<PW>(lane)] = tot;
       __syncthreads();
       if (tid < PW) {
         double sum = 0.0;
