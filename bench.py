@@ -21,6 +21,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import re
 import os
 import subprocess
 import sys
@@ -34,10 +35,10 @@ sys.path.insert(0, ROOT)
 # summarised in profiles/; valid only while the kernel source is unchanged.
 # profiles/sketch_f64_simt_8000x4000.md: 259.5 MB read + 65.8 MB written at 8000 x 4000
 # (split-K 50); at 20000^2 (split-K 12) reads scale with m*n (3244 MB) and the partial
-# writes with ks*c*n at the measured write ratio (79 MB).  The fingerprint was moved
-# once since the capture, when host-side row-block launchers were appended to the file
-# (the kernel itself unchanged).
-TRAFFIC = {"sketch_simt.cu": {"sha1": "0bd2354edcfba92147d9d5b4c102a8c9a3373445",
+# writes with ks*c*n at the measured write ratio (79 MB).  The fingerprint is of the
+# file's code with // comments removed; it was moved once since the capture, when
+# host-side row-block launchers were appended to the file (the kernel unchanged).
+TRAFFIC = {"sketch_simt.cu": {"sha1": "31824a3eff0a3f330025c2a908a52893a001d576",
                               "bytes_per_launch_full": 3.323e9}}
 FP64_PEAK_TFLOPS = 1.25  # GB300 nominal FP64 rate (no FP64 entry in the measured peaks)
 HBM_GBS = 6685.5          # measured copy bandwidth of the GB300s (MEASURED_PEAKS.json)
@@ -195,7 +196,8 @@ class ClockSampler:
 
 def traffic_for_sketch():
     src = os.path.join(ROOT, "paper_2509_21963_gb300", "csrc", "sketch_simt.cu")
-    h = hashlib.sha1(open(src, "rb").read()).hexdigest()
+    code = re.sub(r"//[^\n]*", "", open(src).read())
+    h = hashlib.sha1(code.encode()).hexdigest()
     rec = TRAFFIC["sketch_simt.cu"]
     if rec["sha1"] == h and rec["bytes_per_launch_full"] is not None:
         return rec["bytes_per_launch_full"]
