@@ -214,9 +214,6 @@ __device__ void qr_local_best(const Team& tm, const QrWs& w, int64_t q, double* 
   if (threadIdx.x == 0) { slot[0] = bv; slot[1] = (double)bi; }
 }
 
-// Factorisation; false on a team barrier failure.  Every read of Mc goes
-// through L2 (__ldcg): the team's scratch is reused by jobs of other shapes,
-// so a line cached in this SM's L1 may hold another CTA's older data.
 // Apply H_j = I - tau v v^T (v = vloc, rows j..p-1) to one column x of the
 // trailing matrix with one warp, and return the column's squared norm over
 // rows j+1..p-1 (the next pivot search needs it).  Columns of at most 32 R rows
@@ -307,6 +304,9 @@ __device__ __forceinline__ double qr_col_apply_l2(double* x, const double* vloc,
   return s;
 }
 
+// Factorisation; false on a team barrier failure.  Every read of Mc goes
+// through L2 (__ldcg): the team's scratch is reused by jobs of other shapes,
+// so a line cached in this SM's L1 may hold another CTA's older data.
 __device__ bool team_qr_factor(const Team& tm, const QrWs& w, int64_t p, int64_t q, double* vloc) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int64_t kmax = p < q ? p : q;
@@ -328,10 +328,21 @@ __device__ bool team_qr_factor(const Team& tm, const QrWs& w, int64_t p, int64_t
 
   for (int64_t j = 0; j < kmax; ++j) {
     const double* slot = w.slots + (j & 1) * 2 * tm.T;
-    if (threadIdx.x < 32) {  // warp 0 reads the T candidates in parallel
+    if (threadIdx.x < 32) {  // warp 0 reads the T candidates, all loads in flight together
       double bv = -1.0;
       int64_t bi = -1;
-      for (int r = threadIdx.x; r < tm.T; r += 32) {
+      constexpr int kR = 8;
+      double cv[kR], ci[kR];
+#pragma unroll
+      for (int u = 0; u < kR; ++u) {
+        const int r = threadIdx.x + 32 * u;
+        cv[u] = r < tm.T ? __ldcg(slot + 2 * r) : -1.0;
+        ci[u] = r < tm.T ? __ldcg(slot + 2 * r + 1) : -1.0;
+      }
+#pragma unroll
+      for (int u = 0; u < kR; ++u)
+        if (better(cv[u], (int64_t)ci[u], bv, bi)) { bv = cv[u]; bi = (int64_t)ci[u]; }
+      for (int r = threadIdx.x + 32 * kR; r < tm.T; r += 32) {  // teams above 256 CTAs
         double v = __ldcg(slot + 2 * r);
         int64_t i = (int64_t)__ldcg(slot + 2 * r + 1);
         if (better(v, i, bv, bi)) { bv = v; bi = i; }

@@ -7,6 +7,8 @@
 
 #include "cur_internal.cuh"
 
+#include <climits>
+
 namespace cur {
 
 __device__ __forceinline__ void dev_set_err(DevStatus* st, int code) {
@@ -38,6 +40,60 @@ __device__ __forceinline__ bool bar_arrive_wait(GridBar* bar, unsigned n, DevSta
   }
   __threadfence();  // the other CTAs' writes before theirs
   return true;
+}
+
+// The best (largest value, then smallest index) of G per-CTA records written
+// before a barrier: slot g holds its value at slot[g * stride] and its index
+// (bit pattern of a long long) at slot[g * stride + 1].  Called by a whole
+// warp; each lane issues its loads (up to eight) together, so reading the
+// records costs one L2 round trip instead of one per 32 records.  Every lane
+// returns the winner and its record number; records with value -1 and index
+// LLONG_MAX stand for "no candidate", and when no record beats them the result
+// is {-1, LLONG_MAX, -1}.
+struct SlotWin {
+  double a;
+  long long i;
+  int g;
+};
+__device__ __forceinline__ SlotWin warp_slot_best(const double* slot, size_t stride, int G,
+                                                  int lane) {
+  constexpr int kR = 8;
+  double av[kR];
+  long long iv[kR];
+#pragma unroll
+  for (int k = 0; k < kR; ++k) {
+    const int g = lane + 32 * k;
+    av[k] = -1.0;
+    iv[k] = LLONG_MAX;
+    if (g < G) {
+      const double* s = slot + (size_t)g * stride;
+      av[k] = __ldcg(s);
+      iv[k] = __double_as_longlong(__ldcg(s + 1));
+    }
+  }
+  SlotWin c{-1.0, LLONG_MAX, -1};
+#pragma unroll
+  for (int k = 0; k < kR; ++k) {
+    const int g = lane + 32 * k;
+    if (g < G && (av[k] > c.a || (av[k] == c.a && iv[k] < c.i))) {
+      c.a = av[k];
+      c.i = iv[k];
+      c.g = g;
+    }
+  }
+  for (int g = lane + 32 * kR; g < G; g += 32) {  // grids above 256 CTAs
+    const double* s = slot + (size_t)g * stride;
+    const double a = __ldcg(s);
+    const long long i = __double_as_longlong(__ldcg(s + 1));
+    if (a > c.a || (a == c.a && i < c.i)) { c.a = a; c.i = i; c.g = g; }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const double oa = __shfl_xor_sync(0xffffffffu, c.a, o);
+    const long long oi = __shfl_xor_sync(0xffffffffu, c.i, o);
+    const int og = __shfl_xor_sync(0xffffffffu, c.g, o);
+    if (oa > c.a || (oa == c.a && oi < c.i)) { c.a = oa; c.i = oi; c.g = og; }
+  }
+  return c;
 }
 
 // Grid-wide barrier of a cooperative launch.  Returns true when every CTA

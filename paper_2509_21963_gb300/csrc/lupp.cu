@@ -90,21 +90,8 @@ __global__ void __launch_bounds__(kThreads) lupp_kernel(LuppParams p) {
     if (!grid_barrier(p.bar, p.st)) return;
     // 3. global winner (every CTA computes the same answer)
     if (wid == 0) {
-      Best c{-1.0, LLONG_MAX};
-      int ccta = -1;
-      for (int g = lane; g < G; g += 32) {
-        const double* s = slot + (size_t)g * stride;
-        double a = __ldcg(s);
-        long long i = __double_as_longlong(__ldcg(s + 1));
-        if (better(a, i, c)) { c.a = a; c.i = i; ccta = g; }
-      }
-      for (int o = 16; o > 0; o >>= 1) {
-        double oa = __shfl_down_sync(0xffffffffu, c.a, o);
-        long long oi = __shfl_down_sync(0xffffffffu, c.i, o);
-        int oc = __shfl_down_sync(0xffffffffu, ccta, o);
-        if (better(oa, oi, c)) { c.a = oa; c.i = oi; ccta = oc; }
-      }
-      if (lane == 0) { s_win = c; s_wcta = ccta; }
+      const SlotWin c = warp_slot_best(slot, (size_t)stride, G, lane);
+      if (lane == 0) { s_win = Best{c.a, c.i}; s_wcta = c.g; }
     }
     __syncthreads();
     Best w = s_win;
@@ -205,21 +192,8 @@ __global__ void __launch_bounds__(kThreads) lupp_blocked_kernel(LuppParams p, in
       __threadfence();
       if (!grid_barrier(p.bar, p.st)) return;
       if (wid == 0) {
-        Best c{-1.0, LLONG_MAX};
-        int ccta = -1;
-        for (int g = lane; g < G; g += 32) {
-          const double* sg = slot + (size_t)g * stride;
-          const double a = __ldcg(sg);
-          const long long i = __double_as_longlong(__ldcg(sg + 1));
-          if (better(a, i, c)) { c.a = a; c.i = i; ccta = g; }
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-          double oa = __shfl_down_sync(0xffffffffu, c.a, o);
-          long long oi = __shfl_down_sync(0xffffffffu, c.i, o);
-          int oc = __shfl_down_sync(0xffffffffu, ccta, o);
-          if (better(oa, oi, c)) { c.a = oa; c.i = oi; ccta = oc; }
-        }
-        if (lane == 0) { s_win = c; s_wcta = ccta; }
+        const SlotWin c = warp_slot_best(slot, (size_t)stride, G, lane);
+        if (lane == 0) { s_win = Best{c.a, c.i}; s_wcta = c.g; }
       }
       __syncthreads();
       const Best w = s_win;
@@ -333,21 +307,8 @@ __global__ void __launch_bounds__(kThreads) lupp_smem_kernel(LuppParams p, int p
     __threadfence();
     if (!grid_barrier(p.bar, p.st)) return;
     if (wid == 0) {
-      Best c{-1.0, LLONG_MAX};
-      int ccta = -1;
-      for (int g = lane; g < G; g += 32) {
-        const double* s = slot + (size_t)g * stride;
-        double a = __ldcg(s);
-        long long i = __double_as_longlong(__ldcg(s + 1));
-        if (better(a, i, c)) { c.a = a; c.i = i; ccta = g; }
-      }
-      for (int o = 16; o > 0; o >>= 1) {
-        double oa = __shfl_down_sync(0xffffffffu, c.a, o);
-        long long oi = __shfl_down_sync(0xffffffffu, c.i, o);
-        int oc = __shfl_down_sync(0xffffffffu, ccta, o);
-        if (better(oa, oi, c)) { c.a = oa; c.i = oi; ccta = oc; }
-      }
-      if (lane == 0) { s_win = c; s_wcta = ccta; }
+      const SlotWin c = warp_slot_best(slot, (size_t)stride, G, lane);
+      if (lane == 0) { s_win = Best{c.a, c.i}; s_wcta = c.g; }
     }
     __syncthreads();
     Best w = s_win;

@@ -83,14 +83,9 @@ __global__ void __launch_bounds__(kThreads) qrcp_factor_kernel(QrcpParams P) {
     __threadfence();
     if (!grid_barrier(P.w.bar, P.st)) return;
     // B. global pivot (largest norm, smallest index) and its reflector
-    if (tid == 0) {
-      double a = -1.0; long long ii = LLONG_MAX;
-      for (int g = 0; g < G; ++g) {
-        double ga = __ldcg(slot + 2 * g);
-        long long gi = __double_as_longlong(__ldcg(slot + 2 * g + 1));
-        if (ga > a || (ga == a && gi < ii)) { a = ga; ii = gi; }
-      }
-      s_nrm2 = a; s_jp = ii;
+    if (wid == 0) {
+      const SlotWin c = warp_slot_best(slot, 2, G, lane);
+      if (lane == 0) { s_nrm2 = c.a; s_jp = c.i; }
     }
     __syncthreads();
     const long long jp = s_jp;
@@ -237,20 +232,8 @@ __global__ void __launch_bounds__(kThreads) qrcp_factor_smem_kernel(QrcpParams P
     __threadfence();
     if (!grid_barrier(P.w.bar, P.st)) return;
     if (wid == 0) {
-      double a = -1.0; long long ii = LLONG_MAX; int wc = -1;
-      for (int g = lane; g < G; g += 32) {
-        const double* sg = slot + (size_t)g * stride;
-        double ga = __ldcg(sg);
-        long long gi = __double_as_longlong(__ldcg(sg + 1));
-        if (ga > a || (ga == a && gi < ii)) { a = ga; ii = gi; wc = g; }
-      }
-      for (int o = 16; o > 0; o >>= 1) {
-        double oa = __shfl_down_sync(0xffffffffu, a, o);
-        long long oi = __shfl_down_sync(0xffffffffu, ii, o);
-        int oc = __shfl_down_sync(0xffffffffu, wc, o);
-        if (oa > a || (oa == a && oi < ii)) { a = oa; ii = oi; wc = oc; }
-      }
-      if (lane == 0) { s_nrm2 = a; s_jp = ii; s_wcta = wc; }
+      const SlotWin c = warp_slot_best(slot, (size_t)stride, G, lane);
+      if (lane == 0) { s_nrm2 = c.a; s_jp = c.i; s_wcta = c.g; }
     }
     __syncthreads();
     const long long jp = s_jp;
