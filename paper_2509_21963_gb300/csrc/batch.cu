@@ -17,7 +17,8 @@
 //     Rt_k = A(I_k,:) - L(I_k,:) Rt, S -= (S(:,J_k) N^+) Rt_k, ||S||_F
 //                                   team-partitioned over columns   | barrier
 //   U = A(I,J)^+                    team pivoted QR (one barrier per
-//                                   reflector) + per-column solve
+//                                   reflector) + shared-memory panel solve
+//                                   (8, 4 or 2 right-hand sides per panel)
 //
 // Redundant small steps replace barriers: every CTA of a team computes the
 // same pivots from the same data with the same code and reduction order, so

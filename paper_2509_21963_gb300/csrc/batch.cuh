@@ -196,7 +196,9 @@ struct BatchParams {
 constexpr size_t kBatchMaxPanelBytes = 160 * 1024;
 // Co-resident CTAs of the batch kernel (256 threads) with `dyn_smem` bytes.
 int batch_max_ctas(const LaunchEnv& env, int threads, bool a_f32, size_t dyn_smem);
-// Panel bytes of the core solve for cores up to rmax (0 when it does not fit).
+// Dynamic shared memory of the core solve for cores up to rmax: the widest
+// panel (8, 4 or 2 columns of rmax doubles) that fits kBatchMaxPanelBytes with
+// 256 threads; 0 when none fits (the per-column solve then runs).
 size_t batch_panel_bytes(int64_t rmax);
 
 // Whole-GPU pivoted-QR generalised inverse (the team QR of the batch kernel
