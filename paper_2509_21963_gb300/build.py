@@ -30,7 +30,8 @@ def _nvcc() -> str:
 def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(OUT, exist_ok=True)
     sources = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
-    headers = glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(INCLUDE, "*.h"))
+    headers = (glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h")) +
+               glob.glob(os.path.join(INCLUDE, "*.h")))
     newest_header = max((os.path.getmtime(h) for h in headers), default=0.0)
     nvcc = _nvcc()
     jobs = []

@@ -19,6 +19,7 @@
 #include "../../include/cur.h"
 #include "../../include/cur_batch.h"
 #include "../../include/cur_server.h"
+#include "arena.h"
 #include "batch.cuh"
 #include "ctx.cuh"
 
@@ -32,49 +33,6 @@ double now_ms() {
 }
 
 size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
-
-// First-fit allocator over one device range with coalescing on release.
-struct Arena {
-  size_t cap = 0, used = 0, peak = 0;
-  std::map<size_t, size_t> free_;  // offset -> bytes
-  void init(size_t c) {
-    cap = c;
-    used = peak = 0;
-    free_.clear();
-    if (c) free_[0] = c;
-  }
-  bool alloc(size_t bytes, size_t* off) {
-    bytes = al256(bytes ? bytes : 1);
-    for (auto it = free_.begin(); it != free_.end(); ++it) {
-      if (it->second < bytes) continue;
-      *off = it->first;
-      const size_t rest = it->second - bytes, noff = it->first + bytes;
-      free_.erase(it);
-      if (rest) free_[noff] = rest;
-      used += bytes;
-      peak = std::max(peak, used);
-      return true;
-    }
-    return false;
-  }
-  void release(size_t off, size_t bytes) {
-    bytes = al256(bytes ? bytes : 1);
-    used -= std::min(used, bytes);
-    auto it = free_.emplace(off, bytes).first;
-    auto nx = std::next(it);
-    if (nx != free_.end() && it->first + it->second == nx->first) {
-      it->second += nx->second;
-      free_.erase(nx);
-    }
-    if (it != free_.begin()) {
-      auto pv = std::prev(it);
-      if (pv->first + pv->second == it->first) {
-        pv->second += it->second;
-        free_.erase(it);
-      }
-    }
-  }
-};
 
 enum ReqState { kPending = 0, kAdmitted = 1, kRunning = 2, kDone = 3 };
 
