@@ -6,9 +6,11 @@ with the CUDA library under ``paper_2509_21963_gb300/``: the arithmetic lives in
 ``cur_oracle.c`` (plain C, compiled with ``-ffp-contract=off``); this module only
 compiles it and marshals numpy arrays through ctypes.
 
-Parity status: every function is pinned by ``tests/test_oracle_*.py`` (see the
-header of ``cur_oracle.c`` for which pin covers which function).  None is
-"parity unpinned".
+Parity status: each function is pinned by ``tests/test_oracle_pins.py`` or
+``tests/test_oracle_precision_pins.py``; the header of ``cur_oracle.c`` lists
+which pin covers which function.  The precision-form functions (the 8-bit
+sketch, the fixed points, the exact fixed-point sketch) are this project's own
+definitions, pinned to the error bounds and exact rational values they state.
 """
 from __future__ import annotations
 
@@ -78,6 +80,12 @@ def lib():
         L.cur_oracle_run_sketched.restype = ctypes.c_int
         L.cur_oracle_gaussian_sketch_q8.argtypes = [u64, i64, i64, vp]
         L.cur_oracle_fixed_point.argtypes = [vp, i64, i64, i64, ctypes.c_int, vp]
+        L.cur_oracle_quantize_q8.argtypes = [vp, i64, vp]
+        L.cur_oracle_fixed_point_digits.argtypes = [dbl, ctypes.c_int, ctypes.c_int, vp]
+        L.cur_oracle_sketch_fx.argtypes = [vp, i64, vp, i64, i64, i64, ctypes.c_int, vp]
+        L.cur_oracle_run_y.argtypes = [vp, i64, i64, i64, dbl, i64, i64, vp, i64,
+                                       ctypes.c_int, ctypes.POINTER(_Out)]
+        L.cur_oracle_run_y.restype = ctypes.c_int
         L.cur_oracle_risk_threshold.argtypes = [dbl, dbl, dbl, dbl]
         L.cur_oracle_risk_threshold.restype = dbl
     return _lib
@@ -240,9 +248,62 @@ def gaussian_sketch_q8(seed: int, c: int, m: int) -> np.ndarray:
     return G
 
 
+def quantize_q8(G: np.ndarray) -> np.ndarray:
+    """clamp(rint(16 G), -127, 127) of a given sketch (ties to even)."""
+    G = _f64(G)
+    out = np.empty_like(G)
+    lib().cur_oracle_quantize_q8(_p(G), G.size, _p(out))
+    return out
+
+
 def fixed_point(A: np.ndarray, S: int) -> np.ndarray:
     A = _f64(A)
     m, n = A.shape
     out = np.empty_like(A)
     lib().cur_oracle_fixed_point(_p(A), m, n, n, S, _p(out))
     return out
+
+
+def fixed_point_digits(x: float, E: int, S: int) -> np.ndarray:
+    """The S digits of fix_S(x) at column scale 2^E, least significant first."""
+    d = np.zeros(S, dtype=np.float64)
+    lib().cur_oracle_fixed_point_digits(float(x), int(E), int(S), _p(d))
+    return d
+
+
+# The tensor-core FP64 form of the sketch: 52-bit fixed point per column.
+FX_BITS = 52
+
+
+def sketch_fx(Gq: np.ndarray, A: np.ndarray, Q: int = FX_BITS) -> np.ndarray:
+    """Y = RN(Gq trunc(A 2^(Q-E_j))) 2^(E_j-Q), the integer sum exact."""
+    Gq, A = _f64(Gq), _f64(A)
+    c, m = Gq.shape
+    m2, n = A.shape
+    assert m == m2
+    Y = np.empty((c, n), dtype=np.float64)
+    lib().cur_oracle_sketch_fx(_p(Gq), c, _p(A), m, n, n, Q, _p(Y))
+    return Y
+
+
+def run_y(A: np.ndarray, tol: float, b: int, c: int, Y: np.ndarray, max_rank: int = 0,
+          mode: int = 1, want_S: bool = False) -> Result:
+    """Algorithm 1's loop on A from the given initial sketch Y (c x n)."""
+    A, Y = _f64(A), _f64(Y)
+    m, n = A.shape
+    assert Y.shape == (c, n)
+    R = min(m, n) if max_rank <= 0 else min(max_rank, m, n)
+    o, bufs = _alloc_out(m, n, c, b, R, want_S)
+    rc = lib().cur_oracle_run_y(_p(A), m, n, n, tol, b, c, _p(Y), R, mode, ctypes.byref(o))
+    if rc != 0:
+        raise ValueError("invalid arguments")
+    return _result(o, bufs)
+
+
+def run_fx(A: np.ndarray, tol: float, b: int, c: int, seed: int = 0, max_rank: int = 0,
+           mode: int = 1, want_S: bool = False) -> Result:
+    """The FP64 tensor-core form: the 8-bit sketch G_q of the seed and the exact
+    52-bit fixed-point sketch, then Algorithm 1's loop in FP64."""
+    A = _f64(A)
+    Gq = gaussian_sketch_q8(seed, c, A.shape[0])
+    return run_y(A, tol, b, c, sketch_fx(Gq, A), max_rank=max_rank, mode=mode, want_S=want_S)

@@ -19,6 +19,21 @@
  *                      interpolation S(:,J)=0, S(I,:)=0 (Sec. 3.2.2),
  *                      Theorem 2 brute force on tiny matrices (Sec. 4.2),
  *                      estimator vs truth (Sec. 3.3), naive loop (Sec. 3.1)
+ *   run_sketched     - bit-equal to run when the sketched matrix is A
+ *   run_y            - bit-equal to run started from run's own sketch
+ *   true_error       - numpy norm(A - C U R) / norm(A)
+ *   gaussian_sketch_q8, quantize_q8
+ *                    - integer, |q| <= 127, |q - 16 g| <= 1/2 inside the clamp,
+ *                      the clamp and ties-to-even on crafted values, moments
+ *   fixed_point, fixed_point_digits
+ *                    - |fix_S(x) - x| <= 2^(E-8S-1); one rounding half-to-even
+ *                      of x 2^(8S-E) in exact rational arithmetic; grid values
+ *                      unchanged; E = frexp of the column max; digits integer,
+ *                      |d| <= 256, reassembling fix_S
+ *   sketch_fx        - exact rational evaluation with Python integers; the
+ *                      truncation error bound; integer data equal to an int64
+ *                      matmul; truncation toward zero on a crafted entry
+ * (tests/test_oracle_pins.py, tests/test_oracle_precision_pins.py).
  */
 #include "cur_oracle.h"
 
@@ -361,8 +376,6 @@ int cur_oracle_run_sketched(const double *A, const double *Asketch, int64_t m, i
                             int64_t lda, double tol, int64_t b, int64_t c, uint64_t seed,
                             const double *Gin, int64_t max_rank, int mode,
                             cur_oracle_out *out) {
-  int64_t mn = m < n ? m : n;
-  if (max_rank <= 0 || max_rank > mn) max_rank = mn;
   out->rank = 0; out->iters = 0; out->rho = 1.0; out->status = 0;
   if (m <= 0 || n <= 0 || b <= 0 || c < b || !(tol > 0.0)) { out->status = -1; return -1; }
 
@@ -371,10 +384,25 @@ int cur_oracle_run_sketched(const double *A, const double *Asketch, int64_t m, i
   if (Gin) memcpy(G, Gin, sizeof(double) * (size_t)(c * m));
   else cur_oracle_gaussian_sketch(seed, c, m, G);
 
-  /* initial sketch S_0 = G A, rho_0 = ||S_0|| / ||G A|| = 1 */
+  /* initial sketch S_0 = G A */
   double *Y = (double *)malloc(sizeof(double) * (size_t)(c * n));
   if (Asketch) cur_oracle_sketch(G, c, Asketch, m, n, n, Y);
   else cur_oracle_sketch(G, c, A, m, n, lda, Y);
+  free(G);
+  int rc = cur_oracle_run_y(A, m, n, lda, tol, b, c, Y, max_rank, mode, out);
+  free(Y);
+  return rc;
+}
+
+int cur_oracle_run_y(const double *A, int64_t m, int64_t n, int64_t lda, double tol,
+                     int64_t b, int64_t c, const double *Y, int64_t max_rank, int mode,
+                     cur_oracle_out *out) {
+  int64_t mn = m < n ? m : n;
+  if (max_rank <= 0 || max_rank > mn) max_rank = mn;
+  out->rank = 0; out->iters = 0; out->rho = 1.0; out->status = 0;
+  if (m <= 0 || n <= 0 || b <= 0 || c < b || !(tol > 0.0)) { out->status = -1; return -1; }
+
+  /* rho_0 = ||S_0|| / ||G A|| = 1 */
   double nY = frob(Y, c * n);
   out->normY = nY;
   out->maxabsY = maxabs(Y, c * n);
@@ -383,7 +411,7 @@ int cur_oracle_run_sketched(const double *A, const double *Asketch, int64_t m, i
   if (nY == 0.0) { /* G A = 0: nothing to approximate (reading of 0/0) */
     out->rho = 0.0;
     if (out->S_final) memcpy(out->S_final, S, sizeof(double) * (size_t)(c * n));
-    free(S); free(Y); free(G);
+    free(S);
     return 0;
   }
   double rho = 1.0;
@@ -485,7 +513,7 @@ int cur_oracle_run_sketched(const double *A, const double *Asketch, int64_t m, i
     for (int64_t a = 0; a < r * r; ++a) out->U[a] = U[a];
   if (out->S_final) memcpy(out->S_final, S, sizeof(double) * (size_t)(c * n));
   free(Rt); free(L); free(T1); free(Np); free(N); free(Srow); free(ST);
-  free(excl_row); free(excl_col); free(U); free(S); free(Y); free(G);
+  free(excl_row); free(excl_col); free(U); free(S);
   return 0;
 }
 
@@ -592,11 +620,16 @@ double cur_oracle_risk_threshold(double eps, double delta, double alpha, double 
  * sketch (the scale 16 cancels in rho and in the LUPP choices). */
 void cur_oracle_gaussian_sketch_q8(uint64_t seed, int64_t c, int64_t m, double *G) {
   cur_oracle_gaussian_sketch(seed, c, m, G);
-  for (int64_t t = 0; t < c * m; ++t) {
+  cur_oracle_quantize_q8(G, c * m, G);
+}
+
+/* out[t] = clamp(rint(16 G[t]), -127, 127) (ties to even); out may alias G. */
+void cur_oracle_quantize_q8(const double *G, int64_t len, double *out) {
+  for (int64_t t = 0; t < len; ++t) {
     double q = rint(16.0 * G[t]);
     if (q > 127.0) q = 127.0;
     if (q < -127.0) q = -127.0;
-    G[t] = q;
+    out[t] = q;
   }
 }
 
@@ -623,4 +656,53 @@ void cur_oracle_fixed_point(const double *A, int64_t m, int64_t n, int64_t lda, 
       Afix[k * n + j] = ldexp(v, E - 8 * S);
     }
   }
+}
+
+/* The S digits of fix_S(x) for a column scale 2^E (the recursion above):
+ * d[S-1] = rint(x 2^(8-E)), then d = rint(256 r) of each remainder r, most
+ * significant first in d[S-1] ... d[0]. */
+void cur_oracle_fixed_point_digits(double x, int E, int S, double *d) {
+  double y = ldexp(x, 8 - E);
+  for (int s = S - 1; s >= 0; --s) {
+    d[s] = rint(y);
+    y = (y - d[s]) * 256.0;
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Exact fixed-point sketch of the FP64 tensor-core form.                   */
+/* ------------------------------------------------------------------------ */
+/* Column j gets E_j with max_k |A(k,j)| < 2^E_j (frexp of the column max; 0
+ * for a zero column).  Every entry is truncated toward zero onto the grid
+ * 2^(E_j - Q): X(k,j) = trunc(A(k,j) 2^(Q - E_j)), an integer with |X| < 2^Q.
+ * With Gq integer-valued, the integer sum V(i,j) = sum_k Gq(i,k) X(k,j) is
+ * formed exactly (128-bit) and rounded once to FP64 (to nearest, ties to
+ * even), then scaled: Y(i,j) = RN(V) 2^(E_j - Q) (a power-of-two scaling,
+ * itself rounded only if the result is subnormal).  A column holding Inf or
+ * NaN gives NaN in every row of Y.  Requires Q <= 62 and |Gq| < 2^31. */
+void cur_oracle_sketch_fx(const double *Gq, int64_t c, const double *A, int64_t m,
+                          int64_t n, int64_t lda, int Q, double *Y) {
+  int64_t *X = (int64_t *)malloc(sizeof(int64_t) * (size_t)(m > 0 ? m : 1));
+  for (int64_t j = 0; j < n; ++j) {
+    double mx = 0.0;
+    int finite = 1;
+    for (int64_t k = 0; k < m; ++k) {
+      double a = A[k * lda + j];
+      if (!isfinite(a)) finite = 0;
+      else if (fabs(a) > mx) mx = fabs(a);
+    }
+    if (!finite) {
+      for (int64_t i = 0; i < c; ++i) Y[i * n + j] = NAN;
+      continue;
+    }
+    int E = 0;
+    if (mx > 0.0) frexp(mx, &E); /* mx = f 2^E, f in [0.5, 1): mx < 2^E */
+    for (int64_t k = 0; k < m; ++k) X[k] = (int64_t)trunc(ldexp(A[k * lda + j], Q - E));
+    for (int64_t i = 0; i < c; ++i) {
+      __int128 v = 0;
+      for (int64_t k = 0; k < m; ++k) v += (__int128)(int64_t)Gq[i * m + k] * (__int128)X[k];
+      Y[i * n + j] = ldexp((double)v, E - Q);
+    }
+  }
+  free(X);
 }

@@ -109,12 +109,33 @@ int cur_oracle_run_sketched(const double *A, const double *Asketch, int64_t m, i
                             const double *G, int64_t max_rank, int mode,
                             cur_oracle_out *out);
 
+/* The loop of cur_oracle_run (Algorithm 1 after its initial sketch) started
+ * from a given initial sketch Y = S_0^col (c x n, stride n) of A. */
+int cur_oracle_run_y(const double *A, int64_t m, int64_t n, int64_t lda, double tol,
+                     int64_t b, int64_t c, const double *Y, int64_t max_rank, int mode,
+                     cur_oracle_out *out);
+
 /* 8-bit Gaussian sketch: clamp(rint(16 Z), -127, 127), Z as above. */
 void cur_oracle_gaussian_sketch_q8(uint64_t seed, int64_t c, int64_t m, double *G);
+
+/* The same rounding of a given sketch: out = clamp(rint(16 G), -127, 127),
+ * ties to even (the precision forms' reading of an explicit sketch). */
+void cur_oracle_quantize_q8(const double *G, int64_t len, double *out);
 
 /* S-digit base-256 fixed point of A per column (see cur_oracle.c). */
 void cur_oracle_fixed_point(const double *A, int64_t m, int64_t n, int64_t lda, int S,
                             double *Afix);
+
+/* The S base-256 digits of fix_S(x) at column scale 2^E, d[S-1] the most
+ * significant (see cur_oracle.c). */
+void cur_oracle_fixed_point_digits(double x, int E, int S, double *d);
+
+/* Exact fixed-point sketch of the FP64 tensor-core form: per column the scale
+ * 2^E_j > max |A(:,j)|, X = trunc(A 2^(Q - E_j)) (integers), and
+ * Y(i,j) = RN(sum_k Gq(i,k) X(k,j)) 2^(E_j - Q) with the integer sum exact
+ * and rounded once.  Gq c x m integer-valued; A m x n (stride lda); Y c x n. */
+void cur_oracle_sketch_fx(const double *Gq, int64_t c, const double *A, int64_t m,
+                          int64_t n, int64_t lda, int Q, double *Y);
 
 /* The naive loop of Sec. 3.1: identical selections, but the residual
  * S = A - C U R is formed in full every iteration and sketched afresh
