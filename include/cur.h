@@ -62,8 +62,15 @@ typedef enum {
   CUR_SKETCH_BF16 = 1,  /* S = 1: one BF16 digit per entry (2^-8 of column max)  */
   CUR_SKETCH_BF16X2 = 2,/* S = 2: hi + lo digits (2^-16)                         */
   CUR_SKETCH_BF16X3 = 3,/* S = 3: hi + mid + lo digits (2^-24)                   */
-  CUR_SKETCH_BF16X4 = 4 /* S = 4: four digits (2^-32; exact for FP32 entries
+  CUR_SKETCH_BF16X4 = 4,/* S = 4: four digits (2^-32; exact for FP32 entries
                            within 2^-8 of their column's largest)               */
+  CUR_SKETCH_F64_TC = 5 /* FP64 form on the tensor cores: FP64 A (lda % 2 == 0,
+                           16-byte aligned base), the 8-bit sketch G_q above and
+                           the 52-bit fixed point of each column:
+                           Y = RN(G_q trunc(A 2^(52-E_j))) 2^(E_j-52), the
+                           integer sum exact and rounded once to FP64, so
+                           |Y - G_q A| <= 2^(E_j-52) sum_k |G_q| + ulp(Y)/2.
+                           Any c.  See cur_step_sketch_fx.                      */
 } cur_sketch_mode;
 
 typedef struct cur_opts {

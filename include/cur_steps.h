@@ -44,6 +44,24 @@ int cur_step_sketch(cur_ctx *ctx, const double *G, int64_t c, const void *A,
 int cur_step_sketch_q(cur_ctx *ctx, const double *G, int64_t c, const float *A, int64_t m,
                       int64_t n, int64_t lda, int digits, double *Y, double *sumsq_host);
 
+/* FP64 form of the initial sketch S_0^col = Y = G A (Algorithm 1) on the
+ * tensor cores.  Sec. 3.4 counts this pass among the method's primary costs.
+ * GB300's FP64 pipe cannot run it at the HBM rate; this form makes every
+ * product exact on BF16 tensor cores instead:
+ *   G_q = clamp(rint(16 G), -127, 127)   (8-bit integers; G c x m FP64, stride m)
+ *   E_j: max_k |A(k,j)| < 2^E_j          (frexp of the column max, 0 for a zero column)
+ *   X(k,j) = trunc(A(k,j) 2^(52-E_j))    (52-bit fixed point, |X| < 2^52)
+ *   Y(i,j) = RN(sum_k G_q(i,k) X(k,j)) 2^(E_j-52)   (the integer sum exact,
+ *                                        rounded once to nearest-even)
+ * so |Y - G_q A| <= 2^(E_j-52) sum_k |G_q(i,k)| + ulp(Y)/2.
+ *   A  m x n FP64, row stride lda (lda % 2 == 0), base 16-byte aligned;
+ *   Y  c x n FP64 output (stride n), any c >= 1 (one pass of A per 64 rows of G);
+ *   sumsq_host (may be NULL) receives ||Y||_F^2 (synchronises the stream).
+ *   A column holding Inf or NaN turns that column of Y into NaN.
+ * CUR_EINVAL for bad sizes, odd lda or a misaligned A. */
+int cur_step_sketch_fx(cur_ctx *ctx, const double *G, int64_t c, const double *A, int64_t m,
+                       int64_t n, int64_t lda, double *Y, double *sumsq_host);
+
 /* LUPP index selection (Sec. 3.2.1, 3.2.2): the candidates are the ncand
  * columns of X (nr x ncand, stride ldx, FP64; read only).  Step t picks the
  * eligible candidate with the largest |W[t, i]| of the running Schur

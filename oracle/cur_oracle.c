@@ -679,7 +679,8 @@ void cur_oracle_fixed_point_digits(double x, int E, int S, double *d) {
  * formed exactly (128-bit) and rounded once to FP64 (to nearest, ties to
  * even), then scaled: Y(i,j) = RN(V) 2^(E_j - Q) (a power-of-two scaling,
  * itself rounded only if the result is subnormal).  A column holding Inf or
- * NaN gives NaN in every row of Y.  Requires Q <= 62 and |Gq| < 2^31. */
+ * NaN gives NaN in every row of Y.  Requires Q <= 52 and |Gq| <= 1024 (every
+ * product then fits an int64; the sum is taken in 128 bits). */
 void cur_oracle_sketch_fx(const double *Gq, int64_t c, const double *A, int64_t m,
                           int64_t n, int64_t lda, int Q, double *Y) {
   int64_t *X = (int64_t *)malloc(sizeof(int64_t) * (size_t)(m > 0 ? m : 1));
@@ -700,7 +701,7 @@ void cur_oracle_sketch_fx(const double *Gq, int64_t c, const double *A, int64_t 
     for (int64_t k = 0; k < m; ++k) X[k] = (int64_t)trunc(ldexp(A[k * lda + j], Q - E));
     for (int64_t i = 0; i < c; ++i) {
       __int128 v = 0;
-      for (int64_t k = 0; k < m; ++k) v += (__int128)(int64_t)Gq[i * m + k] * (__int128)X[k];
+      for (int64_t k = 0; k < m; ++k) v += (__int128)((int64_t)Gq[i * m + k] * X[k]);
       Y[i * n + j] = ldexp((double)v, E - Q);
     }
   }

@@ -26,6 +26,7 @@ CUR_OK, CUR_EINVAL, CUR_ENONFINITE, CUR_ENOMEM, CUR_EBUDGET, CUR_ECUDA, CUR_ETIM
     CUR_TOL_UNREACHED = range(8)
 CUR_F64, CUR_F32 = 0, 1
 CUR_SKETCH_F64, CUR_SKETCH_BF16, CUR_SKETCH_BF16X2, CUR_SKETCH_BF16X3, CUR_SKETCH_BF16X4 = 0, 1, 2, 3, 4
+CUR_SKETCH_F64_TC = 5
 PHASES = ("gaussian", "sketch", "lupp_col", "row_res", "lupp_row", "factors", "col_res", "core")
 
 _STATUS_NAMES = {0: "CUR_OK", 1: "CUR_EINVAL", 2: "CUR_ENONFINITE", 3: "CUR_ENOMEM",
@@ -89,6 +90,7 @@ _SIGNATURES = {
     "cur_step_gaussian": (_int, [_vp, _u64, _i64, _i64, _vp]),
     "cur_step_sketch": (_int, [_vp, _vp, _i64, _vp, _i64, _i64, _i64, _int, _vp, _vp]),
     "cur_step_sketch_q": (_int, [_vp, _vp, _i64, _vp, _i64, _i64, _i64, _int, _vp, _vp]),
+    "cur_step_sketch_fx": (_int, [_vp, _vp, _i64, _vp, _i64, _i64, _i64, _vp, _vp]),
     "cur_step_lupp": (_int, [_vp, _vp, _i64, _i64, _i64, _i64, _vp, _vp]),
     "cur_step_pinv": (_int, [_vp, _vp, _i64, _i64, _i64, _dbl, _vp, _vp]),
     "cur_step_lupp_noalloc": (_int, [_int, _vp, _vp, _i64, _i64, _i64, _i64, _vp, _vp,
@@ -304,6 +306,17 @@ class Context:
         _check(self.ptr, lib().cur_step_sketch_q(self.ptr, _vp(G.data_ptr()), c, _vp(A.data_ptr()), m,
                                                  n, A.stride(0), int(digits), _vp(Y.data_ptr()),
                                                  ctypes.byref(ss)))
+        return Y, ss.value
+
+    def sketch_fx(self, G, A):
+        """FP64 tensor-core sketch Y = RN(G_q trunc(A 2^(52-E))) 2^(E-52) (A: CUDA float64)."""
+        import torch
+        c, m = G.shape
+        n = A.shape[1]
+        Y = torch.empty(c, n, dtype=torch.float64, device=A.device)
+        ss = ctypes.c_double()
+        _check(self.ptr, lib().cur_step_sketch_fx(self.ptr, _vp(G.data_ptr()), c, _vp(A.data_ptr()), m,
+                                                  n, A.stride(0), _vp(Y.data_ptr()), ctypes.byref(ss)))
         return Y, ss.value
 
     def lupp(self, X, steps: int, mask=None):

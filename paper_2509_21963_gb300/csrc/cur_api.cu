@@ -346,6 +346,28 @@ int sketch_q(cur_ctx* ctx, int S, const double* G, int64_t c, const float* A, in
   return CUR_OK;
 }
 
+// FP64 form on the tensor cores: Y = RN(G_q trunc(A 2^(52-E_j))) 2^(E_j-52),
+// ||Y||^2 into scalar[slot].
+int sketch_fx(cur_ctx* ctx, const double* G, int64_t c, const double* A, int64_t m, int64_t n,
+              int64_t lda, double* Y, int slot, BufId parts_id, BufId scratch_id) {
+  LaunchEnv env = env_of(ctx);
+  TRY(ensure(ctx, scratch_id, sketch_fx_scratch_bytes(c, m, n)));
+  TRY(ensure(ctx, parts_id, sizeof(double) * (size_t)sketch_fx_max_parts(c, n)));
+  int64_t nparts = 0;
+  CK(launch_sketch_fx(env, G, c, A, lda, m, n, ctx->buf[scratch_id].p, Y,
+                      bp<double>(ctx, parts_id), &nparts, &dstat(ctx)->err));
+  ctx->launches += 4 + (c + 63) / 64;
+  TRY(sum_parts(ctx, bp<double>(ctx, parts_id), nparts, &dstat(ctx)->scalar[slot]));
+  return CUR_OK;
+}
+
+int check_fx_form(cur_ctx* ctx, const void* A, int64_t lda, int dtype) {
+  if (dtype != CUR_F64) return fail(ctx, CUR_EINVAL, "the FP64 tensor-core sketch needs FP64 A");
+  if (lda % 2 != 0 || (reinterpret_cast<uintptr_t>(A) & 15) != 0)
+    return fail(ctx, CUR_EINVAL, "the FP64 tensor-core sketch needs lda %% 2 == 0 and a 16-byte aligned A");
+  return CUR_OK;
+}
+
 int check_precision_form(cur_ctx* ctx, int S, const void* A, int64_t lda, int dtype, int64_t c) {
   if (S < 1 || S > 4) return fail(ctx, CUR_EINVAL, "unknown sketch_mode %d", S);
   if (dtype != CUR_F32) return fail(ctx, CUR_EINVAL, "the precision forms of the sketch need FP32 A");
@@ -375,7 +397,9 @@ int validate(cur_ctx* ctx, const void* A, int64_t m, int64_t n, int64_t lda, int
   if (o) {
     if (o->max_rank < 0) return fail(ctx, CUR_EINVAL, "max_rank < 0");
     if (o->max_rank > 0 && o->max_rank < mn) *max_rank = o->max_rank;
-    if (o->sketch_mode != CUR_SKETCH_F64)
+    if (o->sketch_mode == CUR_SKETCH_F64_TC)
+      TRY(check_fx_form(ctx, A, lda, dtype));
+    else if (o->sketch_mode != CUR_SKETCH_F64)
       TRY(check_precision_form(ctx, o->sketch_mode, A, lda, dtype, *c));
     if (o->alpha != 0.0) {
       if (!(o->alpha > 0.0 && o->alpha < 1.0) || !(o->delta >= 0.0))
@@ -429,6 +453,8 @@ int run_device(cur_ctx* ctx, const void* A, int64_t m, int64_t n, int64_t lda, i
                              B_PARTS));
   } else if (smode == CUR_SKETCH_F64) {
     TRY(sketch_f64(ctx, G, c, A, f32, m, n, lda, S, 0, B_PARTS));
+  } else if (smode == CUR_SKETCH_F64_TC) {
+    TRY(sketch_fx(ctx, G, c, static_cast<const double*>(A), m, n, lda, S, 0, B_PARTS, B_FX));
   } else {
     TRY(sketch_q(ctx, smode, G, c, static_cast<const float*>(A), m, n, lda, S, 0, B_PARTS, B_TC));
   }
@@ -779,6 +805,21 @@ int cur_step_sketch_q(cur_ctx* ctx, const double* G, int64_t c, const float* A, 
   TRY(ensure(ctx, B_STATUS, sizeof(DevStatus)));
   CK(cudaMemsetAsync(ctx->buf[B_STATUS].p, 0, sizeof(DevStatus), ctx->stream));
   TRY(sketch_q(ctx, digits, G, c, A, m, n, lda, Y, 0, B_STEP_PARTS, B_STEP_TC));
+  TRY(read_status(ctx));
+  if (sumsq_host) *sumsq_host = ctx->st_host->scalar[0];
+  return CUR_OK;
+}
+
+int cur_step_sketch_fx(cur_ctx* ctx, const double* G, int64_t c, const double* A, int64_t m,
+                       int64_t n, int64_t lda, double* Y, double* sumsq_host) {
+  if (!ctx) return CUR_EINVAL;
+  if (!G || !A || !Y || c < 1 || m < 1 || n < 1 || lda < n)
+    return fail(ctx, CUR_EINVAL, "bad arguments");
+  TRY(check_fx_form(ctx, A, lda, CUR_F64));
+  CK(cudaSetDevice(ctx->device));
+  TRY(ensure(ctx, B_STATUS, sizeof(DevStatus)));
+  CK(cudaMemsetAsync(ctx->buf[B_STATUS].p, 0, sizeof(DevStatus), ctx->stream));
+  TRY(sketch_fx(ctx, G, c, A, m, n, lda, Y, 0, B_STEP_PARTS, B_STEP_FX));
   TRY(read_status(ctx));
   if (sumsq_host) *sumsq_host = ctx->st_host->scalar[0];
   return CUR_OK;

@@ -139,6 +139,24 @@ cudaError_t launch_sketch_tc(const LaunchEnv& env, int S, const double* G, int64
                              const float* A, int64_t lda, int64_t m, int64_t n, void* scratch,
                              int ks, double* Y, double* sumsq_part, int64_t* nparts, int* err);
 
+// G_q = clamp(rint(16 G), +-127) as BF16 (c x ldq, columns m..ldq-1 zero):
+// the 8-bit sketch of both tensor-core forms.
+cudaError_t launch_gaussian_q8(const LaunchEnv& env, const double* G, int64_t c, int64_t m,
+                               int64_t ldq, uint16_t* Gq);
+
+// ---- sketch_fx.cu ------------------------------------------------------------
+// FP64 form of Y = G A on tcgen05: Y = RN(G_q trunc(A 2^(52-E_j))) 2^(E_j-52)
+// with the integer sum exact (six balanced base-512 BF16 digits per entry,
+// exact FP32 chunk sums, int64 combination).  A is FP64 with lda % 2 == 0 and a
+// 16-byte aligned base.  Any c >= 1 (row groups of 64 rows of G, one pass of A
+// each).  A column holding Inf/NaN gives NaN in Y (and so in the sum of
+// squares).  Writes *nparts sum-of-squares partials into sumsq_part.
+size_t sketch_fx_scratch_bytes(int64_t c, int64_t m, int64_t n);
+int64_t sketch_fx_max_parts(int64_t c, int64_t n);
+cudaError_t launch_sketch_fx(const LaunchEnv& env, const double* G, int64_t c, const double* A,
+                             int64_t lda, int64_t m, int64_t n, void* scratch, double* Y,
+                             double* sumsq_part, int64_t* nparts, int* err);
+
 // ---- gather.cu ------------------------------------------------------------
 // out[a * ldo + t] = src(r(a), c(t)) for a < rows, t < cols, where
 // r(a) = ridx ? ridx[a] : a, c(t) = cidx ? cidx[t] : t and src(i, j) =

@@ -1,0 +1,557 @@
+// sketch_fx.cu -- FP64 form of the initial sketch Y = G A of IterativeCUR
+// (arXiv 2509.21963, Algorithm 1; Sec. 3.4 counts the sketch among the primary
+// costs) on the 5th-generation tensor cores, exact by construction.
+//
+// GB300 has no fast FP64 arithmetic (about 2 DFMA per clock per SM), so an FP64
+// sketch on the FP64 pipe runs ~30x below the HBM rate.  Here the products
+// run on tcgen05 with BF16 operands holding small integers:
+//   * G_q = clamp(rint(16 Z), -127, 127): the Gaussian sketch rounded to 8-bit
+//     integers (exact in BF16).
+//   * column j of A gets E_j with max |A(:,j)| < 2^E_j (a column-max pass);
+//     every entry x becomes the integer X = trunc(x 2^(52 - E_j)), |X| < 2^52,
+//     written with six balanced base-512 digits d_k in [-256, 255] (exact in
+//     BF16): with K = 256 sum_k 512^k, X + K lies in [0, 2^54) and its 9-bit
+//     fields f_k give d_k = f_k - 256, X = sum_k d_k 512^k.
+//   * per digit an M = 128 (columns of A) x N = c_pad (rows of G_q) x K = 16
+//     (rows of A) MMA accumulates in FP32 in tensor memory: |G_q d| <= 32512
+//     and a chunk of 512 rows sums to at most 16646144 < 2^24, so every
+//     accumulator is an exact integer.
+//   * at the end of a chunk the six digit sums s_k are drained (exact int32)
+//     and combined into lo = s_0 + 2^9 s_1 + 2^18 s_2 and hi = s_3 + 2^9 s_4 +
+//     2^18 s_5 (int64, per CTA in shared memory), added into global int64 sums
+//     when the CTA leaves a column strip; the reduction forms V = 2^27 hi + lo
+//     exactly (128 bits), rounds it once to FP64 and scales by 2^(E_j - 52).
+// So Y = RN(G_q trunc(A 2^(52-E))) 2^(E-52): the exact sketch of A's 52-bit
+// fixed point, rounded once.
+//
+// Kernel structure (one persistent CTA per SM, 10 warps):
+//   warp 0     TMA producer: A tiles (16 rows x 128 columns FP64 = 16 KB, no
+//              swizzle) into a 4-stage ring; G_q tiles (c_pad rows x 64 rows of
+//              A, BF16, 128-byte swizzle = the K-major SW128 operand layout)
+//              into a 2-slot ring.
+//   warp 1     MMA issuer (one thread): per stage six MMAs, one per digit,
+//              whose A operand is the stage's digit tile in tensor memory.
+//   warps 2-9  converters in two groups of four (one warp per 32-lane quarter
+//              of tensor memory): group g converts the stages t with t % 2 == g
+//              into its digit buffer (tcgen05.st: lane = column of A, two rows
+//              of A per 32-bit column); all eight drain the accumulators at the
+//              end of each chunk.
+// Tensor memory: six accumulators of c_pad columns, then two digit buffers of
+// 6 x 8 columns.  Digits going to tensor memory instead of shared memory keep
+// the shared-memory traffic at ~22 bytes per entry of A.  Every wait is
+// bounded: on timeout the CTA records an error and leaves its loops.
+#include <cuda.h>
+
+#include "cur_internal.cuh"
+#include "tc_ptx.cuh"
+
+namespace cur {
+namespace {
+
+using namespace tc;
+
+constexpr int kRows = 16;          // rows of A per stage = K of one MMA
+constexpr int kCols = 128;         // columns of A per tile = MMA M
+constexpr int kChunkRows = 512;    // rows per exact accumulation chunk (= work unit)
+constexpr int kGRows = 64;         // rows of A per G_q tile (128-byte rows of BF16)
+constexpr int kNA = 4;             // A ring depth
+constexpr int kDigits = 6;
+constexpr int kConvWarps = 8;
+constexpr int kThreads = (2 + kConvWarps) * 32;
+constexpr int kOpCols = kDigits * (kRows / 2);   // tensor-memory columns of one digit buffer
+// 256 * sum_{k<6} 512^k: adding it makes every 9-bit field of X + K equal d_k + 256.
+constexpr uint64_t kBias = 0x0020100804020100ull;
+
+static_assert(kBias == 256ull * (1ull + (1ull << 9) + (1ull << 18) + (1ull << 27) +
+                                 (1ull << 36) + (1ull << 45)), "bias");
+
+template <int CP>
+struct FxLayout {
+  static constexpr int kABytes = kRows * kCols * 8;             // 16384
+  static constexpr int kGBytes = CP * kGRows * 2;               // CP * 128
+  static constexpr int kAccBytes = 2 * CP * kCols * 8;          // lo and hi, int64
+  static constexpr int kGOffset = kNA * kABytes;
+  static constexpr int kAccOffset = kGOffset + 2 * kGBytes;
+  static constexpr int kBarOffset = kAccOffset + kAccBytes;
+  static constexpr int kTotal = kBarOffset + 256 + 1024;        // barriers + alignment slack
+  static constexpr int kOpCol = kDigits * CP;                   // first digit-buffer column
+  static constexpr int kUsed = kOpCol + 2 * kOpCols;
+  static constexpr uint32_t kTmemCols = kUsed <= 32 ? 32 : kUsed <= 64 ? 64 : kUsed <= 128 ? 128
+                                        : kUsed <= 256 ? 256 : 512;
+};
+
+struct FxArgs {
+  int64_t m, n;
+  int c;                   // rows of Y in this row group
+  int64_t row0;            // first row of this group in Y / the global sums
+  int64_t ldy;             // row stride of the global sums (n)
+  const int* colexp;       // E_j per column
+  unsigned long long* acc_lo;  // int64 sums (two's complement), zeroed by the host
+  unsigned long long* acc_hi;
+  int64_t nstrips, nchunks;    // units: strip-major (strip, chunk)
+  int* err;
+};
+
+// Balanced base-512 digits of X = trunc(x 2^(52-E)) as FP32 values (exact
+// integers in [-256, 255]): rshift_base = 1023 + E.
+__device__ __forceinline__ void fx_digits(uint64_t bits, int rshift_base, float (&f)[kDigits]) {
+  const uint32_t hi = (uint32_t)(bits >> 32);
+  const uint32_t e = (hi >> 20) & 0x7FFu;
+  // |x| = M 2^(max(e,1) - 1075) with the implicit bit only for normal numbers
+  const uint64_t M = (bits & 0x000FFFFFFFFFFFFFull) | ((uint64_t)(e != 0) << 52);
+  // X = M 2^-r: a right shift (r >= 1) unless the column's largest entry is
+  // itself subnormal (E < -1021), where the subnormal mantissas move left
+  const int r = rshift_base - (int)(e != 0 ? e : 1u);
+  const uint64_t T = (r >= 64) ? 0ull : (r >= 0 ? (M >> r) : (M << (-r)));
+  const uint64_t sm = (uint64_t)((int64_t)(int32_t)hi >> 31);  // all ones for x < 0
+  const uint64_t Yb = (T ^ sm) + (kBias - sm);                 // X + K, X = -T for x < 0
+#pragma unroll
+  for (int k = 0; k < kDigits; ++k) {
+    const uint32_t fld = (uint32_t)(Yb >> (9 * k)) & 0x1FFu;
+    // (2^23 + fld) - (2^23 + 256) = fld - 256, exact
+    f[k] = __uint_as_float(0x4B000000u | fld) - 8388864.0f;
+  }
+}
+
+template <int CP>
+__global__ void __launch_bounds__(kThreads, 1)
+    sketch_fx_kernel(const __grid_constant__ CUtensorMap mapA,
+                     const __grid_constant__ CUtensorMap mapG, FxArgs g) {
+  using L = FxLayout<CP>;
+  static_assert(CP % 16 == 0 && CP >= 16 && CP <= 64, "N must be a multiple of 16, <= 64");
+  static_assert(L::kUsed <= 512, "tensor memory");
+  static_assert(L::kTotal <= 227 * 1024, "shared memory");
+  constexpr int HALF = CP / 2;   // rows of Y drained per converter group
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                             ~uintptr_t(1023));
+  long long* acc_lo = reinterpret_cast<long long*>(smem + L::kAccOffset);   // [CP][128]
+  long long* acc_hi = acc_lo + CP * kCols;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L::kBarOffset);
+  uint64_t* fullA = bars;            // [kNA] A tile landed (TMA)
+  uint64_t* emptyA = fullA + kNA;    // [kNA] A tile read by its converter group
+  uint64_t* fullG = emptyA + kNA;    // [2]   G_q tile landed (TMA)
+  uint64_t* emptyG = fullG + 2;      // [2]   MMAs done with the G_q tile
+  uint64_t* opfull = emptyG + 2;     // [2]   digit buffer written
+  uint64_t* opempty = opfull + 2;    // [2]   MMAs done with the digit buffer
+  uint64_t* accf = opempty + 2;      // chunk accumulators complete
+  uint64_t* acce = accf + 1;         // chunk accumulators drained
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acce + 1);
+  int* s_abort = reinterpret_cast<int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kNA; ++s) {
+      mbar_init(&fullA[s], 1);
+      mbar_init(&emptyA[s], 4);
+    }
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(&fullG[s], 1);
+      mbar_init(&emptyG[s], 1);
+      mbar_init(&opfull[s], 4);
+      mbar_init(&opempty[s], 1);
+    }
+    mbar_init(accf, 1);
+    mbar_init(acce, kConvWarps);
+    *s_abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) tmem_alloc(tmem_slot, L::kTmemCols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  // this CTA's units: a contiguous range of the strip-major (strip, chunk) list
+  const int64_t nunits = g.nstrips * g.nchunks;
+  const int64_t u0 = nunits * blockIdx.x / gridDim.x;
+  const int64_t u1 = nunits * (blockIdx.x + 1) / gridDim.x;
+  auto unit_stages = [&](int64_t u) -> int {
+    const int64_t z = u % g.nchunks;
+    const int64_t r0 = z * kChunkRows, r1 = min(g.m, r0 + kChunkRows);
+    return (int)((r1 - r0 + kRows - 1) / kRows);
+  };
+  auto abort_now = [&]() {
+    atomicCAS(g.err, 0, kDevTimeout);
+    *((volatile int*)s_abort) = 1;
+  };
+  auto aborted = [&]() { return *((volatile int*)s_abort) != 0; };
+
+  if (warp == 0) {
+    // ---------------- TMA producer ----------------
+    if (lane == 0) {
+      uint32_t t = 0, gs = 0;
+      bool ok = true;
+      for (int64_t u = u0; u < u1 && ok; ++u) {
+        const int64_t strip = u / g.nchunks, z = u % g.nchunks;
+        const int nt = unit_stages(u);
+        for (int i = 0; i < nt; ++i, ++t) {
+          if (aborted()) { ok = false; break; }
+          if (i % (kGRows / kRows) == 0) {
+            const uint32_t sl = gs & 1;
+            if (gs >= 2 && !mbar_wait(&emptyG[sl], ((gs >> 1) - 1) & 1)) { abort_now(); ok = false; break; }
+            mbar_expect_tx(&fullG[sl], (uint32_t)L::kGBytes);
+            tma_load_2d(smem + L::kGOffset + sl * L::kGBytes, &mapG, &fullG[sl],
+                        (int)(z * kChunkRows + i * kRows), 0);
+            ++gs;
+          }
+          const uint32_t s = t % kNA;
+          if (t >= (uint32_t)kNA && !mbar_wait(&emptyA[s], ((t / kNA) - 1) & 1)) { abort_now(); ok = false; break; }
+          mbar_expect_tx(&fullA[s], (uint32_t)L::kABytes);
+          tma_load_2d(smem + s * L::kABytes, &mapA, &fullA[s], (int)(strip * kCols),
+                      (int)(z * kChunkRows + i * kRows));
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      constexpr uint32_t idesc = idesc_bf16(kCols, CP);
+      uint32_t t = 0, gs = 0, ch = 0;
+      bool ok = true;
+      for (int64_t u = u0; u < u1 && ok; ++u) {
+        const int nt = unit_stages(u);
+        if (ch >= 1 && !mbar_wait(acce, (ch - 1) & 1)) { abort_now(); break; }
+        for (int i = 0; i < nt; ++i, ++t) {
+          const uint32_t b = t & 1, sl = gs & 1;
+          const int kk = i % (kGRows / kRows);
+          if (!mbar_wait(&opfull[b], (t >> 1) & 1)) { abort_now(); ok = false; break; }
+          if (kk == 0 && !mbar_wait(&fullG[sl], (gs >> 1) & 1)) { abort_now(); ok = false; break; }
+          tc_fence_after();
+          const uint32_t gaddr = smem_u32(smem + L::kGOffset + sl * L::kGBytes) + kk * 32;
+#pragma unroll
+          for (int d = 0; d < kDigits; ++d)
+            mma_bf16_tmem_a(tmem + (uint32_t)(d * CP),
+                            tmem + (uint32_t)(L::kOpCol + b * kOpCols + d * (kRows / 2)),
+                            desc_sw128(gaddr), idesc, i > 0 ? 1u : 0u);
+          mma_commit(&opempty[b]);
+          if (kk == (kGRows / kRows) - 1 || i == nt - 1) {
+            mma_commit(&emptyG[sl]);
+            ++gs;
+          }
+        }
+        if (!ok) break;
+        mma_commit(accf);
+        ++ch;
+      }
+    }
+  } else {
+    // ---------------- converters + drain ----------------
+    const int cw = warp - 2;                 // 0..7
+    const int grp = cw >> 2;                 // converter group: stages t % 2 == grp
+    const int q = warp & 3;                  // tensor-memory lane quarter of this warp
+    const int jl = q * 32 + lane;            // this thread's column of the tile (= TMEM lane)
+    const int rb = grp * HALF;               // rows of Y this thread drains: [rb, rb + HALF)
+    const uint32_t tlane = (uint32_t)(q * 32) << 16;
+    for (int r = rb; r < rb + HALF; ++r) acc_lo[r * kCols + jl] = acc_hi[r * kCols + jl] = 0;
+    uint32_t t = 0, ch = 0;
+    int64_t cur_strip = -1;
+    int base = 0;
+    bool ok = true;
+    for (int64_t u = u0; u < u1 && ok; ++u) {
+      const int64_t strip = u / g.nchunks;
+      const int nt = unit_stages(u);
+      if (strip != cur_strip) {
+        const int64_t jg = strip * kCols + jl;
+        base = 1023 + (jg < g.n ? g.colexp[jg] : 0);
+        cur_strip = strip;
+      }
+      for (int i = 0; i < nt; ++i, ++t) {
+        if ((int)(t & 1) != grp) continue;
+        if (t >= 2 && !mbar_wait(&opempty[grp], ((t >> 1) - 1) & 1)) { ok = false; break; }
+        const uint32_t s = t % kNA;
+        if (!mbar_wait(&fullA[s], (t / kNA) & 1)) { ok = false; break; }
+        tc_fence_after();
+        const unsigned long long* At =
+            reinterpret_cast<const unsigned long long*>(smem + s * L::kABytes);
+        uint32_t w[kDigits][8];
+#pragma unroll
+        for (int p = 0; p < kRows / 2; ++p) {
+          float f0[kDigits], f1[kDigits];
+          fx_digits(At[(2 * p) * kCols + jl], base, f0);
+          fx_digits(At[(2 * p + 1) * kCols + jl], base, f1);
+#pragma unroll
+          for (int d = 0; d < kDigits; ++d)   // two BF16 digits (rows 2p, 2p+1) per column
+            w[d][p] = __byte_perm(__float_as_uint(f0[d]), __float_as_uint(f1[d]), 0x7632);
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&emptyA[s]);   // the FP64 tile may be refilled
+#pragma unroll
+        for (int d = 0; d < kDigits; ++d)
+          tmem_st8(tmem + tlane + (uint32_t)(L::kOpCol + grp * kOpCols + d * (kRows / 2)), w[d]);
+        tmem_wait_st();
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&opfull[grp]);
+      }
+      if (!ok) break;
+      // chunk drain: six digit sums per (row of Y, column of A) -> lo, hi
+      if (!mbar_wait(accf, ch & 1)) { ok = false; break; }
+      tc_fence_after();
+#pragma unroll 1
+      for (int g8 = 0; g8 < HALF; g8 += 8) {
+        uint32_t v[kDigits][8];
+#pragma unroll
+        for (int d = 0; d < kDigits; ++d) tmem_ld8(tmem + tlane + (uint32_t)(d * CP + rb + g8), v[d]);
+        tmem_wait_ld();
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const long long lo = (long long)f2i_exact(v[0][e]) +
+                               ((long long)f2i_exact(v[1][e]) << 9) +
+                               ((long long)f2i_exact(v[2][e]) << 18);
+          const long long hi = (long long)f2i_exact(v[3][e]) +
+                               ((long long)f2i_exact(v[4][e]) << 9) +
+                               ((long long)f2i_exact(v[5][e]) << 18);
+          const int r = rb + g8 + e;
+          acc_lo[r * kCols + jl] += lo;
+          acc_hi[r * kCols + jl] += hi;
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(acce);
+      ++ch;
+      // leaving the strip: add this thread's sums into the global ones
+      if (u + 1 == u1 || (u + 1) / g.nchunks != strip) {
+        const int64_t jg = strip * kCols + jl;
+        for (int r = rb; r < rb + HALF; ++r) {
+          const long long lo = acc_lo[r * kCols + jl], hi = acc_hi[r * kCols + jl];
+          if (r < g.c && jg < g.n) {
+            const int64_t o = (g.row0 + r) * g.ldy + jg;
+            if (lo) atomicAdd(&g.acc_lo[o], (unsigned long long)lo);
+            if (hi) atomicAdd(&g.acc_hi[o], (unsigned long long)hi);
+          }
+          acc_lo[r * kCols + jl] = acc_hi[r * kCols + jl] = 0;
+        }
+      }
+    }
+    if (!ok) abort_now();
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, L::kTmemCols);
+  }
+}
+
+// ---- column scales: E_j with max_k |A(k,j)| < 2^E_j ------------------------
+// |x| compares as an unsigned integer of its bit pattern (NaN above Inf).
+__global__ void colmax_f64_kernel(const double* __restrict__ A, int64_t lda, int64_t m, int64_t n,
+                                  int64_t rows_per_cta, unsigned long long* __restrict__ cmax) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const int64_t r0 = (int64_t)blockIdx.y * rows_per_cta, r1 = min(m, r0 + rows_per_cta);
+  const unsigned long long* p = reinterpret_cast<const unsigned long long*>(A) + j;
+  unsigned long long mx[4] = {0, 0, 0, 0};
+  int64_t k = r0;
+  for (; k + 4 <= r1; k += 4) {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const unsigned long long b = __ldg(p + (k + e) * lda) & 0x7FFFFFFFFFFFFFFFull;
+      mx[e] = b > mx[e] ? b : mx[e];
+    }
+  }
+  for (; k < r1; ++k) {
+    const unsigned long long b = __ldg(p + k * lda) & 0x7FFFFFFFFFFFFFFFull;
+    mx[0] = b > mx[0] ? b : mx[0];
+  }
+  unsigned long long v = mx[0] > mx[1] ? mx[0] : mx[1];
+  const unsigned long long w = mx[2] > mx[3] ? mx[2] : mx[3];
+  v = v > w ? v : w;
+  if (v) atomicMax(&cmax[j], v);
+}
+
+// E_j (frexp of the column max; 0 for a zero column), 1 << 20 for Inf/NaN.
+__global__ void colexp_f64_kernel(const unsigned long long* __restrict__ cmax, int64_t n,
+                                  int* __restrict__ colexp) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const unsigned long long b = cmax[j];
+  int E = 0;
+  if (b >= 0x7FF0000000000000ull) E = 1 << 20;
+  else if (b != 0) frexp(__longlong_as_double((long long)b), &E);
+  colexp[j] = E;
+}
+
+// Round the 128-bit integer 2^27 hi + lo once to FP64 (to nearest, ties to
+// even): the magnitude's leading 64 bits with a sticky bit for the rest, then
+// one conversion (the 11 extra bits and the sticky bit make it exact RN).
+__device__ double fx_round(long long hi, long long lo) {
+  // v = hi * 2^27 + lo as (vh, vl), two's complement
+  unsigned long long vl = (unsigned long long)hi << 27;
+  long long vh = hi >> 37;
+  const unsigned long long s = vl + (unsigned long long)lo;
+  vh += (lo < 0 ? -1 : 0) + (s < vl ? 1 : 0);
+  vl = s;
+  const bool neg = vh < 0;
+  unsigned long long uh = (unsigned long long)vh, ul = vl;
+  if (neg) {  // magnitude
+    ul = ~ul + 1ull;
+    uh = ~uh + (ul == 0 ? 1ull : 0ull);
+  }
+  double d;
+  if (uh == 0) {
+    d = __ull2double_rn(ul);
+  } else {
+    const int sh = 64 - __clzll((long long)uh);               // 1..64 bits above the low word
+    unsigned long long top = sh == 64 ? uh : ((uh << (64 - sh)) | (ul >> sh));
+    const unsigned long long rest = sh == 64 ? ul : (ul << (64 - sh));
+    top |= (rest != 0) ? 1ull : 0ull;
+    d = __ull2double_rn(top) * __longlong_as_double((long long)(1023 + sh) << 52);  // exact 2^sh
+  }
+  return neg ? -d : d;
+}
+
+// y 2^e with one rounding (the first factor keeps y normal and exact).
+__device__ double fx_scale(double y, int e) {
+  const int e1 = e < -1000 ? -1000 : (e > 1000 ? 1000 : e);
+  const int e2 = e - e1;                                      // in [-126, 100] for our exponents
+  y *= __longlong_as_double((long long)(1023 + e1) << 52);
+  if (e2 != 0) {
+    y *= e2 >= -1022 ? __longlong_as_double((long long)(1023 + e2) << 52)
+                     : __longlong_as_double(1ll << (e2 + 1074));   // subnormal power of two
+  }
+  return y;
+}
+
+constexpr int kReduceRows = 16;
+
+// Y[i, j] = RN(2^27 hi + lo) 2^(E_j - 52) (NaN for a non-finite column), one
+// thread per column of a 256-column block and kReduceRows rows, plus per-CTA
+// sums of squares.
+__global__ void fx_reduce_kernel(const long long* __restrict__ acc_lo,
+                                 const long long* __restrict__ acc_hi, int64_t c, int64_t n,
+                                 const int* __restrict__ colexp, double* __restrict__ Y,
+                                 double* __restrict__ sumsq_part) {
+  __shared__ double red[8];
+  const int64_t j = (int64_t)blockIdx.x * 256 + threadIdx.x;
+  const int64_t i0 = (int64_t)blockIdx.y * kReduceRows, i1 = min(c, i0 + kReduceRows);
+  double ss = 0.0;
+  if (j < n) {
+    const int E = colexp[j];
+    for (int64_t i = i0; i < i1; ++i) {
+      const int64_t o = i * n + j;
+      const double y = E >= (1 << 20) ? __longlong_as_double(0x7FF8000000000000LL)
+                                      : fx_scale(fx_round(acc_hi[o], acc_lo[o]), E - 52);
+      Y[o] = y;
+      ss = fma(y, y, ss);
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) ss += __shfl_down_sync(0xffffffffu, ss, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = ss;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += red[w];
+    sumsq_part[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = t;
+  }
+}
+
+template <int CP>
+cudaError_t launch_fx(const LaunchEnv& env, const CUtensorMap& mA, const CUtensorMap& mG,
+                      const FxArgs& a, int grid) {
+  using L = FxLayout<CP>;
+  cudaError_t e = smem_opt_in((const void*)sketch_fx_kernel<CP>, L::kTotal);
+  if (e != cudaSuccess) return e;
+  sketch_fx_kernel<CP><<<grid, kThreads, L::kTotal, env.stream>>>(mA, mG, a);
+  return cudaGetLastError();
+}
+
+int64_t ldq_of(int64_t m) { return (m + kGRows - 1) / kGRows * kGRows; }
+
+}  // namespace
+
+size_t sketch_fx_scratch_bytes(int64_t c, int64_t m, int64_t n) {
+  size_t b = 0;
+  auto add = [&](size_t x) { b += (x + 255) / 256 * 256; };
+  add(sizeof(uint16_t) * (size_t)(c * ldq_of(m)));   // G_q
+  add(sizeof(unsigned long long) * (size_t)n);        // column max bits
+  add(sizeof(int) * (size_t)n);                       // column exponents
+  add(2 * sizeof(long long) * (size_t)(c * n));       // lo and hi sums
+  return b;
+}
+
+int64_t sketch_fx_max_parts(int64_t c, int64_t n) {
+  return ((n + 255) / 256) * ((c + kReduceRows - 1) / kReduceRows);
+}
+
+cudaError_t launch_sketch_fx(const LaunchEnv& env, const double* G, int64_t c, const double* A,
+                             int64_t lda, int64_t m, int64_t n, void* scratch, double* Y,
+                             double* sumsq_part, int64_t* nparts, int* err) {
+  if (c < 1 || m < 1 || n < 1 || lda < n || (lda & 1) || (reinterpret_cast<uintptr_t>(A) & 15))
+    return cudaErrorInvalidValue;
+  const int64_t ldq = ldq_of(m);
+  char* p = static_cast<char*>(scratch);
+  auto take = [&](size_t x) { char* r = p; p += (x + 255) / 256 * 256; return r; };
+  uint16_t* Gq = (uint16_t*)take(sizeof(uint16_t) * (size_t)(c * ldq));
+  unsigned long long* cmax = (unsigned long long*)take(sizeof(unsigned long long) * (size_t)n);
+  int* cexp = (int*)take(sizeof(int) * (size_t)n);
+  long long* acc = (long long*)take(2 * sizeof(long long) * (size_t)(c * n));
+  long long* acc_lo = acc;
+  long long* acc_hi = acc + c * n;
+
+  cudaError_t e = launch_gaussian_q8(env, G, c, m, ldq, Gq);
+  if (e == cudaSuccess) e = cudaMemsetAsync(cmax, 0, sizeof(unsigned long long) * (size_t)n, env.stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(acc, 0, 2 * sizeof(long long) * (size_t)(c * n), env.stream);
+  if (e != cudaSuccess) return e;
+  {
+    const int64_t rows_per = 512;
+    dim3 grid((unsigned)((n + 255) / 256), (unsigned)((m + rows_per - 1) / rows_per));
+    colmax_f64_kernel<<<grid, 256, 0, env.stream>>>(A, lda, m, n, rows_per, cmax);
+    colexp_f64_kernel<<<(unsigned)((n + 255) / 256), 256, 0, env.stream>>>(cmax, n, cexp);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return cudaErrorNotSupported;
+  CUtensorMap mA;
+  {
+    cuuint64_t gdim[2] = {(cuuint64_t)n, (cuuint64_t)m};
+    cuuint64_t gstride[1] = {(cuuint64_t)lda * 8};
+    cuuint32_t box[2] = {kCols, kRows};
+    cuuint32_t es[2] = {1, 1};
+    if (enc(&mA, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, (void*)A, gdim, gstride, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return cudaErrorInvalidValue;
+  }
+  FxArgs a;
+  a.m = m; a.n = n; a.ldy = n; a.colexp = cexp;
+  a.acc_lo = reinterpret_cast<unsigned long long*>(acc_lo);
+  a.acc_hi = reinterpret_cast<unsigned long long*>(acc_hi);
+  a.nstrips = (n + kCols - 1) / kCols;
+  a.nchunks = (m + kChunkRows - 1) / kChunkRows;
+  a.err = err;
+  const int64_t units = a.nstrips * a.nchunks;
+  const int grid = (int)(units < env.num_sms ? units : env.num_sms);
+  // row groups of at most 64 rows of G_q: one pass of A each
+  for (int64_t g0 = 0; g0 < c; g0 += 64) {
+    const int64_t cg = c - g0 < 64 ? c - g0 : 64;
+    const int CP = (int)((cg + 15) / 16 * 16);
+    CUtensorMap mG;
+    cuuint64_t gdim[2] = {(cuuint64_t)ldq, (cuuint64_t)(c - g0)};
+    cuuint64_t gstride[1] = {(cuuint64_t)ldq * 2};
+    cuuint32_t box[2] = {kGRows, (cuuint32_t)CP};
+    cuuint32_t es[2] = {1, 1};
+    if (enc(&mG, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)(Gq + g0 * ldq), gdim, gstride, box,
+            es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return cudaErrorInvalidValue;
+    a.c = (int)cg;
+    a.row0 = g0;
+    switch (CP) {
+      case 16: e = launch_fx<16>(env, mA, mG, a, grid); break;
+      case 32: e = launch_fx<32>(env, mA, mG, a, grid); break;
+      case 48: e = launch_fx<48>(env, mA, mG, a, grid); break;
+      default: e = launch_fx<64>(env, mA, mG, a, grid); break;
+    }
+    if (e != cudaSuccess) return e;
+  }
+  const dim3 rgrid((unsigned)((n + 255) / 256), (unsigned)((c + kReduceRows - 1) / kReduceRows));
+  fx_reduce_kernel<<<rgrid, 256, 0, env.stream>>>(acc_lo, acc_hi, c, n, cexp, Y, sumsq_part);
+  *nparts = (int64_t)rgrid.x * rgrid.y;
+  return cudaGetLastError();
+}
+
+}  // namespace cur

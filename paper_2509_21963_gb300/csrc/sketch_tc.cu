@@ -35,106 +35,18 @@
 #include <cuda.h>
 
 #include "gridbar.cuh"
+#include "tc_ptx.cuh"
 
 namespace cur {
 namespace {
+
+using namespace tc;
 
 constexpr int kTileK = 64;        // rows of A per stage = MMA K per stage
 constexpr int kTileN = 128;       // columns of A per CTA tile = MMA M
 constexpr int kChunkTiles = 8;    // stages per exact accumulation chunk (512 rows)
 constexpr int kConvWarps = 8;
 constexpr int kThreads = (2 + kConvWarps) * 32;
-constexpr long long kWaitBudget = 4000000000LL;  // ~2 s at 2 GHz
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-               "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
-// Bounded parity wait; false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t done = 0;
-  long long t0 = clock64();
-  while (true) {
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        " selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    if (done) return true;
-    if (clock64() - t0 > kWaitBudget) return false;
-  }
-}
-
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar,
-                                            int x, int y) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, "
-      "{%3, %4}], [%2];" ::"r"(smem_u32(dst)),
-      "l"(map), "r"(smem_u32(bar)), "r"(x), "r"(y)
-      : "memory");
-}
-
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row core
-// groups 1024 bytes apart (SBO), sm_100 descriptor version 1.
-__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
-  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
-  d |= (uint64_t)1 << 16;             // leading byte offset (unused for this layout)
-  d |= (uint64_t)(1024 >> 4) << 32;   // stride byte offset
-  d |= (uint64_t)1 << 46;             // descriptor version
-  d |= (uint64_t)2 << 61;             // SWIZZLE_128B
-  return d;
-}
-
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
-                                         uint32_t accumulate) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-      "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
-}
-
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-          smem_u32(bar))
-      : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7])
-      : "r"(taddr));
-}
-
-__device__ __forceinline__ void tmem_wait_ld() {
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_before() {
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_after() {
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void fence_async_smem() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
 
 // Packed pairs of FP32 (Blackwell f32x2): each lane rounds like the scalar
 // instruction, so the digits below are bit-identical to scalar arithmetic.
@@ -160,9 +72,6 @@ __device__ __forceinline__ uint64_t f2_pack(float lo, float hi) {
 // integer (ties to even) through the FP32 adder.
 constexpr uint64_t kMagic2 = 0x4B4000004B400000ull;
 constexpr uint64_t k256x2 = 0x4380000043800000ull;  // 256.0f in both lanes
-
-// FP32 accumulator holding an exact integer (|v| < 2^24) -> int32.
-__device__ __forceinline__ int f2i_exact(uint32_t bits) { return __float2int_rn(__uint_as_float(bits)); }
 
 struct TcArgs {
   int64_t m, n;
@@ -501,24 +410,6 @@ __global__ void gaussian_q8_kernel(const double* __restrict__ G, int64_t c, int6
   Gq[e] = (uint16_t)(__float_as_uint(q) >> 16);  // exact: |q| <= 127
 }
 
-typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
-                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
-                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
-                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-EncodeTiledFn encode_fn() {
-  static EncodeTiledFn fn = nullptr;
-  if (!fn) {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
-                                         &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<EncodeTiledFn>(p);
-  }
-  return fn;
-}
-
 template <int S, int CP>
 cudaError_t launch_tc(const LaunchEnv& env, const CUtensorMap& mA, const CUtensorMap& mG,
                       const TcArgs& a, int grid) {
@@ -531,6 +422,13 @@ cudaError_t launch_tc(const LaunchEnv& env, const CUtensorMap& mA, const CUtenso
 }
 
 }  // namespace
+
+cudaError_t launch_gaussian_q8(const LaunchEnv& env, const double* G, int64_t c, int64_t m,
+                               int64_t ldq, uint16_t* Gq) {
+  const int64_t tot = c * ldq;
+  gaussian_q8_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, env.stream>>>(G, c, m, ldq, Gq);
+  return cudaGetLastError();
+}
 
 int sketch_tc_cpad(int c, int S) {
   int cp = (c + 15) / 16 * 16;
@@ -579,12 +477,10 @@ cudaError_t launch_sketch_tc(const LaunchEnv& env, int S, const double* G, int64
   long long* acc64 = (long long*)take(sizeof(long long) * (size_t)c * n);
 
   // G_q (BF16, rows padded to a multiple of 64 so TMA strides are 16-byte multiples)
-  {
-    int64_t tot = c * ldq;
-    gaussian_q8_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, env.stream>>>(G, c, m, ldq, Gq);
-  }
+  cudaError_t e = launch_gaussian_q8(env, G, c, m, ldq, Gq);
+  if (e != cudaSuccess) return e;
   // column scales
-  cudaError_t e = cudaMemsetAsync(cmax, 0, sizeof(unsigned) * (size_t)n, env.stream);
+  e = cudaMemsetAsync(cmax, 0, sizeof(unsigned) * (size_t)n, env.stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(acc64, 0, sizeof(long long) * (size_t)(c * n), env.stream);
   if (e != cudaSuccess) return e;
   {
