@@ -24,18 +24,19 @@
 // So Y = RN(G_q trunc(A 2^(52-E))) 2^(E-52): the exact sketch of A's 52-bit
 // fixed point, rounded once.
 //
-// Kernel structure (one persistent CTA per SM, 10 warps):
+// Kernel structure (one persistent CTA per SM, 18 warps):
 //   warp 0     TMA producer: A tiles (16 rows x 128 columns FP64 = 16 KB, no
-//              swizzle) into a 4-stage ring; G_q tiles (c_pad rows x 64 rows of
-//              A, BF16, 128-byte swizzle = the K-major SW128 operand layout)
-//              into a 2-slot ring.
-//   warp 1     MMA issuer (one thread): per stage six MMAs, one per digit,
-//              whose A operand is the stage's digit tile in tensor memory.
-//   warps 2-9  converters in two groups of four (one warp per 32-lane quarter
-//              of tensor memory): group g converts the stages t with t % 2 == g
-//              into its digit buffer (tcgen05.st: lane = column of A, two rows
-//              of A per 32-bit column); all eight drain the accumulators at the
-//              end of each chunk.
+//              swizzle) into a 4-stage ring, with an L2 prefetch running ahead;
+//              G_q tiles (c_pad rows x 64 rows of A, BF16, 128-byte swizzle =
+//              the K-major SW128 operand layout) into a 2-slot ring.
+//   warp 1     allocates and frees tensor memory.
+//   warps 2-17 converters in two groups of eight (two warps per 32-lane
+//              quarter of tensor memory, eight rows each): group g converts
+//              the stages i with i % 2 == g into its digit buffer (tcgen05.st:
+//              lane = column of A, two rows of A per 32-bit column), and the
+//              group's first thread issues that stage's six MMAs (one per
+//              digit) with the digit tile as the A operand; all sixteen warps
+//              drain and zero the accumulators at the end of each chunk.
 // Tensor memory: six accumulators of c_pad columns, then two digit buffers of
 // 6 x 8 columns.  Digits going to tensor memory instead of shared memory keep
 // the shared-memory traffic at ~22 bytes per entry of A.  Every wait is
@@ -55,12 +56,17 @@ constexpr int kCols = 128;         // columns of A per tile = MMA M
 constexpr int kChunkRows = 512;    // rows per exact accumulation chunk (= work unit)
 constexpr int kGRows = 64;         // rows of A per G_q tile (128-byte rows of BF16)
 constexpr int kNA = 4;             // A ring depth
+constexpr int kPrefetch = 12;      // tiles of A prefetched into L2 ahead of the ring
 constexpr int kDigits = 6;
-constexpr int kConvWarps = 8;
+constexpr int kConvWarps = 16;     // two groups of 8: two warps per lane quarter each
 constexpr int kThreads = (2 + kConvWarps) * 32;
 constexpr int kOpCols = kDigits * (kRows / 2);   // tensor-memory columns of one digit buffer
 // 256 * sum_{k<6} 512^k: adding it makes every 9-bit field of X + K equal d_k + 256.
 constexpr uint64_t kBias = 0x0020100804020100ull;
+constexpr uint32_t kBiasLo = (uint32_t)kBias, kBiasHi = (uint32_t)(kBias >> 32);
+// Columns whose scale is at least 2^-970 hold every subnormal entry below the
+// grid 2^(E-52) (X = 0); the fast digit path relies on it.
+constexpr int kFastMinExp = -970;
 
 static_assert(kBias == 256ull * (1ull + (1ull << 9) + (1ull << 18) + (1ull << 27) +
                                  (1ull << 36) + (1ull << 45)), "bias");
@@ -93,7 +99,7 @@ struct FxArgs {
 };
 
 // Balanced base-512 digits of X = trunc(x 2^(52-E)) as FP32 values (exact
-// integers in [-256, 255]): rshift_base = 1023 + E.
+// integers in [-256, 255]), any finite column: rshift_base = 1023 + E.
 __device__ __forceinline__ void fx_digits(uint64_t bits, int rshift_base, float (&f)[kDigits]) {
   const uint32_t hi = (uint32_t)(bits >> 32);
   const uint32_t e = (hi >> 20) & 0x7FFu;
@@ -113,6 +119,42 @@ __device__ __forceinline__ void fx_digits(uint64_t bits, int rshift_base, float 
   }
 }
 
+// The same digits for columns with E >= kFastMinExp, branch-free: the implicit
+// bit is always set (an exponent field of 0 gives a shift >= 53, X = 0), the
+// 64-bit shift is done with clamped funnel shifts, and each 9-bit field goes
+// straight into an FP32 mantissa whose exponent gives that field weight one
+// (2^23 + f for bits 0-8, 2^14 + f for bits 9-17 left in place), so one
+// subtraction yields the digit.  f[0..5] hold FP32 bit patterns.
+__device__ __forceinline__ void fx_digits_fast(uint32_t lo, uint32_t hi, int rshift_base,
+                                               uint32_t (&f)[kDigits]) {
+  const uint32_t r = (uint32_t)(rshift_base - (int)((hi >> 20) & 0x7FFu));   // >= 1
+  const uint32_t mh = (hi & 0x000FFFFFu) | 0x00100000u;
+  const uint32_t th = __funnelshift_rc(mh, 0u, r);             // 0 for r >= 32
+  const uint32_t tl = r < 32u ? __funnelshift_rc(lo, mh, r) : __funnelshift_rc(mh, 0u, r - 32u);
+  const uint32_t sm = (uint32_t)((int32_t)hi >> 31);           // all ones for x < 0
+  uint32_t yl, yh;                                             // X + K, X = -T for x < 0
+  asm("add.cc.u32 %0, %2, %3;\n\taddc.u32 %1, %4, %5;"
+      : "=r"(yl), "=r"(yh)
+      : "r"(tl ^ sm), "r"(kBiasLo - sm), "r"(th ^ sm), "r"(kBiasHi));
+  const uint32_t t = __funnelshift_r(yl, yh, 18);              // bits 18..49
+  const uint32_t u = yh >> 4;                                  // bits 36..63
+  f[0] = 0x4B000000u | (yl & 0x1FFu);
+  f[1] = 0x46800000u | (yl & 0x3FE00u);
+  f[2] = 0x4B000000u | (t & 0x1FFu);
+  f[3] = 0x46800000u | (t & 0x3FE00u);
+  f[4] = 0x4B000000u | (u & 0x1FFu);
+  f[5] = 0x46800000u | (u & 0x3FE00u);
+  // (2^23 + f) - (2^23 + 256) and (2^14 + f) - (2^14 + 256), two lanes at a time
+  constexpr uint64_t kSub = ((uint64_t)0xC6820000u << 32) | 0xCB000100u;   // (-16640, -8388864)
+#pragma unroll
+  for (int k = 0; k < kDigits; k += 2) {
+    uint64_t v = (uint64_t)f[k] | ((uint64_t)f[k + 1] << 32), d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(v), "l"(kSub));
+    f[k] = (uint32_t)d;
+    f[k + 1] = (uint32_t)(d >> 32);
+  }
+}
+
 template <int CP>
 __global__ void __launch_bounds__(kThreads, 1)
     sketch_fx_kernel(const __grid_constant__ CUtensorMap mapA,
@@ -121,7 +163,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   static_assert(CP % 16 == 0 && CP >= 16 && CP <= 64, "N must be a multiple of 16, <= 64");
   static_assert(L::kUsed <= 512, "tensor memory");
   static_assert(L::kTotal <= 227 * 1024, "shared memory");
-  constexpr int HALF = CP / 2;   // rows of Y drained per converter group
+  constexpr int QROWS = CP / 4;            // rows of Y drained per converter warp
+  constexpr int kSuper = kGRows / kRows;   // stages per G_q tile
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~uintptr_t(1023));
@@ -131,28 +174,28 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint64_t* fullA = bars;            // [kNA] A tile landed (TMA)
   uint64_t* emptyA = fullA + kNA;    // [kNA] A tile read by its converter group
   uint64_t* fullG = emptyA + kNA;    // [2]   G_q tile landed (TMA)
-  uint64_t* emptyG = fullG + 2;      // [2]   MMAs done with the G_q tile
-  uint64_t* opfull = emptyG + 2;     // [2]   digit buffer written
-  uint64_t* opempty = opfull + 2;    // [2]   MMAs done with the digit buffer
-  uint64_t* accf = opempty + 2;      // chunk accumulators complete
-  uint64_t* acce = accf + 1;         // chunk accumulators drained
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acce + 1);
+  uint64_t* emptyG = fullG + 2;      // [2]   both groups' MMAs done with the G_q tile
+  uint64_t* opfull = emptyG + 2;     // [2]   group's digit buffer written
+  uint64_t* opempty = opfull + 2;    // [2]   MMAs done with the group's digit buffer
+  uint64_t* accf = opempty + 2;      // both groups' MMAs of the chunk complete
+  uint64_t* drained = accf + 1;      // accumulators read and zeroed
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drained + 1);
   int* s_abort = reinterpret_cast<int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     for (int s = 0; s < kNA; ++s) {
       mbar_init(&fullA[s], 1);
-      mbar_init(&emptyA[s], 4);
+      mbar_init(&emptyA[s], kConvWarps / 2);
     }
     for (int s = 0; s < 2; ++s) {
       mbar_init(&fullG[s], 1);
-      mbar_init(&emptyG[s], 1);
-      mbar_init(&opfull[s], 4);
+      mbar_init(&emptyG[s], 2);
+      mbar_init(&opfull[s], kConvWarps / 2);
       mbar_init(&opempty[s], 1);
     }
-    mbar_init(accf, 1);
-    mbar_init(acce, kConvWarps);
+    mbar_init(accf, 2);
+    mbar_init(drained, kConvWarps);
     *s_abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -162,15 +205,19 @@ __global__ void __launch_bounds__(kThreads, 1)
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
-  // this CTA's units: a contiguous range of the strip-major (strip, chunk) list
+  // this CTA's units: a contiguous range of the strip-major (strip, chunk) list;
+  // every unit has an even number of stages (a zero stage past the last row
+  // pads an odd count), so stage i of every unit goes to converter group i % 2
+  // (units are walked with incremental (strip, chunk) counters: 64-bit
+  // divisions on the single-thread producer path cost hundreds of cycles)
   const int64_t nunits = g.nstrips * g.nchunks;
   const int64_t u0 = nunits * blockIdx.x / gridDim.x;
   const int64_t u1 = nunits * (blockIdx.x + 1) / gridDim.x;
-  auto unit_stages = [&](int64_t u) -> int {
-    const int64_t z = u % g.nchunks;
-    const int64_t r0 = z * kChunkRows, r1 = min(g.m, r0 + kChunkRows);
-    return (int)((r1 - r0 + kRows - 1) / kRows);
-  };
+  const int nch = (int)g.nchunks;
+  const int strip0 = (int)(u0 / nch), z0 = (int)(u0 % nch);
+  const int last_rows = (int)(g.m - (int64_t)(nch - 1) * kChunkRows);     // rows of the last chunk
+  const int last_nt = (((last_rows + kRows - 1) / kRows) + 1) & ~1;
+  auto unit_stages = [&](int z) -> int { return z == nch - 1 ? last_nt : kChunkRows / kRows; };
   auto abort_now = [&]() {
     atomicCAS(g.err, 0, kDevTimeout);
     *((volatile int*)s_abort) = 1;
@@ -182,139 +229,177 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 0) {
       uint32_t t = 0, gs = 0;
       bool ok = true;
-      for (int64_t u = u0; u < u1 && ok; ++u) {
-        const int64_t strip = u / g.nchunks, z = u % g.nchunks;
-        const int nt = unit_stages(u);
+      // L2 prefetch cursor, kPrefetch tiles ahead of the loads
+      int64_t pu = u0;
+      int pstrip = strip0, pz = z0, pi = 0;
+      auto prefetch_next = [&]() {
+        if (pu >= u1) return;
+        tma_prefetch_2d(&mapA, pstrip * kCols, pz * kChunkRows + pi * kRows);
+        if (++pi == unit_stages(pz)) {
+          pi = 0;
+          ++pu;
+          if (++pz == nch) { pz = 0; ++pstrip; }
+        }
+      };
+      for (int k = 0; k < kPrefetch; ++k) prefetch_next();
+      int strip = strip0, z = z0;
+      for (int64_t u = u0; u < u1 && ok; ++u, (++z == nch ? (z = 0, ++strip) : 0)) {
+        const int nt = unit_stages(z);
         for (int i = 0; i < nt; ++i, ++t) {
           if (aborted()) { ok = false; break; }
-          if (i % (kGRows / kRows) == 0) {
+          prefetch_next();
+          if (i % kSuper == 0) {
             const uint32_t sl = gs & 1;
             if (gs >= 2 && !mbar_wait(&emptyG[sl], ((gs >> 1) - 1) & 1)) { abort_now(); ok = false; break; }
             mbar_expect_tx(&fullG[sl], (uint32_t)L::kGBytes);
             tma_load_2d(smem + L::kGOffset + sl * L::kGBytes, &mapG, &fullG[sl],
-                        (int)(z * kChunkRows + i * kRows), 0);
+                        z * kChunkRows + i * kRows, 0);
             ++gs;
           }
           const uint32_t s = t % kNA;
           if (t >= (uint32_t)kNA && !mbar_wait(&emptyA[s], ((t / kNA) - 1) & 1)) { abort_now(); ok = false; break; }
           mbar_expect_tx(&fullA[s], (uint32_t)L::kABytes);
-          tma_load_2d(smem + s * L::kABytes, &mapA, &fullA[s], (int)(strip * kCols),
-                      (int)(z * kChunkRows + i * kRows));
+          tma_load_2d(smem + s * L::kABytes, &mapA, &fullA[s], strip * kCols,
+                      z * kChunkRows + i * kRows);
         }
       }
     }
-  } else if (warp == 1) {
-    // ---------------- MMA issuer ----------------
-    if (lane == 0) {
-      constexpr uint32_t idesc = idesc_bf16(kCols, CP);
-      uint32_t t = 0, gs = 0, ch = 0;
-      bool ok = true;
-      for (int64_t u = u0; u < u1 && ok; ++u) {
-        const int nt = unit_stages(u);
-        if (ch >= 1 && !mbar_wait(acce, (ch - 1) & 1)) { abort_now(); break; }
-        for (int i = 0; i < nt; ++i, ++t) {
-          const uint32_t b = t & 1, sl = gs & 1;
-          const int kk = i % (kGRows / kRows);
-          if (!mbar_wait(&opfull[b], (t >> 1) & 1)) { abort_now(); ok = false; break; }
-          if (kk == 0 && !mbar_wait(&fullG[sl], (gs >> 1) & 1)) { abort_now(); ok = false; break; }
+  } else if (warp >= 2) {
+    // ------- converters; the first thread of each group issues its MMAs -------
+    const int cw = warp - 2;                 // 0..15
+    const int grp = cw >> 3;                 // converter group: stages i % 2 == grp
+    const int q = warp & 3;                  // tensor-memory lane quarter of this warp
+    const int hk = (cw >> 2) & 1;            // which 8 of the stage's 16 rows
+    const int jl = q * 32 + lane;            // this thread's column of the tile (= TMEM lane)
+    const int rb = (cw >> 2) * QROWS;        // rows of Y this thread drains: [rb, rb + QROWS)
+    const bool issuer = (cw & 7) == 0 && lane == 0;
+    const uint32_t tlane = (uint32_t)(q * 32) << 16;
+    constexpr uint32_t idesc = idesc_bf16(kCols, CP);
+    const uint32_t zero4[4] = {0u, 0u, 0u, 0u};
+    // every MMA accumulates: the accumulators start at zero and every drain
+    // zeroes what it read, so the two groups' MMAs need no ordering
+    for (int r = rb; r < rb + QROWS; ++r) acc_lo[r * kCols + jl] = acc_hi[r * kCols + jl] = 0;
+#pragma unroll 1
+    for (int g4 = 0; g4 < QROWS; g4 += 4)
+      for (int d = 0; d < kDigits; ++d) tmem_st4(tmem + tlane + (uint32_t)(d * CP + rb + g4), zero4);
+    tmem_wait_st();
+    tc_fence_before();
+    __syncwarp();
+    if (lane == 0) mbar_arrive(drained);
+    uint32_t t = 0, ch = 0, gs = 0;
+    int cur_strip = -1;
+    int base = 0;
+    bool fast = true;
+    bool ok = true;
+    int strip = strip0, z = z0;
+    for (int64_t u = u0; u < u1 && ok; ++u, (++z == nch ? (z = 0, ++strip) : 0)) {
+      const int nt = unit_stages(z);
+      if (strip != cur_strip) {
+        const int64_t jg = (int64_t)strip * kCols + jl;
+        const int E = jg < g.n ? g.colexp[jg] : 0;
+        base = 1023 + E;
+        fast = __all_sync(0xffffffffu, E >= kFastMinExp);
+        cur_strip = strip;
+      }
+      for (int i = 0; i < nt; ++i, ++t) {
+        if ((i & 1) != grp) continue;
+        const uint32_t s = t % kNA;
+        if (!mbar_wait(&fullA[s], (t / kNA) & 1)) { ok = false; break; }
+        const uint2* At = reinterpret_cast<const uint2*>(smem + s * L::kABytes) + hk * 8 * kCols;
+        uint32_t w[kDigits][4];
+        if (fast) {
+#pragma unroll
+          for (int p = 0; p < 4; ++p) {
+            uint32_t f0[kDigits], f1[kDigits];
+            const uint2 x0 = At[(2 * p) * kCols + jl], x1 = At[(2 * p + 1) * kCols + jl];
+            fx_digits_fast(x0.x, x0.y, base, f0);
+            fx_digits_fast(x1.x, x1.y, base, f1);
+#pragma unroll
+            for (int d = 0; d < kDigits; ++d)   // two BF16 digits (rows 2p, 2p+1) per column
+              w[d][p] = __byte_perm(f0[d], f1[d], 0x7632);
+          }
+        } else {
+#pragma unroll
+          for (int p = 0; p < 4; ++p) {
+            float f0[kDigits], f1[kDigits];
+            const uint2 x0 = At[(2 * p) * kCols + jl], x1 = At[(2 * p + 1) * kCols + jl];
+            fx_digits(((uint64_t)x0.y << 32) | x0.x, base, f0);
+            fx_digits(((uint64_t)x1.y << 32) | x1.x, base, f1);
+#pragma unroll
+            for (int d = 0; d < kDigits; ++d)
+              w[d][p] = __byte_perm(__float_as_uint(f0[d]), __float_as_uint(f1[d]), 0x7632);
+          }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&emptyA[s]);   // the FP64 rows may be refilled
+        // the digits are in registers: only now wait for the MMAs that read this
+        // group's buffer last (the conversion overlapped them)
+        if (t >= 2 && !mbar_wait(&opempty[grp], ((t >> 1) - 1) & 1)) { ok = false; break; }
+        tc_fence_after();
+#pragma unroll
+        for (int d = 0; d < kDigits; ++d)
+          tmem_st4(tmem + tlane +
+                       (uint32_t)(L::kOpCol + grp * kOpCols + d * (kRows / 2) + hk * 4),
+                   w[d]);
+        tmem_wait_st();
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&opfull[grp]);
+        if (issuer) {
+          const uint32_t sl = gs & 1;
+          const int kk = i % kSuper;
+          if (i == grp && !mbar_wait(drained, ch & 1)) { ok = false; break; }
+          if (!mbar_wait(&opfull[grp], (t >> 1) & 1)) { ok = false; break; }
+          if (kk == grp && !mbar_wait(&fullG[sl], (gs >> 1) & 1)) { ok = false; break; }
           tc_fence_after();
           const uint32_t gaddr = smem_u32(smem + L::kGOffset + sl * L::kGBytes) + kk * 32;
 #pragma unroll
           for (int d = 0; d < kDigits; ++d)
             mma_bf16_tmem_a(tmem + (uint32_t)(d * CP),
-                            tmem + (uint32_t)(L::kOpCol + b * kOpCols + d * (kRows / 2)),
-                            desc_sw128(gaddr), idesc, i > 0 ? 1u : 0u);
-          mma_commit(&opempty[b]);
-          if (kk == (kGRows / kRows) - 1 || i == nt - 1) {
+                            tmem + (uint32_t)(L::kOpCol + grp * kOpCols + d * (kRows / 2)),
+                            desc_sw128(gaddr), idesc, 1u);
+          mma_commit(&opempty[grp]);
+          if (kk >= kSuper - 2 || i + 2 >= nt) {   // this group's last stage on the G_q tile
             mma_commit(&emptyG[sl]);
             ++gs;
           }
+          if (i + 2 >= nt) mma_commit(accf);       // this group's last stage of the chunk
         }
-        if (!ok) break;
-        mma_commit(accf);
-        ++ch;
-      }
-    }
-  } else {
-    // ---------------- converters + drain ----------------
-    const int cw = warp - 2;                 // 0..7
-    const int grp = cw >> 2;                 // converter group: stages t % 2 == grp
-    const int q = warp & 3;                  // tensor-memory lane quarter of this warp
-    const int jl = q * 32 + lane;            // this thread's column of the tile (= TMEM lane)
-    const int rb = grp * HALF;               // rows of Y this thread drains: [rb, rb + HALF)
-    const uint32_t tlane = (uint32_t)(q * 32) << 16;
-    for (int r = rb; r < rb + HALF; ++r) acc_lo[r * kCols + jl] = acc_hi[r * kCols + jl] = 0;
-    uint32_t t = 0, ch = 0;
-    int64_t cur_strip = -1;
-    int base = 0;
-    bool ok = true;
-    for (int64_t u = u0; u < u1 && ok; ++u) {
-      const int64_t strip = u / g.nchunks;
-      const int nt = unit_stages(u);
-      if (strip != cur_strip) {
-        const int64_t jg = strip * kCols + jl;
-        base = 1023 + (jg < g.n ? g.colexp[jg] : 0);
-        cur_strip = strip;
-      }
-      for (int i = 0; i < nt; ++i, ++t) {
-        if ((int)(t & 1) != grp) continue;
-        if (t >= 2 && !mbar_wait(&opempty[grp], ((t >> 1) - 1) & 1)) { ok = false; break; }
-        const uint32_t s = t % kNA;
-        if (!mbar_wait(&fullA[s], (t / kNA) & 1)) { ok = false; break; }
-        tc_fence_after();
-        const unsigned long long* At =
-            reinterpret_cast<const unsigned long long*>(smem + s * L::kABytes);
-        uint32_t w[kDigits][8];
-#pragma unroll
-        for (int p = 0; p < kRows / 2; ++p) {
-          float f0[kDigits], f1[kDigits];
-          fx_digits(At[(2 * p) * kCols + jl], base, f0);
-          fx_digits(At[(2 * p + 1) * kCols + jl], base, f1);
-#pragma unroll
-          for (int d = 0; d < kDigits; ++d)   // two BF16 digits (rows 2p, 2p+1) per column
-            w[d][p] = __byte_perm(__float_as_uint(f0[d]), __float_as_uint(f1[d]), 0x7632);
-        }
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&emptyA[s]);   // the FP64 tile may be refilled
-#pragma unroll
-        for (int d = 0; d < kDigits; ++d)
-          tmem_st8(tmem + tlane + (uint32_t)(L::kOpCol + grp * kOpCols + d * (kRows / 2)), w[d]);
-        tmem_wait_st();
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&opfull[grp]);
       }
       if (!ok) break;
-      // chunk drain: six digit sums per (row of Y, column of A) -> lo, hi
+      // chunk drain: six digit sums per (row of Y, column of A) -> lo, hi; zero them
       if (!mbar_wait(accf, ch & 1)) { ok = false; break; }
       tc_fence_after();
 #pragma unroll 1
-      for (int g8 = 0; g8 < HALF; g8 += 8) {
-        uint32_t v[kDigits][8];
+      for (int g4 = 0; g4 < QROWS; g4 += 4) {
+        uint32_t v[kDigits][4];
 #pragma unroll
-        for (int d = 0; d < kDigits; ++d) tmem_ld8(tmem + tlane + (uint32_t)(d * CP + rb + g8), v[d]);
+        for (int d = 0; d < kDigits; ++d) tmem_ld4(tmem + tlane + (uint32_t)(d * CP + rb + g4), v[d]);
         tmem_wait_ld();
 #pragma unroll
-        for (int e = 0; e < 8; ++e) {
+        for (int d = 0; d < kDigits; ++d) tmem_st4(tmem + tlane + (uint32_t)(d * CP + rb + g4), zero4);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
           const long long lo = (long long)f2i_exact(v[0][e]) +
                                ((long long)f2i_exact(v[1][e]) << 9) +
                                ((long long)f2i_exact(v[2][e]) << 18);
           const long long hi = (long long)f2i_exact(v[3][e]) +
                                ((long long)f2i_exact(v[4][e]) << 9) +
                                ((long long)f2i_exact(v[5][e]) << 18);
-          const int r = rb + g8 + e;
+          const int r = rb + g4 + e;
           acc_lo[r * kCols + jl] += lo;
           acc_hi[r * kCols + jl] += hi;
         }
       }
+      tmem_wait_st();
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(acce);
+      if (lane == 0) mbar_arrive(drained);
       ++ch;
       // leaving the strip: add this thread's sums into the global ones
-      if (u + 1 == u1 || (u + 1) / g.nchunks != strip) {
-        const int64_t jg = strip * kCols + jl;
-        for (int r = rb; r < rb + HALF; ++r) {
+      if (u + 1 == u1 || z + 1 == nch) {
+        const int64_t jg = (int64_t)strip * kCols + jl;
+        for (int r = rb; r < rb + QROWS; ++r) {
           const long long lo = acc_lo[r * kCols + jl], hi = acc_hi[r * kCols + jl];
           if (r < g.c && jg < g.n) {
             const int64_t o = (g.row0 + r) * g.ldy + jg;
