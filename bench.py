@@ -4,17 +4,21 @@
 Default workload (one "step" = one complete cur_run to tolerance):
   A = U diag(i^-2) V^T + noise, 20000 x 20000 FP64 (U, V thin orthonormal factors
   of rank 2000 from QR of seeded Gaussians; i.i.d. N(0, (1e-8)^2) noise),
-  tol 1e-2, block size b = 50, sketch rows c = floor(1.1 b) = 55, seed 0.
-With this noise (1.85e-4 of ||A||_F) the cross approximation stalls near
-rho ~ 1.2e-3, so 1e-2 is the tolerance of the family that the method reaches;
-the line also reports tol 1e-3 on the same spectrum with N(0, (1e-10)^2) noise
-("second_form").  A (3.2 GB) is resident in HBM and larger than L2, so no L2
-flush is needed.
+  tol 1e-2, block size b = 50, sketch rows c = floor(1.1 b) = 55, seed 0, the
+  FP64 form of the sketch on the tensor cores (CUR_SKETCH_F64_TC: exact sketch
+  of the 52-bit fixed point of A by the 8-bit Gaussian sketch; every later step
+  FP64).  With this noise (1.85e-4 of ||A||_F) the cross approximation stalls
+  near rho ~ 1.2e-3, so 1e-2 is the tolerance of the family that the method
+  reaches; the line also reports the same step with the FP64-pipe Gaussian
+  sketch, tol 1e-3 and 1e-4 on the same spectrum with N(0, (1e-10)^2) noise,
+  and the FP32 matrix with the FP64 sketch and with the two-digit tensor-core
+  sketch.  A (3.2 GB) is resident in HBM and larger than L2, so no L2 flush is
+  needed.
 
 Prints ONE JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
-instead (the reference arm: a bounded column-slab sample, scaled to the full
-matrix).  Under torchrun every rank runs an independent replica (the method
-has no data-parallel exchange): value = max-over-ranks time / (ranks x steps).
+instead (the reference arm: one whole oracle run per step on the host cores).
+Under torchrun every rank runs an independent replica (the method has no
+data-parallel exchange): value = max-over-ranks time / (ranks x steps).
 """
 from __future__ import annotations
 
@@ -39,9 +43,22 @@ sys.path.insert(0, ROOT)
 # file's code with // comments removed; it was moved once since the capture, when
 # host-side row-block launchers were appended to the file (the kernel unchanged).
 TRAFFIC = {"sketch_simt.cu": {"sha1": "31824a3eff0a3f330025c2a908a52893a001d576",
-                              "bytes_per_launch_full": 3.323e9}}
-FP64_PEAK_TFLOPS = 1.25  # GB300 nominal FP64 rate (no FP64 entry in the measured peaks)
-HBM_GBS = 6685.5          # measured copy bandwidth of the GB300s (MEASURED_PEAKS.json)
+                              "bytes_per_launch_full": 3.323e9},
+           "sketch_fx.cu": {"sha1": None, "bytes_per_launch_full": None}}
+FP64_PEAK_TFLOPS = 1.25  # GB300 nominal FP64 rate; the line reports the measured one beside it
+
+
+def hbm_peak():
+    """Measured copy bandwidth of the GB300s (MEASURED_PEAKS.json, written
+    by the driver), else the profiling recipe's fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+HBM_GBS, HBM_SRC = hbm_peak()
 
 
 def parse():
@@ -53,8 +70,10 @@ def parse():
     p.add_argument("--m", type=int, default=20000)
     p.add_argument("--n", type=int, default=20000)
     p.add_argument("--dtype", choices=["f64", "f32"], default="f64")
-    p.add_argument("--sketch-mode", type=int, default=0,
-                   help="0 FP64 sketch; 1-4 tensor-core precision form with 1-4 digits (FP32 A)")
+    p.add_argument("--sketch-mode", type=int, default=None,
+                   help="0 FP64-pipe Gaussian sketch; 1-4 tensor-core precision form with 1-4 "
+                        "digits (FP32 A); 5 FP64 tensor-core form (FP64 A).  Default: 5 for "
+                        "FP64 A, 0 for FP32 A")
     p.add_argument("--tol", type=float, default=1e-2)
     p.add_argument("--block", type=int, default=50)
     p.add_argument("--sketch", type=int, default=55)
@@ -63,6 +82,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-second-form", action="store_true")
+    p.add_argument("--no-extra-forms", action="store_true",
+                   help="skip the FP64-pipe, tol 1e-4 and FP32 forms")
     p.add_argument("--second-tol", type=float, default=1e-3)
     p.add_argument("--second-noise", type=float, default=1e-10)
     p.add_argument("--e2e-steps", type=int, default=3)
@@ -126,9 +147,13 @@ def aggregate(elapsed_ms, steps, ws, device=None):
     return elapsed_ms, elapsed_ms / (steps * ws)
 
 
+SKETCH_FORMS = {0: "FP64-pipe Gaussian sketch", 5: "FP64 tensor-core sketch (52-bit fixed point)"}
+
+
 def workload_name(a):
     dt = "FP64" if a.dtype == "f64" else "FP32"
-    form = "" if a.sketch_mode == 0 else f", tensor-core sketch with {a.sketch_mode} digit(s)"
+    form = ", " + SKETCH_FORMS.get(a.sketch_mode,
+                                   f"tensor-core precision sketch with {a.sketch_mode} digit(s)")
     return (f"{a.m}x{a.n} {dt} A=U diag(i^-2) V^T + N(0,({a.noise:g})^2) noise, tol {a.tol:g}, "
             f"b={a.block}, c={a.sketch}{form}")
 
@@ -194,70 +219,84 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def traffic_for_sketch():
-    src = os.path.join(ROOT, "paper_2509_21963_gb300", "csrc", "sketch_simt.cu")
+def source_sha1(name):
+    src = os.path.join(ROOT, "paper_2509_21963_gb300", "csrc", name)
     code = re.sub(r"//[^\n]*", "", open(src).read())
-    h = hashlib.sha1(code.encode()).hexdigest()
-    rec = TRAFFIC["sketch_simt.cu"]
-    if rec["sha1"] == h and rec["bytes_per_launch_full"] is not None:
+    return hashlib.sha1(code.encode()).hexdigest()
+
+
+def traffic_for(name):
+    """DRAM bytes per full-size launch from the committed ncu capture, or None
+    once the kernel source has changed since the counters were taken."""
+    rec = TRAFFIC[name]
+    if rec["sha1"] == source_sha1(name) and rec["bytes_per_launch_full"] is not None:
         return rec["bytes_per_launch_full"]
     return None
 
 
-def oracle_sample(a, A_host_cols, frac_cols):
-    """Time the FP64 oracle (Algorithm 1, Lemma 1 form) on a column slab and scale
-    to the full matrix by n / n_slab (the sketch pass, the column selection and
-    the column residual all scale linearly in n)."""
-    import oracle
-    t0 = time.perf_counter()
-    oracle.run(A_host_cols, a.tol, a.block, a.sketch, seed=a.seed, mode=1)
-    dt = time.perf_counter() - t0
-    return dt * 1000.0 * (a.n / A_host_cols.shape[1]), dt
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+    return platform.processor() or platform.machine()
 
 
-def adaptive_oracle_sample(a, A, target_s=12.0):
-    """Oracle on a column slab widened until one run takes about target_s
-    (the slab starts at n/64 and is rescaled from the measured time)."""
+def oracle_run_for(a, A_host, tol=None):
+    """The oracle's run of the same method on the same matrix, for the sketch
+    form a.sketch_mode (FP64 data; FP32 inputs upcast exactly)."""
     import numpy as np
-    import torch
-    ns = max(a.sketch + 1, a.n // 64)
-    while True:
-        slab = np.ascontiguousarray(A[:, :ns].to(torch.float64).cpu().numpy())
-        v, dt = oracle_sample(a, slab, ns)
-        if dt >= 0.5 * target_s or ns >= a.n // 2:
-            return v, dt, ns
-        grow = int(ns * min(8.0, target_s / max(dt, 1e-3)))
-        ns = min(a.n // 2, max(ns + 1, grow))
+    import oracle
+    tol = a.tol if tol is None else tol
+    m = A_host.shape[0]
+    if a.sketch_mode == 5:
+        return oracle.run_fx(A_host, tol, a.block, a.sketch, seed=a.seed)
+    if a.sketch_mode == 0:
+        return oracle.run(A_host, tol, a.block, a.sketch, seed=a.seed, mode=1)
+    Gq = oracle.gaussian_sketch_q8(a.seed, a.sketch, m)
+    Y = oracle.sketch(Gq, oracle.fixed_point(A_host, a.sketch_mode))
+    return oracle.run_y(A_host, tol, a.block, a.sketch, Y)
+
+
+def timed_oracle(a, A_host, threads):
+    import oracle
+    oracle.set_threads(threads)
+    t0 = time.perf_counter()
+    r = oracle_run_for(a, A_host)
+    return (time.perf_counter() - t0) * 1000.0, r
 
 
 def run_reference(a, ws, rank):
+    """The reference arm: the FP64 CPU oracle as it stands (the same method,
+    sketch form and matrix), one whole run per step on all host cores."""
     if rank != 0:
         return 0
-    import numpy as np
     import torch
     dev = "cuda" if torch.cuda.is_available() else "cpu"
     dtype = torch.float64 if a.dtype == "f64" else torch.float32
     A = make_matrix(a, dev, dtype)
-    _, _, ns = adaptive_oracle_sample(a, A, target_s=8.0)
-    slab = np.ascontiguousarray(A[:, :ns].to(torch.float64).cpu().numpy())
+    A_host = A.to(torch.float64).cpu().numpy()
     del A
+    cores = os.cpu_count() or 1
     for _ in range(a.warmup):
-        oracle_sample(a, slab, ns)
+        timed_oracle(a, A_host, cores)
     vals = []
-    t_all = 0.0
     for _ in range(a.steps):
-        v, dt = oracle_sample(a, slab, ns)
-        vals.append(v)
-        t_all += dt
+        ms, r = timed_oracle(a, A_host, cores)
+        vals.append(ms)
     value = sum(vals) / len(vals)
-    sample = (f"oracle on the column slab A[:, :{ns}] of the same matrix (same m, tol, b, c), "
-              f"wall time x n/{ns}")
+    sample = (f"one whole oracle run per step on the {a.m}x{a.n} matrix ({cores} threads, "
+              f"rank {r.rank}, rho {r.rho:.3e}); {a.steps} steps after {a.warmup} warm-up runs")
     line = {"impl": "reference", "metric": "time-to-tolerance per CUR", "value": value, "unit": "ms",
             "n_gpus": ws, "steps": a.steps, "warmup": a.warmup, "ms_per_step": value,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": workload_name(a)},
-            "cpu_baseline": {"value": value, "unit": "ms", "cores": 1, "kind": "oracle",
-                             "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "ms", "cores": cores, "kind": "oracle",
+                             "sample": sample, "cpu_model": cpu_model()},
             "e2e": {"value": value, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -398,8 +437,10 @@ def run_batch(a, ws, rank, local):
     achieved = flops / (value * 1e-3) / 1e12
     ph = B.phase_cycles()
     tot = sum(v for k, v in ph.items() if k != "jobs")
-    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+    fp64_meas = ctx.fp64_tflops()
+    roofline = {"bound": "alu", "achieved": achieved, "peak": fp64_meas, "unit": "TFLOP/s",
+                "frac": achieved / fp64_meas, "traffic": None,
+                "peak_source": "measured FP64 FMA rate (cur_probe_fp64_tflops); nominal 1.25",
                 "kernel": "batch_kernel (whole batch, FP64 SIMT pipe)", "kernel_ms": value,
                 "flops_per_launch": flops,
                 "phase_share": {k: v / tot for k, v in ph.items() if k != "jobs"}}
@@ -658,6 +699,7 @@ def run_serve(a, ws, rank, local):
         plain = {"p50_ms": pct(lat_p, 50), "p99_ms": pct(lat_p, 99),
                  "throughput_rps": len(specs) / end, "busy_s": end}
 
+    fp64_meas = ctx.fp64_tflops()
     cpu = None
     if rank == 0 and ws == 1 and not a.no_cpu_baseline:
         log("serve: cpu baseline")
@@ -685,8 +727,9 @@ def run_serve(a, ws, rank, local):
                        "parallelism": f"replicas x{ws}"},
             "gpu_launches": stats["launches"] - launches0, "clocks": clk, "e2e": e2e,
             "roofline": {"bound": "alu", "achieved": flops / makespan / 1e12,
-                         "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": flops / makespan / 1e12 / FP64_PEAK_TFLOPS, "traffic": None,
+                         "peak": fp64_meas, "unit": "TFLOP/s",
+                         "frac": flops / makespan / 1e12 / fp64_meas, "traffic": None,
+                         "peak_source": "measured FP64 FMA rate (cur_probe_fp64_tflops); nominal 1.25",
                          "kernel": "serve_kernel waves over the makespan (FP64 SIMT pipe)"},
             "plain_serial": plain, "cpu_baseline": cpu,
         }
@@ -805,7 +848,8 @@ def run_precision(a, ws, rank, local):
 # The sketch step alone (for kernel profiles)
 # ---------------------------------------------------------------------------
 def run_sketch_step(a, ws, rank, local):
-    """cur_step_sketch (FP64) or cur_step_sketch_q (digits) on a Gaussian A of
+    """cur_step_sketch (FP64 pipe), cur_step_sketch_fx (FP64 tensor-core form) or
+    cur_step_sketch_q (digits) on a Gaussian A of
     m x n, c = --sketch rows: W warm-up calls, then K timed calls."""
     import torch
     import paper_2509_21963_gb300 as cur
@@ -816,8 +860,12 @@ def run_sketch_step(a, ws, rank, local):
     A = torch.randn(a.m, a.n, device=f"cuda:{local}", generator=g, dtype=dtype)
     ctx = cur.Context(local)
     G = ctx.gaussian(a.seed, a.sketch, a.m)
-    call = (lambda: ctx.sketch(G, A)) if a.sketch_mode == 0 else \
-        (lambda: ctx.sketch_q(G, A, a.sketch_mode))
+    if a.sketch_mode == 0:
+        call = lambda: ctx.sketch(G, A)
+    elif a.sketch_mode == 5:
+        call = lambda: ctx.sketch_fx(G, A)
+    else:
+        call = lambda: ctx.sketch_q(G, A, a.sketch_mode)
     for _ in range(max(a.warmup, 3)):
         call()
     torch.cuda.synchronize()
@@ -834,9 +882,11 @@ def run_sketch_step(a, ws, rank, local):
         line = {"metric": "sketch step time", "value": ms, "unit": "ms", "n_gpus": ws,
                 "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms,
                 "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-                "dtype": a.dtype if a.sketch_mode == 0 else f"bf16x{a.sketch_mode}",
+                "dtype": {0: a.dtype, 5: "f64 data, bf16 digits"}.get(a.sketch_mode,
+                                                                        f"bf16x{a.sketch_mode}"),
                 "data": "synthetic",
-                "config": {"workload": f"sketch Y = G A, A {a.m}x{a.n} {a.dtype} Gaussian, c={a.sketch}"},
+                "config": {"workload": f"sketch Y = G A, A {a.m}x{a.n} {a.dtype} Gaussian, c={a.sketch}",
+                           "sketch_mode": a.sketch_mode},
                 "one_pass_gbs": a.m * a.n * es / ms / 1e6,
                 "fp64_tflops": 2.0 * a.sketch * a.m * a.n / ms / 1e9}
         print(json.dumps(line), flush=True)
@@ -847,6 +897,8 @@ def run_sketch_step(a, ws, rank, local):
 def main():
     global _VERBOSE
     a = parse()
+    if a.sketch_mode is None:
+        a.sketch_mode = 5 if a.dtype == "f64" else 0
     _VERBOSE = a.verbose
     if a.watchdog > 0:
         import faulthandler
@@ -875,7 +927,7 @@ def main():
     if a.impl == "reference":
         return run_reference(a, ws, rank)
 
-    import numpy as np
+    import copy
     import torch
     import paper_2509_21963_gb300 as cur
 
@@ -894,9 +946,10 @@ def main():
 
     last_phases = [None]
 
-    def one_step(timing):
-        st, out = ctx.run_raw(A, a.tol, a.block, a.sketch, a.seed, timing=timing,
-                              sketch_mode=a.sketch_mode)
+    def one_step(timing, AA=None, tol=None, mode=None):
+        AA = A if AA is None else AA
+        st, out = ctx.run_raw(AA, a.tol if tol is None else tol, a.block, a.sketch, a.seed,
+                              timing=timing, sketch_mode=a.sketch_mode if mode is None else mode)
         if st not in (cur.CUR_OK, cur.CUR_TOL_UNREACHED):
             raise cur.CurError(st, ctx.last_error())
         last_phases[0] = {p: float(L.cur_result_phase_ms(out, i)) for i, p in enumerate(cur.PHASES)}
@@ -905,6 +958,22 @@ def main():
                 int(L.cur_result_kernel_launches(out)), int(st))
         L.cur_result_free(out)
         return info
+
+    def time_form(AA, tol, mode, reps, warm=2):
+        """Time-to-tolerance of one form (CUDA events on the library's stream)."""
+        for _ in range(warm):
+            one_step(True, AA, tol, mode)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            info = one_step(True, AA, tol, mode)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return {"time_to_tolerance_ms": e0.elapsed_time(e1) / reps, "rank": info[0],
+                "iterations": info[1], "rho": info[2], "status": info[5],
+                "sketch_mode": mode, "phase_ms": last_phases[0]}
 
     for _ in range(max(a.warmup, 3)):
         info = one_step(True)
@@ -922,7 +991,11 @@ def main():
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
     t0.record(stream)
-    infos = [one_step(True) for _ in range(a.steps)]
+    infos = []
+    phases = []
+    for _ in range(a.steps):
+        infos.append(one_step(True))
+        phases.append(last_phases[0])
     t1.record(stream)
     barrier()
     clk = clocks.stop()
@@ -930,52 +1003,90 @@ def main():
     log(f"timed {a.steps} steps: {elapsed_ms:.2f} ms")
     elapsed_ms, value = aggregate(elapsed_ms, a.steps, ws, device=f"cuda:{local}")
     rank_r, iters, rho, _, launches, status = infos[-1]
-    phase_ms = last_phases[0]
-    sketch_ms = sum(i[3] for i in infos) / len(infos)
+    phase_ms = {p: sum(ph[p] for ph in phases) / len(phases) for p in cur.PHASES}
+    sketch_ms = phase_ms["sketch"]
     ms_per_step = elapsed_ms / a.steps
 
     # end-to-end: the host-buffer C ABI call, H2D of A and D2H of I, J, U inside
     e2e = None
-    if not a.no_e2e:
-        log("e2e: copying A to pinned host memory")
+    A_host = None
+    if not a.no_e2e or (rank == 0 and ws == 1 and not a.no_cpu_baseline):
+        log("copying A to pinned host memory")
         Ah = A.cpu().pin_memory()
-        An = Ah.numpy()
-        ctx.run_host(An, a.tol, a.block, a.sketch, a.seed, sketch_mode=a.sketch_mode)  # warm
+        A_host = Ah.numpy()
+    if not a.no_e2e:
+        ctx.run_host(A_host, a.tol, a.block, a.sketch, a.seed, sketch_mode=a.sketch_mode)  # warm
         torch.cuda.synchronize()
         w0 = time.perf_counter()
         for _ in range(a.e2e_steps):
-            r = ctx.run_host(An, a.tol, a.block, a.sketch, a.seed, sketch_mode=a.sketch_mode)
+            r = ctx.run_host(A_host, a.tol, a.block, a.sketch, a.seed, sketch_mode=a.sketch_mode)
         torch.cuda.synchronize()
         e2e_ms = (time.perf_counter() - w0) * 1000.0 / a.e2e_steps
         log(f"e2e: {e2e_ms:.2f} ms per step")
-        es = An.itemsize
+        es = A_host.itemsize
         e2e = {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": a.m * a.n * es,
                "d2h_bytes_per_step": 16 * r.rank + 8 * r.rank * r.rank + 8 * (r.iterations + 8)}
-        del Ah, An
 
-    # roofline of the dominant kernel: the sketch Y = G A
-    if a.sketch_mode == 0:
+    # roofline of the dominant kernel: the sketch of A (the one full pass)
+    fp64_meas = ctx.fp64_tflops()
+    a_bytes = float(a.m) * a.n * A.element_size()
+    if a.sketch_mode == 5:
+        achieved = a_bytes / (sketch_ms * 1e-3) / 1e9
+        scales_ms = phase_ms["scales"]
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": HBM_GBS, "unit": "GB/s",
+                    "frac": achieved / HBM_GBS, "traffic": traffic_for("sketch_fx.cu"),
+                    "peak_source": f"{HBM_SRC} copy bandwidth",
+                    "kernel": "sketch_fx_kernel<64> (FP64 tensor-core sketch, tcgen05 + TMA) "
+                              "+ its 20 us reduction; algorithmic bytes m*n*8 per launch",
+                    "kernel_ms": sketch_ms,
+                    "sketch_phase": {"column_scales_ms": scales_ms, "total_ms": scales_ms + sketch_ms,
+                                     "hbm_frac_over_two_reads":
+                                         2 * a_bytes / ((scales_ms + sketch_ms) * 1e-3) / 1e9 / HBM_GBS}}
+    elif a.sketch_mode == 0:
         flops = 2.0 * a.sketch * a.m * a.n
         achieved = flops / (sketch_ms * 1e-3) / 1e12
-        roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                    "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                    "traffic": traffic_for_sketch(),
+        roofline = {"bound": "alu", "achieved": achieved, "peak": fp64_meas, "unit": "TFLOP/s",
+                    "frac": achieved / fp64_meas, "traffic": traffic_for("sketch_simt.cu"),
+                    "peak_source": "measured FP64 FMA rate (cur_probe_fp64_tflops)",
                     "kernel": "sketch_kernel<FP64 A> (Y = G A, FP64 SIMT pipe)",
                     "kernel_ms": sketch_ms,
-                    "hbm_frac_of_measured": (a.m * a.n * A.element_size() / (sketch_ms * 1e-3)) / HBM_GBS / 1e9}
+                    "hbm_frac_of_measured": a_bytes / (sketch_ms * 1e-3) / 1e9 / HBM_GBS}
     else:
-        # algorithmic bytes: two reads of A (column scales, then the sketch pass)
-        byts = 2.0 * a.m * a.n * A.element_size()
+        byts = 2.0 * a_bytes   # two reads of A: column scales, then the sketch pass
         achieved = byts / (sketch_ms * 1e-3) / 1e9
         roofline = {"bound": "hbm", "achieved": achieved, "peak": HBM_GBS, "unit": "GB/s",
                     "frac": achieved / HBM_GBS, "traffic": None,
+                    "peak_source": f"{HBM_SRC} copy bandwidth",
                     "kernel": f"sketch phase, precision form ({a.sketch_mode} digits): colmax + "
                               "sketch_tc_kernel + reduce", "kernel_ms": sketch_ms}
 
-    # second form: tighter tolerance on the low-noise variant of the spectrum
+    # the CPU oracle on the same matrix: all host cores and one core
+    cpu = None
+    if rank == 0 and ws == 1 and not a.no_cpu_baseline:
+        cores = os.cpu_count() or 1
+        log(f"cpu baseline: oracle on the whole matrix, {cores} threads")
+        ms_all, ro = timed_oracle(a, A_host, cores)
+        log(f"cpu baseline: {ms_all:.0f} ms ({cores} threads); one core next")
+        ms_one, _ = timed_oracle(a, A_host, 1)
+        log(f"cpu baseline: {ms_one:.0f} ms (1 thread)")
+        cpu = {"value": ms_all, "unit": "ms", "cores": cores, "kind": "oracle",
+               "one_core_ms": ms_one, "nproc": cores, "cpu_model": cpu_model(),
+               "sample": f"one oracle run of the same method (same sketch form) on the whole "
+                         f"{a.m}x{a.n} matrix with {cores} threads; one_core_ms: the same run "
+                         "on one thread",
+               "oracle_rank": ro.rank, "oracle_rho": ro.rho,
+               "same_indices_as_gpu": bool(ro.rank == rank_r)}
+    del A_host
+
+    extra = {}
+    if not a.no_extra_forms and a.dtype == "f64" and a.sketch_mode == 5:
+        log("FP64-pipe Gaussian sketch on the same matrix")
+        extra["fp64_pipe_sketch"] = time_form(A, a.tol, 0, 2, warm=1)
+
+    # further forms of the configuration: tighter tolerances on the low-noise
+    # spectrum, then the FP32 matrix
     second = None
     if not a.no_second_form:
-        import copy
         b2 = copy.copy(a)
         b2.tol, b2.noise = a.second_tol, a.second_noise
         del A
@@ -983,28 +1094,28 @@ def main():
         log("second form: generating A")
         A = make_matrix(b2, f"cuda:{local}", dtype)
         torch.cuda.synchronize()
-        for _ in range(2):
-            st2, out2 = ctx.run_raw(A, b2.tol, a.block, a.sketch, a.seed, timing=True,
-                                    sketch_mode=a.sketch_mode)
-            L.cur_result_free(out2)
-        s0 = torch.cuda.Event(enable_timing=True)
-        s1 = torch.cuda.Event(enable_timing=True)
+        second = time_form(A, b2.tol, a.sketch_mode, max(2, a.steps // 2))
+        second["workload"] = workload_name(b2)
+        log(f"second form: {second['time_to_tolerance_ms']:.2f} ms, rank {second['rank']}")
+        if not a.no_extra_forms:
+            b3 = copy.copy(b2)
+            b3.tol = 1e-4
+            extra["tol_1e-4"] = time_form(A, 1e-4, a.sketch_mode, 2, warm=1)
+            extra["tol_1e-4"]["workload"] = workload_name(b3)
+            log(f"tol 1e-4: {extra['tol_1e-4']['time_to_tolerance_ms']:.2f} ms")
+    if not a.no_extra_forms and a.dtype == "f64":
+        b4 = copy.copy(a)
+        b4.dtype = "f32"
+        del A
+        torch.cuda.empty_cache()
+        log("FP32 forms: generating A")
+        A = make_matrix(b4, f"cuda:{local}", torch.float32)
         torch.cuda.synchronize()
-        s0.record(stream)
-        reps = max(2, a.steps // 2)
-        for _ in range(reps):
-            st2, out2 = ctx.run_raw(A, b2.tol, a.block, a.sketch, a.seed, timing=True,
-                                    sketch_mode=a.sketch_mode)
-            info2 = (int(L.cur_result_rank(out2)), int(L.cur_result_iterations(out2)),
-                     float(L.cur_result_err(out2)), int(st2))
-            ph = {p: float(L.cur_result_phase_ms(out2, i)) for i, p in enumerate(cur.PHASES)}
-            L.cur_result_free(out2)
-        s1.record(stream)
-        torch.cuda.synchronize()
-        second = {"workload": workload_name(b2), "time_to_tolerance_ms": s0.elapsed_time(s1) / reps,
-                  "rank": info2[0], "iterations": info2[1], "rho": info2[2], "status": info2[3],
-                  "phase_ms": ph}
-        log(f"second form: {second['time_to_tolerance_ms']:.2f} ms, rank {info2[0]}")
+        for mode, key in ((0, "fp32_fp64_pipe_sketch"), (2, "fp32_tensor_core_2_digits")):
+            b4.sketch_mode = mode
+            extra[key] = time_form(A, a.tol, mode, 3)
+            extra[key]["workload"] = workload_name(b4)
+            log(f"{key}: {extra[key]['time_to_tolerance_ms']:.2f} ms")
 
     # the paper's own threshold experiment (Sec. 5.1), on request
     paper = None
@@ -1015,13 +1126,14 @@ def main():
         log("paper workload: generating the 30000^2 Low-Rank matrix")
         A = inputs.low_rank_gaussian_torch(30000, 30000, 2000, seed=5, device=f"cuda:{local}")
         torch.cuda.synchronize()
-        st3, out3 = ctx.run_raw(A, 1e-6, 250, 275, a.seed, timing=True)   # warm
+        pmode = 5
+        st3, out3 = ctx.run_raw(A, 1e-6, 250, 275, a.seed, timing=True, sketch_mode=pmode)   # warm
         L.cur_result_free(out3)
         p0 = torch.cuda.Event(enable_timing=True)
         p1 = torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         p0.record(stream)
-        st3, out3 = ctx.run_raw(A, 1e-6, 250, 275, a.seed, timing=True)
+        st3, out3 = ctx.run_raw(A, 1e-6, 250, 275, a.seed, timing=True, sketch_mode=pmode)
         p1.record(stream)
         torch.cuda.synchronize()
         r3 = int(L.cur_result_rank(out3))
@@ -1035,35 +1147,31 @@ def main():
         terr = float(torch.linalg.norm(E) / torch.linalg.norm(A))
         del E
         ms3 = p0.elapsed_time(p1)
-        paper = {"workload": "Low-Rank 30000x30000 FP64 (G1 G2^T, rank 2000), tol 1e-6, b=250, c=275",
+        paper = {"workload": "Low-Rank 30000x30000 FP64 (G1 G2^T, rank 2000), tol 1e-6, b=250, c=275, "
+                             + SKETCH_FORMS[pmode],
                  "time_to_tolerance_ms": ms3, "rank": r3, "rho": res3.rho,
                  "true_rel_error": terr, "phase_ms": res3.phase_ms,
                  "paper_ms_48core_cpu": 12000.0, "ratio_vs_paper": ms3 / 12000.0}
         log(f"paper workload: {ms3:.1f} ms, rank {r3}, true error {terr:.2e}")
-
-    cpu = None
-    if rank == 0 and ws == 1 and not a.no_cpu_baseline:
-        log("cpu baseline: oracle on a column slab")
-        v, dt, ns = adaptive_oracle_sample(a, A)
-        log(f"cpu baseline: {dt:.2f} s on {ns} columns")
-        cpu = {"value": v, "unit": "ms", "cores": 1, "kind": "oracle",
-               "sample": f"one oracle run on the column slab A[:, :{ns}] ({dt:.1f} s), scaled by n/{ns}"}
 
     if rank == 0:
         line = {
             "metric": "time-to-tolerance per CUR", "value": value, "unit": "ms", "n_gpus": ws,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms_per_step,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if a.sketch_mode == 0 else f"bf16x{a.sketch_mode} sketch, f64 loop",
+            "dtype": {0: "f64", 5: "f64 loop; sketch on bf16 tensor cores, exact 52-bit fixed point"}.get(
+                a.sketch_mode, f"bf16x{a.sketch_mode} sketch, f64 loop"),
             "data": "synthetic",
             "config": {"workload": workload_name(a), "m": a.m, "n": a.n, "tol": a.tol,
                        "block_size": a.block, "sketch_size": a.sketch, "a_dtype": a.dtype,
+                       "sketch_mode": a.sketch_mode,
                        "rank": rank_r, "iterations": iters, "rho": rho, "status": status,
                        "l2": "inputs larger than L2 (A is resident in HBM)",
                        "parallelism": f"replicas x{ws}"},
             "gpu_launches": launches * a.steps,
             "clocks": clk, "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu,
-            "phase_ms": phase_ms, "second_form": second, "paper_workload": paper,
+            "fp64_peak": {"measured_tflops": fp64_meas, "nominal_tflops": FP64_PEAK_TFLOPS},
+            "phase_ms": phase_ms, "second_form": second, "forms": extra, "paper_workload": paper,
         }
         print(json.dumps(line), flush=True)
     ctx.close()

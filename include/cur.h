@@ -97,7 +97,10 @@ typedef enum {
   CUR_PHASE_FACTORS = 5,   /* Rt_k, N_k^+, L_k (Lemma 1 factors)                */
   CUR_PHASE_COL_RES = 6,   /* S^col update and ||S^col||_F (rho_k)              */
   CUR_PHASE_CORE = 7,      /* U = A(I,J)^+ at exit                              */
-  CUR_PHASE_COUNT = 8
+  CUR_PHASE_SCALES = 8,    /* FP64 tensor-core sketch only: G_q and the column
+                              scales (a read of A); CUR_PHASE_SKETCH is then the
+                              tensor-core pass and its reduction                */
+  CUR_PHASE_COUNT = 9
 } cur_phase;
 
 /* Create a context on `device` that enqueues on `cuda_stream` (a cudaStream_t;

@@ -109,6 +109,13 @@ int cur_step_lupp_noalloc(int device, void *cuda_stream, const double *X, int64_
                           int64_t nr, int64_t ncand, int64_t steps, uint8_t *mask,
                           int64_t *piv, char *err, size_t err_len);
 
+/* Measured FP64 FMA rate of the context's device in TFLOP/s (*tflops): five
+ * timed launches of independent FMA chains over all SMs.  The paper has no
+ * counterpart; it is the denominator of the FP64-pipe roofline figures.  It
+ * allocates 8 bytes of device memory for the duration of the call and
+ * synchronises the context's stream. */
+int cur_probe_fp64_tflops(cur_ctx *ctx, double *tflops);
+
 #ifdef __cplusplus
 }
 #endif

@@ -35,9 +35,13 @@ def build(force: bool = False) -> str:
         os.path.getmtime(f) > os.path.getmtime(_LIB) for f in (_SRC, _HDR))
     if force or stale:
         tmp = _LIB + f".tmp{os.getpid()}"
-        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
-               "-o", tmp, _SRC, "-lm"]
-        subprocess.run(cmd, check=True)
+        base = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
+                "-o", tmp, _SRC, "-lm"]
+        # OpenMP over independent outer loops only (no split reductions), so the
+        # arithmetic is that of the serial build; without libgomp, build serial
+        r = subprocess.run(base[:-1] + ["-fopenmp", "-lm"], capture_output=True)
+        if r.returncode != 0:
+            subprocess.run(base, check=True)
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -86,6 +90,8 @@ def lib():
         L.cur_oracle_run_y.argtypes = [vp, i64, i64, i64, dbl, i64, i64, vp, i64,
                                        ctypes.c_int, ctypes.POINTER(_Out)]
         L.cur_oracle_run_y.restype = ctypes.c_int
+        L.cur_oracle_set_threads.argtypes = [ctypes.c_int]
+        L.cur_oracle_threads.restype = ctypes.c_int
         L.cur_oracle_risk_threshold.argtypes = [dbl, dbl, dbl, dbl]
         L.cur_oracle_risk_threshold.restype = dbl
     return _lib
@@ -307,3 +313,12 @@ def run_fx(A: np.ndarray, tol: float, b: int, c: int, seed: int = 0, max_rank: i
     A = _f64(A)
     Gq = gaussian_sketch_q8(seed, c, A.shape[0])
     return run_y(A, tol, b, c, sketch_fx(Gq, A), max_rank=max_rank, mode=mode, want_S=want_S)
+
+
+def set_threads(n: int) -> None:
+    """Host threads of the oracle's parallel loops (results do not change)."""
+    lib().cur_oracle_set_threads(int(n))
+
+
+def threads() -> int:
+    return int(lib().cur_oracle_threads())

@@ -37,6 +37,10 @@
  */
 #include "cur_oracle.h"
 
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
 #include <float.h>
 #include <math.h>
 #include <stdlib.h>
@@ -89,6 +93,7 @@ void cur_oracle_gaussian_sketch(uint64_t seed, int64_t c, int64_t m,
                                 double *G) {
   const double two_pi = 6.283185307179586476925286766559;
   const uint64_t key[2] = {seed, 0x43555200ULL};
+#pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < c; ++i) {
     for (int64_t q = 0; 4 * q < m; ++q) {
       uint64_t ctr[4] = {(uint64_t)q, (uint64_t)i, 0, 0};
@@ -115,6 +120,7 @@ void cur_oracle_gaussian_sketch(uint64_t seed, int64_t c, int64_t m,
 /* ------------------------------------------------------------------------ */
 void cur_oracle_sketch(const double *G, int64_t c, const double *A, int64_t m,
                        int64_t n, int64_t lda, double *Y) {
+#pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < c; ++i) {
     double *y = Y + i * n;
     for (int64_t j = 0; j < n; ++j) y[j] = 0.0;
@@ -163,6 +169,7 @@ int cur_oracle_lupp(const double *M, int64_t p, int64_t q, int64_t ldm,
     excluded[best] = 1;
     if (best_abs == 0.0) continue; /* zero pivot: nothing to eliminate */
     const double *prow = W + best * q;
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < p; ++i) {
       if (excluded[i]) continue;
       double l = W[i * q + t] / prow[t];
@@ -304,6 +311,7 @@ static void row_residual(const double *A, int64_t m, int64_t lda,
       for (int64_t l = 0; l < r; ++l) s = s + U[a * r + l] * A[I[l] * lda + Jk[t]];
       X[a * bk + t] = s;
     }
+#pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < m; ++i)
     for (int64_t t = 0; t < bk; ++t) {
       double s = 0.0;
@@ -325,6 +333,7 @@ static void col_residual(const double *Y, int64_t c, int64_t n,
       for (int64_t l = 0; l < r; ++l) s = s + Y[i * n + J[l]] * U[l * r + a];
       W[i * r + a] = s;
     }
+#pragma omp parallel for collapse(2) schedule(static)
   for (int64_t i = 0; i < c; ++i)
     for (int64_t j = 0; j < n; ++j) {
       double s = 0.0;
@@ -445,6 +454,7 @@ int cur_oracle_run_y(const double *A, int64_t m, int64_t n, int64_t lda, double 
     if (mode == 0) {
       row_residual(A, m, lda, I, J, r, U, J + r, bk, Srow);
     } else {
+#pragma omp parallel for schedule(static)
       for (int64_t i = 0; i < m; ++i)
         for (int64_t t = 0; t < bk; ++t)
           Srow[i * bk + t] = lemma_residual_entry(A, lda, L, max_rank, Rt, n, r, i, J[r + t]);
@@ -473,10 +483,12 @@ int cur_oracle_run_y(const double *A, int64_t m, int64_t n, int64_t lda, double 
       }
       cur_oracle_qrcp_pinv(N, bk, bk, bk, thr_scale * (double)rn, Np, NULL, NULL);
       /* Rt_k = S_{k-1}(I_k, :) */
+#pragma omp parallel for collapse(2) schedule(static)
       for (int64_t a = 0; a < bk; ++a)
         for (int64_t j = 0; j < n; ++j)
           Rt[(r + a) * n + j] = lemma_residual_entry(A, lda, L, max_rank, Rt, n, r, I[r + a], j);
       /* L_k = S^row N^+  (m x bk) */
+#pragma omp parallel for schedule(static)
       for (int64_t i = 0; i < m; ++i)
         for (int64_t a = 0; a < bk; ++a) {
           double s = 0.0;
@@ -490,6 +502,7 @@ int cur_oracle_run_y(const double *A, int64_t m, int64_t n, int64_t lda, double 
           for (int64_t t = 0; t < bk; ++t) s = s + S[i * n + J[r + t]] * Np[t * bk + a];
           T1[i * bk + a] = s;
         }
+#pragma omp parallel for collapse(2) schedule(static)
       for (int64_t i = 0; i < c; ++i)
         for (int64_t j = 0; j < n; ++j) {
           double s = 0.0;
@@ -683,7 +696,10 @@ void cur_oracle_fixed_point_digits(double x, int E, int S, double *d) {
  * product then fits an int64; the sum is taken in 128 bits). */
 void cur_oracle_sketch_fx(const double *Gq, int64_t c, const double *A, int64_t m,
                           int64_t n, int64_t lda, int Q, double *Y) {
+#pragma omp parallel
+  {
   int64_t *X = (int64_t *)malloc(sizeof(int64_t) * (size_t)(m > 0 ? m : 1));
+#pragma omp for schedule(dynamic, 16)
   for (int64_t j = 0; j < n; ++j) {
     double mx = 0.0;
     int finite = 1;
@@ -706,4 +722,23 @@ void cur_oracle_sketch_fx(const double *Gq, int64_t c, const double *A, int64_t 
     }
   }
   free(X);
+  }
+}
+
+/* Host threads used by the loops above (OpenMP builds; 1 otherwise).  Only
+ * independent outer loops run in parallel, so results do not depend on it. */
+void cur_oracle_set_threads(int nthreads) {
+#ifdef _OPENMP
+  omp_set_num_threads(nthreads > 0 ? nthreads : 1);
+#else
+  (void)nthreads;
+#endif
+}
+
+int cur_oracle_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
 }

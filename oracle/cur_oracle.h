@@ -150,6 +150,11 @@ double cur_oracle_true_error(const double *A, int64_t m, int64_t n, int64_t lda,
                              const int64_t *I, const int64_t *J, int64_t r,
                              const double *U);
 
+/* Host threads of the OpenMP-parallel outer loops (1 without OpenMP); the
+ * results are the same for every thread count (no reduction is split). */
+void cur_oracle_set_threads(int nthreads);
+int cur_oracle_threads(void);
+
 /* Risk-aware threshold of Sec. 3.3: eps (1+delta) sqrt(1 - 2 sqrt(-ln(alpha)/c)),
  * or -1 when c <= -4 ln(alpha) (bound undefined). */
 double cur_oracle_risk_threshold(double eps, double delta, double alpha, double c);

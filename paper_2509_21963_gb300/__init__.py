@@ -27,7 +27,8 @@ CUR_OK, CUR_EINVAL, CUR_ENONFINITE, CUR_ENOMEM, CUR_EBUDGET, CUR_ECUDA, CUR_ETIM
 CUR_F64, CUR_F32 = 0, 1
 CUR_SKETCH_F64, CUR_SKETCH_BF16, CUR_SKETCH_BF16X2, CUR_SKETCH_BF16X3, CUR_SKETCH_BF16X4 = 0, 1, 2, 3, 4
 CUR_SKETCH_F64_TC = 5
-PHASES = ("gaussian", "sketch", "lupp_col", "row_res", "lupp_row", "factors", "col_res", "core")
+PHASES = ("gaussian", "sketch", "lupp_col", "row_res", "lupp_row", "factors", "col_res", "core",
+          "scales")
 
 _STATUS_NAMES = {0: "CUR_OK", 1: "CUR_EINVAL", 2: "CUR_ENONFINITE", 3: "CUR_ENOMEM",
                  4: "CUR_EBUDGET", 5: "CUR_ECUDA", 6: "CUR_ETIMEOUT", 7: "CUR_TOL_UNREACHED"}
@@ -91,6 +92,7 @@ _SIGNATURES = {
     "cur_step_sketch": (_int, [_vp, _vp, _i64, _vp, _i64, _i64, _i64, _int, _vp, _vp]),
     "cur_step_sketch_q": (_int, [_vp, _vp, _i64, _vp, _i64, _i64, _i64, _int, _vp, _vp]),
     "cur_step_sketch_fx": (_int, [_vp, _vp, _i64, _vp, _i64, _i64, _i64, _vp, _vp]),
+    "cur_probe_fp64_tflops": (_int, [_vp, ctypes.POINTER(_dbl)]),
     "cur_step_lupp": (_int, [_vp, _vp, _i64, _i64, _i64, _i64, _vp, _vp]),
     "cur_step_pinv": (_int, [_vp, _vp, _i64, _i64, _i64, _dbl, _vp, _vp]),
     "cur_step_lupp_noalloc": (_int, [_int, _vp, _vp, _i64, _i64, _i64, _i64, _vp, _vp,
@@ -318,6 +320,12 @@ class Context:
         _check(self.ptr, lib().cur_step_sketch_fx(self.ptr, _vp(G.data_ptr()), c, _vp(A.data_ptr()), m,
                                                   n, A.stride(0), _vp(Y.data_ptr()), ctypes.byref(ss)))
         return Y, ss.value
+
+    def fp64_tflops(self) -> float:
+        """Measured FP64 FMA rate of the device (TFLOP/s)."""
+        v = ctypes.c_double()
+        _check(self.ptr, lib().cur_probe_fp64_tflops(self.ptr, ctypes.byref(v)))
+        return v.value
 
     def lupp(self, X, steps: int, mask=None):
         import torch

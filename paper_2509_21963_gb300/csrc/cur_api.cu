@@ -354,8 +354,11 @@ int sketch_fx(cur_ctx* ctx, const double* G, int64_t c, const double* A, int64_t
   TRY(ensure(ctx, scratch_id, sketch_fx_scratch_bytes(c, m, n)));
   TRY(ensure(ctx, parts_id, sizeof(double) * (size_t)sketch_fx_max_parts(c, n)));
   int64_t nparts = 0;
-  CK(launch_sketch_fx(env, G, c, A, lda, m, n, ctx->buf[scratch_id].p, Y,
-                      bp<double>(ctx, parts_id), &nparts, &dstat(ctx)->err));
+  tick(ctx, CUR_PHASE_SCALES);
+  CK(launch_sketch_fx_scales(env, G, c, A, lda, m, n, ctx->buf[scratch_id].p));
+  tick(ctx, CUR_PHASE_SKETCH);
+  CK(launch_sketch_fx_main(env, c, A, lda, m, n, ctx->buf[scratch_id].p, Y,
+                           bp<double>(ctx, parts_id), &nparts, &dstat(ctx)->err));
   ctx->launches += 4 + (c + 63) / 64;
   TRY(sum_parts(ctx, bp<double>(ctx, parts_id), nparts, &dstat(ctx)->scalar[slot]));
   return CUR_OK;

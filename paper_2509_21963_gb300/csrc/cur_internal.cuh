@@ -151,11 +151,16 @@ cudaError_t launch_gaussian_q8(const LaunchEnv& env, const double* G, int64_t c,
 // 16-byte aligned base.  Any c >= 1 (row groups of 64 rows of G, one pass of A
 // each).  A column holding Inf/NaN gives NaN in Y (and so in the sum of
 // squares).  Writes *nparts sum-of-squares partials into sumsq_part.
+// Two launches on the same scratch: the scales (G_q, column exponents, zeroed
+// sums), then the tensor-core pass and the reduction into Y.
 size_t sketch_fx_scratch_bytes(int64_t c, int64_t m, int64_t n);
 int64_t sketch_fx_max_parts(int64_t c, int64_t n);
-cudaError_t launch_sketch_fx(const LaunchEnv& env, const double* G, int64_t c, const double* A,
-                             int64_t lda, int64_t m, int64_t n, void* scratch, double* Y,
-                             double* sumsq_part, int64_t* nparts, int* err);
+cudaError_t launch_sketch_fx_scales(const LaunchEnv& env, const double* G, int64_t c,
+                                    const double* A, int64_t lda, int64_t m, int64_t n,
+                                    void* scratch);
+cudaError_t launch_sketch_fx_main(const LaunchEnv& env, int64_t c, const double* A, int64_t lda,
+                                  int64_t m, int64_t n, void* scratch, double* Y,
+                                  double* sumsq_part, int64_t* nparts, int* err);
 
 // ---- gather.cu ------------------------------------------------------------
 // out[a * ldo + t] = src(r(a), c(t)) for a < rows, t < cols, where

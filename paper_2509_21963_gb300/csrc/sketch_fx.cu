@@ -561,20 +561,45 @@ int64_t sketch_fx_max_parts(int64_t c, int64_t n) {
   return ((n + 255) / 256) * ((c + kReduceRows - 1) / kReduceRows);
 }
 
-cudaError_t launch_sketch_fx(const LaunchEnv& env, const double* G, int64_t c, const double* A,
-                             int64_t lda, int64_t m, int64_t n, void* scratch, double* Y,
-                             double* sumsq_part, int64_t* nparts, int* err) {
-  if (c < 1 || m < 1 || n < 1 || lda < n || (lda & 1) || (reinterpret_cast<uintptr_t>(A) & 15))
-    return cudaErrorInvalidValue;
+namespace {
+struct FxScratch {
+  uint16_t* Gq;
+  unsigned long long* cmax;
+  int* cexp;
+  long long* acc_lo;
+  long long* acc_hi;
+};
+
+FxScratch carve_fx(void* scratch, int64_t c, int64_t m, int64_t n) {
   const int64_t ldq = ldq_of(m);
   char* p = static_cast<char*>(scratch);
   auto take = [&](size_t x) { char* r = p; p += (x + 255) / 256 * 256; return r; };
-  uint16_t* Gq = (uint16_t*)take(sizeof(uint16_t) * (size_t)(c * ldq));
-  unsigned long long* cmax = (unsigned long long*)take(sizeof(unsigned long long) * (size_t)n);
-  int* cexp = (int*)take(sizeof(int) * (size_t)n);
+  FxScratch f;
+  f.Gq = (uint16_t*)take(sizeof(uint16_t) * (size_t)(c * ldq));
+  f.cmax = (unsigned long long*)take(sizeof(unsigned long long) * (size_t)n);
+  f.cexp = (int*)take(sizeof(int) * (size_t)n);
   long long* acc = (long long*)take(2 * sizeof(long long) * (size_t)(c * n));
-  long long* acc_lo = acc;
-  long long* acc_hi = acc + c * n;
+  f.acc_lo = acc;
+  f.acc_hi = acc + c * n;
+  return f;
+}
+
+bool fx_args_ok(int64_t c, const double* A, int64_t lda, int64_t m, int64_t n) {
+  return c >= 1 && m >= 1 && n >= 1 && lda >= n && !(lda & 1) &&
+         !(reinterpret_cast<uintptr_t>(A) & 15);
+}
+}  // namespace
+
+cudaError_t launch_sketch_fx_scales(const LaunchEnv& env, const double* G, int64_t c,
+                                    const double* A, int64_t lda, int64_t m, int64_t n,
+                                    void* scratch) {
+  if (!fx_args_ok(c, A, lda, m, n)) return cudaErrorInvalidValue;
+  const int64_t ldq = ldq_of(m);
+  const FxScratch f = carve_fx(scratch, c, m, n);
+  uint16_t* Gq = f.Gq;
+  unsigned long long* cmax = f.cmax;
+  int* cexp = f.cexp;
+  long long* acc = f.acc_lo;
 
   cudaError_t e = launch_gaussian_q8(env, G, c, m, ldq, Gq);
   if (e == cudaSuccess) e = cudaMemsetAsync(cmax, 0, sizeof(unsigned long long) * (size_t)n, env.stream);
@@ -585,9 +610,21 @@ cudaError_t launch_sketch_fx(const LaunchEnv& env, const double* G, int64_t c, c
     dim3 grid((unsigned)((n + 255) / 256), (unsigned)((m + rows_per - 1) / rows_per));
     colmax_f64_kernel<<<grid, 256, 0, env.stream>>>(A, lda, m, n, rows_per, cmax);
     colexp_f64_kernel<<<(unsigned)((n + 255) / 256), 256, 0, env.stream>>>(cmax, n, cexp);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sketch_fx_main(const LaunchEnv& env, int64_t c, const double* A, int64_t lda,
+                                  int64_t m, int64_t n, void* scratch, double* Y,
+                                  double* sumsq_part, int64_t* nparts, int* err) {
+  if (!fx_args_ok(c, A, lda, m, n)) return cudaErrorInvalidValue;
+  const int64_t ldq = ldq_of(m);
+  const FxScratch f = carve_fx(scratch, c, m, n);
+  const uint16_t* Gq = f.Gq;
+  int* cexp = f.cexp;
+  long long* acc_lo = f.acc_lo;
+  long long* acc_hi = f.acc_hi;
+  cudaError_t e = cudaSuccess;
   EncodeTiledFn enc = encode_fn();
   if (!enc) return cudaErrorNotSupported;
   CUtensorMap mA;

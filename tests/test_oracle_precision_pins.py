@@ -272,3 +272,23 @@ def test_true_error_matches_numpy():
     assert abs(oracle.true_error(A, I, J, U) - ref) <= 1e-13 * max(ref, 1.0)
     # U^T or swapped roles change the value
     assert abs(oracle.true_error(A, I, J, U.T) - ref) > 1e-3
+
+
+def test_threads_do_not_change_results():
+    """The oracle's parallel loops are independent outer loops (no split
+    reduction): one thread and many give bit-identical runs."""
+    A = inputs.cfg_small(6)
+    t = oracle.threads()
+    try:
+        oracle.set_threads(1)
+        a = oracle.run_fx(A, 1e-6, 10, 30, seed=1)
+        b = oracle.run(A, 1e-6, 10, 30, seed=1, mode=0)
+        oracle.set_threads(max(t, 4))
+        c = oracle.run_fx(A, 1e-6, 10, 30, seed=1)
+        d = oracle.run(A, 1e-6, 10, 30, seed=1, mode=0)
+    finally:
+        oracle.set_threads(t)
+    assert np.array_equal(a.I, c.I) and np.array_equal(a.J, c.J)
+    assert np.array_equal(a.rho_hist, c.rho_hist) and np.array_equal(a.U, c.U)
+    assert np.array_equal(b.I, d.I) and np.array_equal(b.rho_hist, d.rho_hist)
+    assert np.array_equal(b.U, d.U)
