@@ -75,11 +75,13 @@ int cur_batch_set_team(cur_batch *batch, int team);
 int cur_batch_get_schedule(const cur_batch *batch, int *team, int *grid, int *teams,
                            int *graph);
 
-/* Autotuner: run the whole batch once per candidate team size (candidates:
- * host array of ncand sizes, or NULL for {1, 2, 4, 8, 16}), time each run
- * with CUDA events, keep the fastest.  Every trial is a complete, valid run,
- * so the results of the last trial are available afterwards.  *best_team and
- * *best_ms (optional) receive the choice and its time. */
+/* Autotuner: for each candidate team size (candidates: host array of ncand
+ * sizes, or NULL for {1, 2, 4, 8, 16}) capture the launch graph first, then
+ * run the whole batch twice, timing each run with CUDA events; the faster run
+ * is the candidate's time and the fastest candidate is kept.  Every trial is
+ * a complete, valid run, so the results of the last trial are available
+ * afterwards.  *best_team and *best_ms (optional) receive the choice and its
+ * time. */
 int cur_batch_tune(cur_batch *batch, const int *candidates, int ncand, int *best_team,
                    double *best_ms);
 

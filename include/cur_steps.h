@@ -95,8 +95,11 @@ int cur_step_pinv(cur_ctx *ctx, const double *M, int64_t p, int64_t q,
  *   Scratch: a fixed 16 MiB device array inside the library (held by every GPU
  *   that loads the library until the process exits) that must hold
  *   nr * ncand + 2 * G * max(nr + 2, 34) doubles plus 256 bytes, G <= the SM count
- *   (e.g. 55 x 20000 fits); larger problems and nr > 6144 return CUR_EINVAL
- *   with a message in err.  The call allocates nothing (no cudaMalloc,
+ *   (e.g. 55 x 20000 fits); larger problems return CUR_EINVAL with a
+ *   message in err that states the bytes needed.  Device errors map as for
+ *   cur_step_lupp: a timed-out barrier CUR_ETIMEOUT, too few eligible
+ *   candidates CUR_EINVAL, any other device status CUR_ECUDA with its code in
+ *   err.  The call allocates nothing (no cudaMalloc,
  *   cudaFree or allocating library routine).
  *   Set-up: the first call on a device resolves the array's device address
  *   (cudaGetSymbolAddress) with that device current; make that first call
@@ -108,6 +111,17 @@ int cur_step_pinv(cur_ctx *ctx, const double *M, int64_t p, int64_t q,
 int cur_step_lupp_noalloc(int device, void *cuda_stream, const double *X, int64_t ldx,
                           int64_t nr, int64_t ncand, int64_t steps, uint8_t *mask,
                           int64_t *piv, char *err, size_t err_len);
+
+/* Test hook for the failure path of the library's bounded device waits (the
+ * paper has no counterpart): launches a kernel whose wait cannot complete and
+ * gives up after budget_ms (0 < budget_ms <= 5000, converted to cycles at the
+ * device's clock rate).  which = 0: `nblocks` CTAs (1 <= nblocks <= SM count)
+ * arrive at the software grid barrier expecting nblocks + 1; which = 1: one
+ * CTA waits on an mbarrier phase that gets one of its two arrivals.  The wait
+ * records the timeout in the context's status word and the kernel returns,
+ * so the call returns CUR_ETIMEOUT and the context stays usable.  Nothing
+ * faults or waits without a limit.  Synchronises the context's stream. */
+int cur_test_wait_timeout(cur_ctx *ctx, int which, int nblocks, double budget_ms);
 
 /* Measured FP64 FMA rate of the context's device in TFLOP/s (*tflops): five
  * timed launches of independent FMA chains over all SMs.  The paper has no

@@ -93,6 +93,7 @@ _SIGNATURES = {
     "cur_step_sketch_q": (_int, [_vp, _vp, _i64, _vp, _i64, _i64, _i64, _int, _vp, _vp]),
     "cur_step_sketch_fx": (_int, [_vp, _vp, _i64, _vp, _i64, _i64, _i64, _vp, _vp]),
     "cur_probe_fp64_tflops": (_int, [_vp, ctypes.POINTER(_dbl)]),
+    "cur_test_wait_timeout": (_int, [_vp, _int, _int, _dbl]),
     "cur_step_lupp": (_int, [_vp, _vp, _i64, _i64, _i64, _i64, _vp, _vp]),
     "cur_step_pinv": (_int, [_vp, _vp, _i64, _i64, _i64, _dbl, _vp, _vp]),
     "cur_step_lupp_noalloc": (_int, [_int, _vp, _vp, _i64, _i64, _i64, _i64, _vp, _vp,
@@ -320,6 +321,10 @@ class Context:
         _check(self.ptr, lib().cur_step_sketch_fx(self.ptr, _vp(G.data_ptr()), c, _vp(A.data_ptr()), m,
                                                   n, A.stride(0), _vp(Y.data_ptr()), ctypes.byref(ss)))
         return Y, ss.value
+
+    def wait_timeout_status(self, which: int, nblocks: int = 2, budget_ms: float = 2.0) -> int:
+        """Status of cur_test_wait_timeout (CUR_ETIMEOUT when the bounded wait gave up)."""
+        return lib().cur_test_wait_timeout(self.ptr, int(which), int(nblocks), float(budget_ms))
 
     def fp64_tflops(self) -> float:
         """Measured FP64 FMA rate of the device (TFLOP/s)."""

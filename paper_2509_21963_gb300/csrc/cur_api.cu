@@ -828,6 +828,23 @@ int cur_step_sketch_fx(cur_ctx* ctx, const double* G, int64_t c, const double* A
   return CUR_OK;
 }
 
+int cur_test_wait_timeout(cur_ctx* ctx, int which, int nblocks, double budget_ms) {
+  if (!ctx) return CUR_EINVAL;
+  if ((which != 0 && which != 1) || nblocks < 1 || nblocks > ctx->num_sms || !(budget_ms > 0.0) ||
+      budget_ms > 5000.0)
+    return fail(ctx, CUR_EINVAL, "bad arguments");
+  CK(cudaSetDevice(ctx->device));
+  TRY(ensure(ctx, B_STATUS, sizeof(DevStatus)));
+  TRY(ensure(ctx, B_STEP_PARTS, sizeof(GridBar) + 256));
+  CK(cudaMemsetAsync(ctx->buf[B_STATUS].p, 0, sizeof(DevStatus), ctx->stream));
+  int khz = 0;
+  CK(cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, ctx->device));
+  const long long budget = (long long)(budget_ms * (double)(khz > 0 ? khz : 2000000));
+  CK(launch_timeout_check(env_of(ctx), which, nblocks, budget, bp<GridBar>(ctx, B_STEP_PARTS),
+                          dstat(ctx)));
+  return read_status(ctx);
+}
+
 int cur_step_lupp(cur_ctx* ctx, const double* X, int64_t ldx, int64_t nr, int64_t ncand,
                   int64_t steps, uint8_t* mask, int64_t* piv) {
   if (!ctx) return CUR_EINVAL;

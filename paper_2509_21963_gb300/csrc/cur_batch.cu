@@ -392,6 +392,9 @@ int cur_batch_run(cur_batch* b) {
   return cur_batch_wait(b);
 }
 
+// Timed launches per candidate team size in cur_batch_tune (the fastest counts).
+constexpr int kTuneReps = 2;
+
 int cur_batch_tune(cur_batch* b, const int* candidates, int ncand, int* best_team,
                    double* best_ms) {
   if (!b) return CUR_EINVAL;
@@ -412,16 +415,25 @@ int cur_batch_tune(cur_batch* b, const int* candidates, int ncand, int* best_tea
     if (t < 1 || t > 32 || t > max_ctas) continue;
     s = plan_schedule(b, t);
     if (s != CUR_OK) break;
-    if (cudaEventRecord(e0, ctx->stream) != cudaSuccess) { s = CUR_ECUDA; break; }
-    s = cur_batch_launch(b);
+    // capture the candidate's graph before timing (host-side work that would
+    // otherwise leave the GPU idle inside the timed interval), then keep the
+    // fastest of kTuneReps graph launches
+    try_capture(b);
+    float cand = -1.f;
+    for (int rep = 0; rep < kTuneReps && s == CUR_OK; ++rep) {
+      if (cudaEventRecord(e0, ctx->stream) != cudaSuccess) { s = CUR_ECUDA; break; }
+      s = cur_batch_launch(b);
+      if (s != CUR_OK) break;
+      if (cudaEventRecord(e1, ctx->stream) != cudaSuccess) { s = CUR_ECUDA; break; }
+      s = cur_batch_wait(b);
+      if (s != CUR_OK) break;
+      float ms = 0.f;
+      cudaEventSynchronize(e1);
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (cand < 0.f || ms < cand) cand = ms;
+    }
     if (s != CUR_OK) break;
-    if (cudaEventRecord(e1, ctx->stream) != cudaSuccess) { s = CUR_ECUDA; break; }
-    s = cur_batch_wait(b);
-    if (s != CUR_OK) break;
-    float ms = 0.f;
-    cudaEventSynchronize(e1);
-    cudaEventElapsedTime(&ms, e0, e1);
-    if (best < 0 || ms < best_t) { best = t; best_t = ms; }
+    if (best < 0 || cand < best_t) { best = t; best_t = cand; }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

@@ -162,6 +162,13 @@ cudaError_t launch_sketch_fx_main(const LaunchEnv& env, int64_t c, const double*
                                   int64_t m, int64_t n, void* scratch, double* Y,
                                   double* sumsq_part, int64_t* nparts, int* err);
 
+// ---- faultcheck.cu -----------------------------------------------------------
+// Drive a bounded device wait past `budget` cycles on purpose (which 0: the
+// grid barrier, `nblocks` CTAs expecting one more; 1: an mbarrier wait); the
+// wait records kDevTimeout in *st and the kernel returns.
+cudaError_t launch_timeout_check(const LaunchEnv& env, int which, int nblocks, long long budget,
+                                 GridBar* bar, DevStatus* st);
+
 // ---- gather.cu ------------------------------------------------------------
 // out[a * ldo + t] = src(r(a), c(t)) for a < rows, t < cols, where
 // r(a) = ridx ? ridx[a] : a, c(t) = cidx ? cidx[t] : t and src(i, j) =

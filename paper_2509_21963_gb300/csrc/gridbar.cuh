@@ -23,7 +23,8 @@ __device__ __forceinline__ void dev_set_err(DevStatus* st, int code) {
 // launch, or left there by completed barriers of the same n CTAs); 64 bits do
 // not wrap in practice.  A wait that outlives kBarrierBudget cycles records
 // kDevTimeout; a wait that sees an error recorded by another CTA gives up too.
-__device__ __forceinline__ bool bar_arrive_wait(GridBar* bar, unsigned n, DevStatus* st) {
+__device__ __forceinline__ bool bar_arrive_wait(GridBar* bar, unsigned n, DevStatus* st,
+                                                long long budget = kBarrierBudget) {
   __threadfence();  // this CTA's writes before its arrival
   const unsigned long long prev = atomicAdd(&bar->count, 1ULL);
   const unsigned long long target = (prev / n + 1) * n;
@@ -33,7 +34,7 @@ __device__ __forceinline__ bool bar_arrive_wait(GridBar* bar, unsigned n, DevSta
     unsigned spins = 0;
     while (*vc < target) {
       if ((++spins & 255u) == 0) {
-        if (clock64() - t0 > kBarrierBudget) { dev_set_err(st, kDevTimeout); return false; }
+        if (clock64() - t0 > budget) { dev_set_err(st, kDevTimeout); return false; }
         if (st && *((volatile int*)&st->err) != 0) return false;
       }
     }

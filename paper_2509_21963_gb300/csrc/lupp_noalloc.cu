@@ -59,10 +59,6 @@ extern "C" int cur_step_lupp_noalloc(int device, void* cuda_stream, const double
     put_err(err, err_len, "cur_step_lupp_noalloc: device index out of range");
     return CUR_EINVAL;
   }
-  if (nr > 6144) {  // the pivot column lives in 48 KB of shared memory
-    put_err(err, err_len, "cur_step_lupp_noalloc: nr > 6144 is not supported");
-    return CUR_EINVAL;
-  }
   cudaError_t e = cudaSetDevice(device);
   if (e != cudaSuccess) {
     put_err(err, err_len, cudaGetErrorString(e));
@@ -120,13 +116,20 @@ extern "C" int cur_step_lupp_noalloc(int device, void* cuda_stream, const double
     put_err(err, err_len, cudaGetErrorString(e));
     return CUR_ECUDA;
   }
+  // the same mapping of the device status as the workspace entry point
   if (host_st.err == kDevTimeout) {
     put_err(err, err_len, "cur_step_lupp_noalloc: grid barrier exceeded its cycle budget");
     return CUR_ETIMEOUT;
   }
-  if (host_st.err != 0) {
+  if (host_st.err == kDevNoCandidate) {
     put_err(err, err_len, "cur_step_lupp_noalloc: fewer eligible candidates than steps");
     return CUR_EINVAL;
+  }
+  if (host_st.err != 0) {
+    char msg[96];
+    snprintf(msg, sizeof(msg), "cur_step_lupp_noalloc: device status %d", host_st.err);
+    put_err(err, err_len, msg);
+    return CUR_ECUDA;
   }
   put_err(err, err_len, "");
   return CUR_OK;

@@ -449,3 +449,27 @@ def test_full_size_parity_fp64(ctx, tol, noise):
     ref = oracle.run(Ah, tol, 50, 55, seed=0, mode=1)
     _check_parity(Ah, got, ref, 50)
     assert got.status == 0 and got.rho <= tol
+
+
+@pytest.mark.parametrize("mode", [0, 2])
+def test_full_size_parity_fp32(ctx, mode):
+    """The FP32 20000^2 forms bench.py reports (A = U diag(i^-2) V^T +
+    N(0, 1e-16) stored as FP32, tol 1e-2, b = 50, c = 55): the FP64 sketch of
+    the FP32 data (mode 0) against the oracle on the same values, and the
+    two-digit tensor-core sketch (mode 2) against the oracle started from its
+    exact sketch G_q fix_2(A) (products and sums exact in FP64 here).  Same I
+    and J; rho as in the FP64 gates (mode 2: within 1e-6 relative)."""
+    m = n = 20000
+    A = inputs.decay_matrix_torch(m, n, "poly2", seed=11, noise=1e-8, dtype=torch.float32)
+    got = ctx.run(A, 1e-2, 50, 55, 0, sketch_mode=mode)
+    Ah = A.cpu().numpy().astype(np.float64)
+    del A
+    torch.cuda.empty_cache()
+    if mode == 0:
+        ref = oracle.run(Ah, 1e-2, 50, 55, seed=0, mode=1)
+        _check_parity(Ah, got, ref, 50)
+    else:
+        Y = oracle.sketch(oracle.gaussian_sketch_q8(0, 55, m), oracle.fixed_point(Ah, 2))
+        ref = oracle.run_y(Ah, 1e-2, 50, 55, Y)
+        _check_parity(Ah, got, ref, 50, rho_rtol=1e-6)
+    assert got.status == 0 and got.rho <= 1e-2

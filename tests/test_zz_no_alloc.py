@@ -58,3 +58,31 @@ def test_noalloc_rejects_oversize(ctx):
     mask = torch.zeros(40000, dtype=torch.uint8, device="cuda")
     st, piv, msg = _noalloc(X, 4, mask)
     assert st == cur.CUR_EINVAL and "maximum" in msg
+
+
+def test_noalloc_largest_problem_that_fits(ctx):
+    """The largest candidate count that fits the fixed scratch at nr = 55 (found
+    by bisection on the size check, which rejects before launching): it runs
+    and equals cur_step_lupp; one more candidate is rejected."""
+    import paper_2509_21963_gb300 as cur
+    nr, steps = 55, 50
+    lo, hi = 20000, 60000                     # fits / does not fit
+    mask = torch.zeros(hi + 1, dtype=torch.uint8, device="cuda")
+    Xbig = torch.zeros((nr, hi + 1), dtype=torch.float64, device="cuda")
+    while hi - lo > 1:
+        mid = (lo + hi) // 2
+        st, _, msg = _noalloc(Xbig[:, :mid], 0, mask[:mid])
+        if st == cur.CUR_OK:
+            lo = mid
+        else:
+            assert st == cur.CUR_EINVAL and "maximum" in msg, msg
+            hi = mid
+    X = torch.from_numpy(np.random.default_rng(22).standard_normal((nr, lo))).cuda()
+    ref_piv, ref_mask = ctx.lupp(X, steps, torch.zeros(lo, dtype=torch.uint8, device="cuda"))
+    m2 = torch.zeros(lo, dtype=torch.uint8, device="cuda")
+    st, piv, msg = _noalloc(X, steps, m2)
+    assert st == cur.CUR_OK, msg
+    assert torch.equal(piv, ref_piv) and torch.equal(m2, ref_mask)
+    X1 = torch.zeros((nr, lo + 1), dtype=torch.float64, device="cuda")
+    st, _, msg = _noalloc(X1, steps, torch.zeros(lo + 1, dtype=torch.uint8, device="cuda"))
+    assert st == cur.CUR_EINVAL and "maximum" in msg
