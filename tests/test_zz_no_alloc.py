@@ -62,8 +62,9 @@ def test_noalloc_rejects_oversize(ctx):
 
 def test_noalloc_largest_problem_that_fits(ctx):
     """The largest candidate count that fits the fixed scratch at nr = 55 (found
-    by bisection on the size check, which rejects before launching): it runs
-    and equals cur_step_lupp; one more candidate is rejected."""
+    by bisection on the size check, which rejects oversize problems before
+    launching; the probes that fit run one step on zeros): it runs and equals
+    cur_step_lupp; one more candidate is rejected."""
     import paper_2509_21963_gb300 as cur
     nr, steps = 55, 50
     lo, hi = 20000, 60000                     # fits / does not fit
@@ -71,7 +72,7 @@ def test_noalloc_largest_problem_that_fits(ctx):
     Xbig = torch.zeros((nr, hi + 1), dtype=torch.float64, device="cuda")
     while hi - lo > 1:
         mid = (lo + hi) // 2
-        st, _, msg = _noalloc(Xbig[:, :mid], 0, mask[:mid])
+        st, _, msg = _noalloc(Xbig[:, :mid], 1, mask[:mid].zero_())
         if st == cur.CUR_OK:
             lo = mid
         else:
