@@ -177,10 +177,10 @@ __device__ bool cta_lupp(double* W, int64_t ldw, int nf, int64_t ncand, int step
     if (bv > 0.0 && t + 1 < nf) {
       for (int u = t + 1 + threadIdx.x; u < nf; u += blockDim.x) prow[u] = W[u * ldw + bi];
       __syncthreads();
-      const double rpt = 1.0 / W[t * ldw + bi];
+      const double pivv = W[t * ldw + bi];
       for (int64_t i = threadIdx.x; i < ncand; i += blockDim.x) {
         if (mask[i]) continue;
-        const double l = W[t * ldw + i] * rpt;
+        const double l = W[t * ldw + i] / pivv;   // divided, as the oracle does
         for (int u = t + 1; u < nf; ++u) W[u * ldw + i] = W[u * ldw + i] - l * prow[u];
       }
     }

@@ -43,6 +43,31 @@ __device__ __forceinline__ bool bar_arrive_wait(GridBar* bar, unsigned n, DevSta
   return true;
 }
 
+// The two halves of bar_arrive_wait, for work that overlaps the wait: arrive
+// (one thread per CTA, after a __syncthreads that orders the CTA's writes)
+// returns the count at which this barrier completes; wait spins for it with
+// the same budget and error rules.
+__device__ __forceinline__ unsigned long long bar_arrive(GridBar* bar, unsigned n) {
+  __threadfence();
+  const unsigned long long prev = atomicAdd(&bar->count, 1ULL);
+  return (prev / n + 1) * n;
+}
+
+__device__ __forceinline__ bool bar_wait(GridBar* bar, unsigned long long target, DevStatus* st,
+                                         long long budget = kBarrierBudget) {
+  volatile unsigned long long* vc = &bar->count;
+  const long long t0 = clock64();
+  unsigned spins = 0;
+  while (*vc < target) {
+    if ((++spins & 255u) == 0) {
+      if (clock64() - t0 > budget) { dev_set_err(st, kDevTimeout); return false; }
+      if (st && *((volatile int*)&st->err) != 0) return false;
+    }
+  }
+  __threadfence();
+  return true;
+}
+
 // The best (largest value, then smallest index) of G per-CTA records written
 // before a barrier: slot g holds its value at slot[g * stride] and its index
 // (bit pattern of a long long) at slot[g * stride + 1].  Called by a whole

@@ -21,22 +21,74 @@ namespace {
 
 constexpr int kThreads = 256;
 
+// Candidate magnitudes compare as integers: the bit pattern of |x| orders like
+// |x| for every non-NaN double (GB300 runs FP64 instructions, compares
+// included, at ~2 per clock per SM; integer compares run on the ALU).  A NaN
+// gets -2, below "no candidate" (-1), so it never wins, as under FP64 compares.
+__device__ __forceinline__ long long mag_key(double x) {
+  const long long k = __double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFLL;
+  return k > 0x7FF0000000000000LL ? -2 : k;
+}
+
 struct Best {
-  double a;
+  long long a;  // mag_key of the value; -1 = none
   long long i;  // LLONG_MAX = none
 };
 
-__device__ __forceinline__ bool better(double a, long long i, const Best& b) {
+__device__ __forceinline__ bool better(long long a, long long i, const Best& b) {
   return a > b.a || (a == b.a && i < b.i);
 }
 
 __device__ __forceinline__ Best warp_best(Best b) {
   for (int o = 16; o > 0; o >>= 1) {
-    double oa = __shfl_down_sync(0xffffffffu, b.a, o);
+    long long oa = __shfl_down_sync(0xffffffffu, b.a, o);
     long long oi = __shfl_down_sync(0xffffffffu, b.i, o);
     if (better(oa, oi, b)) { b.a = oa; b.i = oi; }
   }
   return b;
+}
+
+// The winner among G per-CTA records {key, index, ...} (slot g at slot[g *
+// stride]), read by one warp with every lane's loads in flight together; each
+// lane returns the winner and its record number (-1 when no record has a
+// candidate).
+struct KeyWin {
+  long long a, i;
+  int g;
+};
+__device__ __forceinline__ KeyWin warp_slot_best_key(const double* slot, size_t stride, int G,
+                                                     int lane) {
+  constexpr int kR = 8;
+  long long av[kR], iv[kR];
+#pragma unroll
+  for (int k = 0; k < kR; ++k) {
+    const int g = lane + 32 * k;
+    av[k] = -1;
+    iv[k] = LLONG_MAX;
+    if (g < G) {
+      const double* s = slot + (size_t)g * stride;
+      av[k] = __double_as_longlong(__ldcg(s));
+      iv[k] = __double_as_longlong(__ldcg(s + 1));
+    }
+  }
+  KeyWin c{-1, LLONG_MAX, -1};
+#pragma unroll
+  for (int k = 0; k < kR; ++k) {
+    const int g = lane + 32 * k;
+    if (g < G && (av[k] > c.a || (av[k] == c.a && iv[k] < c.i))) { c.a = av[k]; c.i = iv[k]; c.g = g; }
+  }
+  for (int g = lane + 32 * kR; g < G; g += 32) {  // grids above 256 CTAs
+    const double* s = slot + (size_t)g * stride;
+    const long long a = __double_as_longlong(__ldcg(s)), i = __double_as_longlong(__ldcg(s + 1));
+    if (a > c.a || (a == c.a && i < c.i)) { c.a = a; c.i = i; c.g = g; }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const long long oa = __shfl_xor_sync(0xffffffffu, c.a, o);
+    const long long oi = __shfl_xor_sync(0xffffffffu, c.i, o);
+    const int og = __shfl_xor_sync(0xffffffffu, c.g, o);
+    if (oa > c.a || (oa == c.a && oi < c.i)) { c.a = oa; c.i = oi; c.g = og; }
+  }
+  return c;
 }
 
 struct LuppParams {
@@ -65,17 +117,17 @@ __global__ void __launch_bounds__(kThreads) lupp_kernel(LuppParams p) {
   for (int t = 0; t < p.steps; ++t) {
     double* slot = p.slots + ((size_t)(t & 1) * G) * stride;
     // 1. local argmax over eligible owned candidates
-    Best b{-1.0, LLONG_MAX};
+    Best b{-1, LLONG_MAX};
     for (int64_t i = lo + tid; i < hi; i += kThreads) {
       if (p.mask[i]) continue;
-      double a = fabs(p.W[(int64_t)t * ldw + i]);
+      const long long a = mag_key(p.W[(int64_t)t * ldw + i]);
       if (better(a, i, b)) { b.a = a; b.i = i; }
     }
     b = warp_best(b);
     if (lane == 0) red[wid] = b;
     __syncthreads();
     if (wid == 0) {
-      Best c = lane < kThreads / 32 ? red[lane] : Best{-1.0, LLONG_MAX};
+      Best c = lane < kThreads / 32 ? red[lane] : Best{-1, LLONG_MAX};
       c = warp_best(c);
       if (lane == 0) s_win = c;
     }
@@ -83,14 +135,14 @@ __global__ void __launch_bounds__(kThreads) lupp_kernel(LuppParams p) {
     Best mine = s_win;
     // 2. publish (|value|, index, current column) of the local winner
     double* my = slot + (size_t)cta * stride;
-    if (tid == 0) { my[0] = mine.a; my[1] = __longlong_as_double(mine.i); }
+    if (tid == 0) { my[0] = __longlong_as_double(mine.a); my[1] = __longlong_as_double(mine.i); }
     if (mine.i != LLONG_MAX)
       for (int rr = t + tid; rr < p.nr; rr += kThreads) my[2 + rr] = p.W[rr * ldw + mine.i];
     __threadfence();
     if (!grid_barrier(p.bar, p.st)) return;
     // 3. global winner (every CTA computes the same answer)
     if (wid == 0) {
-      const SlotWin c = warp_slot_best(slot, (size_t)stride, G, lane);
+      const KeyWin c = warp_slot_best_key(slot, (size_t)stride, G, lane);
       if (lane == 0) { s_win = Best{c.a, c.i}; s_wcta = c.g; }
     }
     __syncthreads();
@@ -105,7 +157,7 @@ __global__ void __launch_bounds__(kThreads) lupp_kernel(LuppParams p) {
     if (tid == 0 && w.i >= lo && w.i < hi) p.mask[w.i] = 1;
     __syncthreads();
     // 4. eliminate the owned eligible candidates against the pivot
-    if (w.a > 0.0) {
+    if (w.a > 0) {
       const double pt = pv[t];
       for (int64_t i = lo + tid; i < hi; i += kThreads) {
         if (p.mask[i]) continue;
@@ -166,24 +218,24 @@ __global__ void __launch_bounds__(kThreads) lupp_blocked_kernel(LuppParams p, in
     for (int s = 0; s < ns; ++s) {
       const int t = t0 + s;
       double* slot = p.slots + ((size_t)(t & 1) * G) * stride;
-      Best b{-1.0, LLONG_MAX};
+      Best b{-1, LLONG_MAX};
       for (int li = tid; li < own; li += kThreads) {
         if (p.mask[lo + li]) continue;
-        const double a = fabs(Pn[s * per + li]);
+        const long long a = mag_key(Pn[s * per + li]);
         if (better(a, lo + li, b)) { b.a = a; b.i = lo + li; }
       }
       b = warp_best(b);
       if (lane == 0) red[wid] = b;
       __syncthreads();
       if (wid == 0) {
-        Best c = lane < kThreads / 32 ? red[lane] : Best{-1.0, LLONG_MAX};
+        Best c = lane < kThreads / 32 ? red[lane] : Best{-1, LLONG_MAX};
         c = warp_best(c);
         if (lane == 0) s_win = c;
       }
       __syncthreads();
       const Best mine = s_win;
       double* my = slot + (size_t)cta * stride;
-      if (tid == 0) { my[0] = mine.a; my[1] = __longlong_as_double(mine.i); }
+      if (tid == 0) { my[0] = __longlong_as_double(mine.a); my[1] = __longlong_as_double(mine.i); }
       if (mine.i != LLONG_MAX) {
         const int lw = (int)(mine.i - lo);
         for (int u = s + tid; u < nb; u += kThreads) my[2 + u] = Pn[u * per + lw];
@@ -192,7 +244,7 @@ __global__ void __launch_bounds__(kThreads) lupp_blocked_kernel(LuppParams p, in
       __threadfence();
       if (!grid_barrier(p.bar, p.st)) return;
       if (wid == 0) {
-        const SlotWin c = warp_slot_best(slot, (size_t)stride, G, lane);
+        const KeyWin c = warp_slot_best_key(slot, (size_t)stride, G, lane);
         if (lane == 0) { s_win = Best{c.a, c.i}; s_wcta = c.g; }
       }
       __syncthreads();
@@ -210,11 +262,11 @@ __global__ void __launch_bounds__(kThreads) lupp_blocked_kernel(LuppParams p, in
         if (w.i >= lo && w.i < hi) p.mask[w.i] = 1;
       }
       __syncthreads();
-      if (w.a > 0.0) {
-        const double rp = 1.0 / pv[s];
+      if (w.a > 0) {
+        const double pivv = pv[s];
         for (int li = tid; li < own; li += kThreads) {
           if (p.mask[lo + li]) continue;
-          const double l = Pn[s * per + li] * rp;
+          const double l = Pn[s * per + li] / pivv;   // divided, as the oracle does
           Lm[s * per + li] = l;
           for (int u = s + 1; u < nb; ++u) Pn[u * per + li] = fma(-l, pv[u], Pn[u * per + li]);
         }
@@ -260,16 +312,23 @@ __global__ void __launch_bounds__(kThreads) lupp_blocked_kernel(LuppParams p, in
 
 // Same selection with each CTA's candidate slice resident in shared memory:
 // Wsh[rr * per + li] for candidate lo + li.  Used whenever the slice fits.
-// The elimination of a step is spread over (row, candidate) pairs so that all
-// threads work even when a CTA owns fewer candidates than threads.
+// The elimination of pivot t is split so that its FP64 work overlaps the
+// exchange of step t+1: row t+1 (the next argmax) and the column of the CTA's
+// next local best are updated at once and the record of step t+1 is
+// published; then warp 0 waits for the grid barrier, reads every CTA's record
+// and fetches the winner's column (into the second pivot buffer) while warps
+// 1.. apply pivot t to the other rows.  At ~2 DFMA per clock per SM the FP64
+// elimination takes as long as the exchange.  The multipliers divide,
+// l_i = W(t, i) / pivot, as the oracle does.
 __global__ void __launch_bounds__(kThreads) lupp_smem_kernel(LuppParams p, int per) {
   extern __shared__ double sh[];
   double* Wsh = sh;                                   // nr * per
-  double* pv = Wsh + (size_t)p.nr * per;              // nr
-  double* lm = pv + p.nr;                             // per multipliers (0: skip)
+  double* pvb = Wsh + (size_t)p.nr * per;             // 2 * nr: pivot columns, by step parity
+  double* lm = pvb + 2 * p.nr;                        // per multipliers (0: skip)
   __shared__ Best red[kThreads / 32];
   __shared__ Best s_win;
-  __shared__ int s_wcta;
+  __shared__ int s_ok;
+  __shared__ unsigned long long s_target;
   const int G = gridDim.x, cta = blockIdx.x, tid = threadIdx.x;
   const int lane = tid & 31, wid = tid >> 5;
   const int64_t lo = (int64_t)cta * per;
@@ -280,59 +339,82 @@ __global__ void __launch_bounds__(kThreads) lupp_smem_kernel(LuppParams p, int p
     int rr = e / own, li = e - rr * own;
     Wsh[rr * per + li] = p.X[rr * p.ldx + lo + li];
   }
+  for (int li = tid; li < per; li += kThreads) lm[li] = 0.0;
   __syncthreads();
 
+  bool pending = false;   // pivot t-1 still to be applied to rows > t
   for (int t = 0; t < p.steps; ++t) {
     double* slot = p.slots + ((size_t)(t & 1) * G) * stride;
-    Best b{-1.0, LLONG_MAX};
+    const double* pv = pvb + (size_t)((t + 1) & 1) * p.nr;   // pivot t-1
+    double* pvn = pvb + (size_t)(t & 1) * p.nr;              // pivot t (filled below)
+    // row t with pivot t-1 (rows > t follow during the exchange)
+    if (pending)
+      for (int li = tid; li < own; li += kThreads) Wsh[t * per + li] = fma(-lm[li], pv[t], Wsh[t * per + li]);
+    __syncthreads();
+    Best b{-1, LLONG_MAX};
     for (int li = tid; li < own; li += kThreads) {
       if (p.mask[lo + li]) continue;
-      double a = fabs(Wsh[t * per + li]);
+      const long long a = mag_key(Wsh[t * per + li]);
       if (better(a, lo + li, b)) { b.a = a; b.i = lo + li; }
     }
     b = warp_best(b);
     if (lane == 0) red[wid] = b;
     __syncthreads();
     if (wid == 0) {
-      Best c = lane < kThreads / 32 ? red[lane] : Best{-1.0, LLONG_MAX};
+      Best c = lane < kThreads / 32 ? red[lane] : Best{-1, LLONG_MAX};
       c = warp_best(c);
       if (lane == 0) s_win = c;
     }
     __syncthreads();
-    Best mine = s_win;
+    const Best mine = s_win;
     double* my = slot + (size_t)cta * stride;
-    if (tid == 0) { my[0] = mine.a; my[1] = __longlong_as_double(mine.i); }
-    if (mine.i != LLONG_MAX)
-      for (int rr = t + tid; rr < p.nr; rr += kThreads) my[2 + rr] = Wsh[rr * per + (mine.i - lo)];
-    __threadfence();
-    if (!grid_barrier(p.bar, p.st)) return;
+    if (tid == 0) { my[0] = __longlong_as_double(mine.a); my[1] = __longlong_as_double(mine.i); }
+    if (mine.i != LLONG_MAX) {   // the candidate's column, rows > t with pivot t-1 applied
+      const int lw = (int)(mine.i - lo);
+      for (int rr = t + tid; rr < p.nr; rr += kThreads)
+        my[2 + rr] = (rr == t || !pending) ? Wsh[rr * per + lw]
+                                           : fma(-lm[lw], pv[rr], Wsh[rr * per + lw]);
+    }
+    __syncthreads();
     if (wid == 0) {
-      const SlotWin c = warp_slot_best(slot, (size_t)stride, G, lane);
-      if (lane == 0) { s_win = Best{c.a, c.i}; s_wcta = c.g; }
-    }
-    __syncthreads();
-    Best w = s_win;
-    if (w.i == LLONG_MAX) {
-      if (tid == 0) dev_set_err(p.st, kDevNoCandidate);
-      return;
-    }
-    const double* wcol = slot + (size_t)s_wcta * stride + 2;
-    for (int rr = t + tid; rr < p.nr; rr += kThreads) pv[rr] = __ldcg(wcol + rr);
-    if (cta == 0 && tid == 0) p.piv[t] = w.i;
-    if (tid == 0 && w.i >= lo && w.i < lo + own) p.mask[w.i] = 1;
-    __syncthreads();
-    if (w.a > 0.0 && t + 1 < p.nr) {
-      const double rp = 1.0 / pv[t];     // multipliers l_i = W[t, i] / pivot
-      for (int li = tid; li < own; li += kThreads)
-        lm[li] = p.mask[lo + li] ? 0.0 : Wsh[t * per + li] * rp;
-      __syncthreads();
-      for (int rr = t + 1 + wid; rr < p.nr; rr += kThreads / 32) {   // warp per row
+      // the exchange: arrive, wait, every record, the winner's column
+      if (lane == 0) {
+        s_target = bar_arrive(p.bar, (unsigned)G);
+        s_ok = bar_wait(p.bar, s_target, p.st) ? 1 : 0;
+      }
+      __syncwarp();
+      if (s_ok) {
+        const KeyWin c = warp_slot_best_key(slot, (size_t)stride, G, lane);
+        if (lane == 0) s_win = Best{c.a, c.i};
+        if (c.i != LLONG_MAX) {
+          const double* wcol = slot + (size_t)c.g * stride + 2;
+          for (int rr = t + lane; rr < p.nr; rr += 32) pvn[rr] = __ldcg(wcol + rr);
+        }
+      }
+    } else if (pending && t + 1 < p.nr) {   // rows > t with pivot t-1, meanwhile
+      for (int rr = t + wid; rr < p.nr; rr += kThreads / 32 - 1) {   // warp per row
+        if (rr == t) continue;
         const double pr = pv[rr];
         double* wr = Wsh + rr * per;
         for (int li = lane; li < own; li += 32) wr[li] = fma(-lm[li], pr, wr[li]);
       }
     }
     __syncthreads();
+    if (!s_ok) return;
+    const Best w = s_win;
+    if (w.i == LLONG_MAX) {
+      if (tid == 0) dev_set_err(p.st, kDevNoCandidate);
+      return;
+    }
+    if (cta == 0 && tid == 0) p.piv[t] = w.i;
+    if (tid == 0 && w.i >= lo && w.i < lo + own) p.mask[w.i] = 1;
+    __syncthreads();
+    pending = w.a > 0 && t + 1 < p.nr;   // a zero pivot eliminates nothing
+    if (pending) {
+      const double piv = pvn[t];
+      for (int li = tid; li < own; li += kThreads)
+        lm[li] = p.mask[lo + li] ? 0.0 : Wsh[t * per + li] / piv;
+    }
   }
 }
 
@@ -363,7 +445,7 @@ cudaError_t launch_lupp(const LaunchEnv& env, const double* X, int64_t ldx, int6
   p.X = X; p.ldx = ldx; p.nr = (int)nr; p.ncand = ncand; p.steps = (int)steps;
   p.mask = mask; p.piv = piv; p.W = w.W; p.slots = w.slot_val; p.bar = w.bar; p.st = st;
   const int64_t per = (ncand + grid - 1) / grid;
-  const size_t smem_res = sizeof(double) * ((size_t)nr * per + nr + per);
+  const size_t smem_res = sizeof(double) * ((size_t)nr * per + 2 * nr + per);
   if (smem_res <= kLuppSmemMax) {
     if (smem_res > 0) {  // static shared memory adds to it: always opt in
       e = smem_opt_in((const void*)lupp_smem_kernel, smem_res);

@@ -371,6 +371,7 @@ __global__ void __launch_bounds__(kThreads) qrcp_solve_kernel(SolveParams S) {
 // R(i, i') = R[i, perm[i']] for i < i'.  The same launch forms
 // X = P [R_11^{-1} Q_1^T; 0] with one thread group per column of the identity.
 constexpr int kSmallThreads = 512;
+constexpr int kSmallSplitP = 24;                   // from here on the solve runs on many SMs
 constexpr int kSeg = 8;                            // threads per column
 constexpr int kGroups = kSmallThreads / kSeg;      // columns in flight
 
@@ -381,6 +382,12 @@ __device__ __forceinline__ double seg_sum(double v) {
   return v;
 }
 
+// kSolveHere = false: the CTA only factors, and writes R (column-major, pivot
+// columns frozen), the reflectors, tau, R's diagonal, the permutation and the
+// rank in the layout of qrcp_factor_smem_kernel, for qrcp_solve_kernel to form
+// X with one warp per right-hand side over many SMs (the solve is 3 p^3 of the
+// 4/3 p^3 + 3 p^3 flops, and one SM's FP64 rate is a 64th of the GPU's).
+template <bool kSolveHere>
 __global__ void __launch_bounds__(kSmallThreads) qrcp_small_kernel(QrcpParams P, double* X,
                                                                    int64_t ldx) {
   extern __shared__ double sm[];
@@ -488,6 +495,21 @@ __global__ void __launch_bounds__(kSmallThreads) qrcp_small_kernel(QrcpParams P,
   }
   __syncthreads();
   const int k = s_k;
+  if constexpr (!kSolveHere) {
+    for (int e = tid; e < p * q; e += kSmallThreads) {
+      const int i = e % p, col = e / p;
+      P.w.Rc[(int64_t)col * p + i] = R[i * q + col];
+    }
+    for (int e = tid; e < kmax * p; e += kSmallThreads) {
+      const int j = e / p, i = e - j * p;
+      if (i >= j) P.w.V[(int64_t)j * p + i] = i == j ? vhead[j] : R[i * q + perm[j]];
+    }
+    for (int j = tid; j < kmax; j += kSmallThreads) {
+      P.w.tau[j] = tau[j];
+      P.w.rdiag[j] = rdiag[j];
+    }
+    for (int col = tid; col < q; col += kSmallThreads) P.w.perm[col] = perm[col];
+  } else {
   for (int i = tid; i < k; i += kSmallThreads) rinv[i] = 1.0 / rdiag[i];
   for (int e = tid; e < p * p; e += kSmallThreads) Y[e] = (e / p == e % p) ? 1.0 : 0.0;
   __syncthreads();
@@ -524,6 +546,7 @@ __global__ void __launch_bounds__(kSmallThreads) qrcp_small_kernel(QrcpParams P,
     __syncwarp();
     if (act)
       for (int i = sg; i < q; i += kSeg) X[(int64_t)perm[i] * ldx + l] = (i < k) ? Y[i * p + l] : 0.0;
+  }
   }
 }
 
@@ -592,15 +615,17 @@ cudaError_t launch_qrcp_pinv(const LaunchEnv& env, const double* M, int64_t p, i
   P.M = M; P.p = p; P.q = q; P.ldm = ldm; P.thr_mode = thr_mode; P.thr = thr;
   P.scale_dev = scale_dev; P.w = w; P.st = st;
   if (size_t ssm = qrcp_small_smem(p, q)) {
-    if (ssm > 0) {  // static shared memory adds to it: always opt in
-      e = smem_opt_in((const void*)qrcp_small_kernel, ssm);
+    if (p < kSmallSplitP) {  // tiny: factor and solve in one CTA
+      e = smem_opt_in((const void*)qrcp_small_kernel<true>, ssm);
       if (e != cudaSuccess) return e;
+      qrcp_small_kernel<true><<<1, kSmallThreads, ssm, env.stream>>>(P, X, ldx);
+      return cudaGetLastError();
     }
-    qrcp_small_kernel<<<1, kSmallThreads, ssm, env.stream>>>(P, X, ldx);
-    return cudaGetLastError();
-  }
-  const size_t csm = qrcp_coop_smem(p, q, grid);
-  if (csm <= 200 * 1024) {
+    e = smem_opt_in((const void*)qrcp_small_kernel<false>, ssm);
+    if (e != cudaSuccess) return e;
+    qrcp_small_kernel<false><<<1, kSmallThreads, ssm, env.stream>>>(P, X, ldx);
+    e = cudaGetLastError();
+  } else if (const size_t csm = qrcp_coop_smem(p, q, grid); csm <= 200 * 1024) {
     if (csm > 0) {  // static shared memory adds to it: always opt in
       e = smem_opt_in((const void*)qrcp_factor_smem_kernel, csm);
       if (e != cudaSuccess) return e;
