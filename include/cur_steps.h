@@ -79,9 +79,12 @@ int cur_step_lupp(cur_ctx *ctx, const double *X, int64_t ldx, int64_t nr,
  * U = A(I,J)^+ of Algorithm 1 (the paper's default QR).  thr < 0 selects
  * thr = max(p,q) 2^-52 |R_00|.  rank_host (may be NULL) receives k
  * (synchronises the stream).  The kernels are those cur_run uses for a core
- * of this size: one CTA, a cooperative grid holding M in shared memory, or
- * (square M too large for that, p <= 10240) the whole-GPU team QR with a
- * shared-memory solve panel. */
+ * of this size: one CTA (p < 24), one thread-block cluster (24 <= p <= 512,
+ * q <= 16 columns per CTA of the cluster), a cooperative grid holding M in
+ * shared memory, or (square M too large for that, p <= 10240) the whole-GPU
+ * team QR with a shared-memory solve panel.  When every remaining column norm
+ * of a step is NaN the shared-memory variants return CUR_EINVAL; the team QR
+ * carries the NaN through (its rank then counts no such column). */
 int cur_step_pinv(cur_ctx *ctx, const double *M, int64_t p, int64_t q,
                   int64_t ldm, double thr, double *X, int64_t *rank_host);
 

@@ -160,7 +160,7 @@ int read_status(cur_ctx* ctx) {
   if (ctx->st_host->err == kDevTimeout)
     return fail(ctx, CUR_ETIMEOUT, "a device-side grid barrier exceeded its cycle budget");
   if (ctx->st_host->err == kDevNoCandidate)
-    return fail(ctx, CUR_EINVAL, "LUPP ran out of eligible candidates");
+    return fail(ctx, CUR_EINVAL, "no eligible pivot: LUPP ran out of candidates, or every remaining QR column norm is NaN");
   if (ctx->st_host->err != 0) return fail(ctx, CUR_ECUDA, "device status %d", ctx->st_host->err);
   return CUR_OK;
 }

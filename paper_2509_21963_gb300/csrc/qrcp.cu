@@ -14,6 +14,10 @@
 // apply H_0..H_{k-1}, then column-oriented back substitution with R_11.
 #include <climits>
 
+#include <cooperative_groups.h>
+#include <map>
+#include <mutex>
+
 #include "gridbar.cuh"
 
 // Shared-memory bytes of the single-CTA variant (0 if it does not apply).
@@ -34,6 +38,14 @@ struct QrcpParams {
   int thr_mode; double thr; double* scale_dev;
   QrcpWork w; DevStatus* st;
 };
+
+// Squared norms compare as integers (the bit patterns of non-negative doubles
+// order like their values; FP64 compares cost FP64 pipe slots on GB300).  A NaN
+// gets -2, below every number; callers use -3 for "no column".
+__device__ __forceinline__ long long norm_key(double x) {
+  const long long k = __double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFLL;
+  return k > 0x7FF0000000000000LL ? -2 : k;
+}
 
 __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -325,6 +337,7 @@ struct SolveParams {
   const int64_t* perm; const int64_t* rank;
   double* Ywork;  // p * p: column l of Q^T then Z
   double* X; int64_t ldx;
+  const DevStatus* st;   // a factorisation that recorded an error left no rank or permutation
 };
 
 // One warp per column l of the identity.
@@ -332,6 +345,7 @@ __global__ void __launch_bounds__(kThreads) qrcp_solve_kernel(SolveParams S) {
   const int lane = threadIdx.x & 31;
   const int64_t l = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
   if (l >= S.p) return;
+  if (S.st && *((const volatile int*)&S.st->err) != 0) return;
   const int64_t p = S.p, k = *S.rank;
   double* y = S.Ywork + l * p;
   for (int64_t i = lane; i < p; i += 32) y[i] = (i == l) ? 1.0 : 0.0;
@@ -425,17 +439,25 @@ __global__ void __launch_bounds__(kSmallThreads) qrcp_small_kernel(QrcpParams P,
     }
     __syncthreads();
     if (wid == 0) {   // argmax over columns: largest norm, smallest index
-      double ba = -1.0;
+      long long ba = -3;
       int bi = INT_MAX;
-      for (int col = lane; col < q; col += 32)
-        if (nrm[col] > ba) { ba = nrm[col]; bi = col; }
+      for (int col = lane; col < q; col += 32) {
+        const long long kc = used[col] ? -3 : norm_key(nrm[col]);
+        if (kc > ba) { ba = kc; bi = col; }
+      }
       for (int o = 16; o > 0; o >>= 1) {
-        double oa = __shfl_down_sync(0xffffffffu, ba, o);
-        int oi = __shfl_down_sync(0xffffffffu, bi, o);
+        const long long oa = __shfl_down_sync(0xffffffffu, ba, o);
+        const int oi = __shfl_down_sync(0xffffffffu, bi, o);
         if (oa > ba || (oa == ba && oi < bi)) { ba = oa; bi = oi; }
       }
+      ba = __shfl_sync(0xffffffffu, ba, 0);
+      if (ba < 0) {   // every remaining norm is NaN: no pivot
+        if (lane == 0) { s_jp = -1; dev_set_err(P.st, kDevNoCandidate); }
+        goto pivot_done;
+      }
+      {
       const int ii = __shfl_sync(0xffffffffu, bi, 0);
-      const double a = __shfl_sync(0xffffffffu, ba, 0);
+      const double a = __longlong_as_double(ba);
       double vv = 0.0;          // ||x_{j+1..p-1}||^2 of the pivot column
       for (int i = j + 1 + lane; i < p; i += 32) { double x = R[i * q + ii]; vv = fma(x, x, vv); }
       vv = warp_sum(vv);
@@ -448,9 +470,12 @@ __global__ void __launch_bounds__(kSmallThreads) qrcp_small_kernel(QrcpParams P,
         s_jp = ii; s_tau = t;
         perm[j] = ii; used[ii] = 1; rdiag[j] = alpha; vhead[j] = vh; tau[j] = t;
       }
+      }
     }
+  pivot_done:
     __syncthreads();
     const int jp = s_jp;
+    if (jp < 0) return;
     const double tj = s_tau;
     if (tj != 0.0) {
       const double vh = vhead[j];
@@ -550,7 +575,259 @@ __global__ void __launch_bounds__(kSmallThreads) qrcp_small_kernel(QrcpParams P,
   }
 }
 
+// Cluster variant for mid-size problems (kSmallSplitP <= p <= 512, q <= CL
+// kClMaxLocal): one thread-block cluster of CL CTAs (16 where the GPU schedules
+// it, else 8) factors M, CTA r owning the columns col = r (mod CL) column-major
+// in its shared memory, one warp per column at a time.  A step's pivot search,
+// exchange and reflector take no global-memory round trip: each CTA stores its
+// best candidate {norm^2 as an integer key, column, R(j, col), ||R(j+1:, col)||^2}
+// into every CTA's shared memory (distributed shared memory), one cluster
+// barrier publishes them, every CTA picks the same winner, copies the pivot
+// column from its owner's shared memory and forms the reflector itself.  The
+// norms of the next step are formed in the pass that applies the reflector.
+// Output is the layout of qrcp_small_kernel<false> for qrcp_solve_kernel.
+constexpr int kClMaxLocal = 16;      // columns per CTA handled by the cluster variant
+constexpr int kClRec = 4;            // doubles per candidate record
+
+__global__ void __launch_bounds__(kClMaxLocal * 32) qrcp_cluster_kernel(QrcpParams P) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  extern __shared__ double sm[];
+  const int CL = (int)cl.num_blocks(), r = (int)cl.block_rank();
+  const int p = (int)P.p, q = (int)P.q, kmax = p < q ? p : q;
+  const int nlm = (q + CL - 1) / CL;                 // local column slots (same in every CTA)
+  const int nloc = (q - r + CL - 1) / CL;            // columns this CTA owns
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+  double* Rl = sm;                                   // nlm * p: local column c at Rl[c * p]
+  double* vcol = Rl + (size_t)nlm * p;               // p: pivot column of this step
+  double* rec = vcol + p;                            // 2 * CL * kClRec: records by step parity
+  double* rdiag = rec + 2 * CL * kClRec;             // kmax
+  double* tau = rdiag + kmax;                        // kmax
+  double* vhead = tau + kmax;                        // kmax
+  double* na = vhead + kmax;                         // nlm: ||R(j:, c)||^2 of this step
+  double* ns1 = na + nlm;                            // nlm: ||R(j+1:, c)||^2 of this step
+  int* used = reinterpret_cast<int*>(ns1 + nlm);     // nlm
+  int* perm = used + nlm;                            // q
+  int* gused = perm + q;                             // q
+  __shared__ long long s_wk[kClMaxLocal];
+  __shared__ int s_wc[kClMaxLocal];
+  __shared__ double s_wx[kClMaxLocal], s_ws[kClMaxLocal];
+
+  for (int c = wid; c < nloc; c += nw) {
+    const int col = r + CL * c;
+    double t1 = 0.0;
+    for (int i = lane; i < p; i += 32) {
+      const double x = P.M[(int64_t)i * P.ldm + col];
+      Rl[c * p + i] = x;
+      if (i >= 1) t1 = fma(x, x, t1);
+    }
+    t1 = warp_sum(t1);
+    __syncwarp();
+    if (lane == 0) { const double x0 = Rl[c * p]; ns1[c] = t1; na[c] = fma(x0, x0, t1); used[c] = 0; }
+  }
+  for (int col = tid; col < q; col += blockDim.x) gused[col] = 0;
+  __syncthreads();
+
+  bool nopivot = false;
+  for (int j = 0; j < kmax; ++j) {
+    const int par = j & 1;
+    __syncwarp();   // lane 0's norms of the last pass
+    // this warp's best unused column: largest norm, then smallest index; NaN
+    // norms (key -2) rank below numbers, "none" is -3
+    long long bk = -3;
+    int bc = INT_MAX;
+    double bx = 0.0, bs = 0.0;
+    for (int c = wid; c < nloc; c += nw) {
+      if (used[c]) continue;
+      const long long k = norm_key(na[c]);
+      const int col = r + CL * c;
+      if (k > bk || (k == bk && col < bc)) { bk = k; bc = col; bx = Rl[c * p + j]; bs = ns1[c]; }
+    }
+    if (lane == 0) { s_wk[wid] = bk; s_wc[wid] = bc; s_wx[wid] = bx; s_ws[wid] = bs; }
+    __syncthreads();
+    if (wid == 0) {   // the CTA's best, stored into every CTA's record slot r
+      long long k = lane < nw ? s_wk[lane] : -3;
+      int c = lane < nw ? s_wc[lane] : INT_MAX;
+      int src = lane;
+      for (int o = 16; o > 0; o >>= 1) {
+        const long long ok = __shfl_xor_sync(0xffffffffu, k, o);
+        const int oc = __shfl_xor_sync(0xffffffffu, c, o);
+        const int os = __shfl_xor_sync(0xffffffffu, src, o);
+        if (ok > k || (ok == k && oc < c)) { k = ok; c = oc; src = os; }
+      }
+      if (lane < CL) {
+        double* dst = cl.map_shared_rank(rec + (par * CL + r) * kClRec, lane);
+        dst[0] = __longlong_as_double(k);
+        dst[1] = __longlong_as_double((long long)c);
+        dst[2] = src < nw ? s_wx[src] : 0.0;
+        dst[3] = src < nw ? s_ws[src] : 0.0;
+      }
+    }
+    cl.sync();   // release of the records (and of last step's columns), acquire of the others'
+
+    // every warp: the winner among the CL records (integer compares only)
+    long long wk = -3;
+    int wc = INT_MAX;
+    if (lane < CL) {
+      const double* rr = rec + (par * CL + lane) * kClRec;
+      wk = __double_as_longlong(rr[0]);
+      wc = (int)__double_as_longlong(rr[1]);
+    }
+    int wl = lane;
+    for (int o = 16; o > 0; o >>= 1) {
+      const long long ok = __shfl_xor_sync(0xffffffffu, wk, o);
+      const int oc = __shfl_xor_sync(0xffffffffu, wc, o);
+      const int ol = __shfl_xor_sync(0xffffffffu, wl, o);
+      if (ok > wk || (ok == wk && oc < wc)) { wk = ok; wc = oc; wl = ol; }
+    }
+    if (wk < 0) {   // every remaining norm is NaN: no pivot (the same in every CTA)
+      if (r == 0 && tid == 0) dev_set_err(P.st, kDevNoCandidate);
+      nopivot = true;
+      break;
+    }
+    const int jp = wc;
+    const int own = jp % CL, cjp = jp / CL;
+    {   // the pivot column's rows j.. from its owner (frozen from now on)
+      const double* srcc = cl.map_shared_rank(Rl + (size_t)cjp * p, own);
+      for (int i = j + tid; i < p; i += blockDim.x) vcol[i] = srcc[i];
+    }
+    if (tid == 0) {
+      const double* rr = rec + (par * CL + wl) * kClRec;
+      const double x0 = rr[2], s1 = rr[3];
+      const double normx = sqrt(__longlong_as_double(wk));
+      double alpha = x0, vh = 0.0, t = 0.0;
+      if (normx != 0.0) {   // (a zero column keeps R(j, j) = x0 and no reflector)
+        alpha = x0 >= 0.0 ? -normx : normx;
+        vh = x0 - alpha;
+        t = 2.0 / fma(vh, vh, s1);
+      }
+      rdiag[j] = alpha; tau[j] = t; vhead[j] = vh;
+      perm[j] = jp; gused[jp] = 1;
+      if (own == r) used[cjp] = 1;
+    }
+    __syncthreads();
+
+    // apply H_j to this CTA's unused columns; form their norms for step j + 1
+    const double tj = tau[j], vh = vhead[j];
+    for (int c = wid; c < nloc; c += nw) {
+      if (used[c]) continue;
+      double* R = Rl + (size_t)c * p;
+      if (tj != 0.0) {
+        double d = lane == 0 ? vh * R[j] : 0.0;
+        for (int i = j + 1 + lane; i < p; i += 32) d = fma(vcol[i], R[i], d);
+        d = warp_sum(d) * tj;
+        if (lane == 0) R[j] = fma(-d, vh, R[j]);
+        for (int i = j + 1 + lane; i < p; i += 32) R[i] = fma(-d, vcol[i], R[i]);
+        __syncwarp();   // rows written by the neighbouring lanes
+      }
+      double t1 = 0.0;
+      for (int i = j + 2 + lane; i < p; i += 32) t1 = fma(R[i], R[i], t1);
+      t1 = warp_sum(t1);
+      __syncwarp();
+      if (lane == 0 && j + 1 < p) { const double x0 = R[j + 1]; ns1[c] = t1; na[c] = fma(x0, x0, t1); }
+    }
+  }
+
+  if (nopivot) {   // every thread of the cluster took the break at the same step
+    cl.sync();
+    return;
+  }
+  if (r == 0 && tid == 0) {
+    double thr;
+    const double r0 = kmax > 0 ? fabs(rdiag[0]) : 0.0;
+    if (P.thr_mode == 0) {
+      thr = (double)(p > q ? p : q) * 0x1.0p-52 * r0;
+    } else if (P.thr_mode == 1) {
+      thr = P.thr;
+    } else {
+      double sc = *P.scale_dev;
+      if (sc < 0.0) { sc = 0x1.0p-52 * r0; *P.scale_dev = sc; }
+      thr = P.thr * sc;
+    }
+    int k = 0;
+    while (k < kmax && fabs(rdiag[k]) > thr) ++k;
+    *P.w.rank = k;
+    int pos = kmax;   // columns never pivoted, in increasing order
+    for (int col = 0; col < q && pos < q; ++col)
+      if (!gused[col]) perm[pos++] = col;
+  }
+  __syncthreads();
+  for (int c = wid; c < nloc; c += nw) {   // R column-major by original column
+    const int col = r + CL * c;
+    for (int i = lane; i < p; i += 32) P.w.Rc[(int64_t)col * p + i] = Rl[c * p + i];
+  }
+  for (int j = wid; j < kmax; j += nw) {   // reflector tails from the pivot columns' owners
+    const int pc = perm[j];
+    if (pc % CL != r) continue;
+    const double* R = Rl + (size_t)(pc / CL) * p;
+    for (int i = j + lane; i < p; i += 32) P.w.V[(int64_t)j * p + i] = i == j ? vhead[j] : R[i];
+  }
+  if (r == 0) {
+    for (int j = tid; j < kmax; j += blockDim.x) { P.w.tau[j] = tau[j]; P.w.rdiag[j] = rdiag[j]; }
+    for (int col = tid; col < q; col += blockDim.x) P.w.perm[col] = perm[col];
+  }
+  cl.sync();   // no CTA leaves while another may still read its shared memory
+}
+
 }  // namespace
+
+// Shared-memory bytes of the cluster variant for a cluster of CL CTAs.
+static size_t qrcp_cluster_smem(int64_t p, int64_t q, int CL) {
+  const int64_t kmax = p < q ? p : q, nlm = (q + CL - 1) / CL;
+  return sizeof(double) * (size_t)(nlm * p + p + 2 * CL * kClRec + 3 * kmax + 2 * nlm) +
+         sizeof(int) * (size_t)(nlm + 2 * q);
+}
+
+static cudaLaunchConfig_t cluster_config(int CL, int threads, size_t smem, cudaStream_t stream,
+                                         cudaLaunchAttribute* attr) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(CL);
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CL;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cfg;
+}
+
+// Largest cluster (16, else 8) the device co-schedules with the variant's
+// largest shared-memory request and block, 0 if neither; probed once per device.
+static int qrcp_cluster_size(int device) {
+  static std::mutex mu;
+  static std::map<int, int> cache;
+  std::lock_guard<std::mutex> g(mu);
+  auto it = cache.find(device);
+  if (it != cache.end()) return it->second;
+  int best = 0;
+  const size_t smem = 200 * 1024;
+  if (smem_opt_in((const void*)qrcp_cluster_kernel, smem) == cudaSuccess) {
+    for (int CL : {16, 8}) {
+      if (CL > 8 && cudaFuncSetAttribute((const void*)qrcp_cluster_kernel,
+                                         cudaFuncAttributeNonPortableClusterSizeAllowed,
+                                         1) != cudaSuccess) {
+        cudaGetLastError();
+        continue;
+      }
+      cudaLaunchAttribute attr[1];
+      cudaLaunchConfig_t cfg = cluster_config(CL, kClMaxLocal * 32, smem, nullptr, attr);
+      int n = 0;
+      if (cudaOccupancyMaxActiveClusters(&n, (const void*)qrcp_cluster_kernel, &cfg) ==
+              cudaSuccess &&
+          n >= 1) {
+        best = CL;
+        break;
+      }
+      cudaGetLastError();
+    }
+  }
+  cudaGetLastError();
+  cache[device] = best;
+  return best;
+}
 
 size_t qrcp_work_bytes(int64_t p, int64_t q, int max_grid) {
   int64_t kmax = p < q ? p : q;
@@ -614,7 +891,17 @@ cudaError_t launch_qrcp_pinv(const LaunchEnv& env, const double* M, int64_t p, i
   QrcpParams P;
   P.M = M; P.p = p; P.q = q; P.ldm = ldm; P.thr_mode = thr_mode; P.thr = thr;
   P.scale_dev = scale_dev; P.w = w; P.st = st;
-  if (size_t ssm = qrcp_small_smem(p, q)) {
+  const int CL = (p >= kSmallSplitP && p <= 512) ? qrcp_cluster_size(env.device) : 0;
+  if (CL > 0 && q <= (int64_t)CL * kClMaxLocal && qrcp_cluster_smem(p, q, CL) <= 200 * 1024) {
+    const size_t csm = qrcp_cluster_smem(p, q, CL);
+    e = smem_opt_in((const void*)qrcp_cluster_kernel, csm);
+    if (e != cudaSuccess) return e;
+    int nw = (int)((q + CL - 1) / CL);
+    nw = nw < 4 ? 4 : nw;
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = cluster_config(CL, nw * 32, csm, env.stream, attr);
+    e = cudaLaunchKernelEx(&cfg, qrcp_cluster_kernel, P);
+  } else if (size_t ssm = qrcp_small_smem(p, q)) {
     if (p < kSmallSplitP) {  // tiny: factor and solve in one CTA
       e = smem_opt_in((const void*)qrcp_small_kernel<true>, ssm);
       if (e != cudaSuccess) return e;
@@ -647,7 +934,7 @@ cudaError_t launch_qrcp_pinv(const LaunchEnv& env, const double* M, int64_t p, i
   if (e != cudaSuccess) return e;
   SolveParams S;
   S.p = p; S.q = q; S.Rc = w.Rc; S.V = w.V; S.tau = w.tau; S.rdiag = w.rdiag; S.perm = w.perm;
-  S.rank = w.rank; S.Ywork = w.Ysolve; S.X = X; S.ldx = ldx;
+  S.rank = w.rank; S.Ywork = w.Ysolve; S.X = X; S.ldx = ldx; S.st = st;
   unsigned blocks = (unsigned)((p + kWarps - 1) / kWarps);
   qrcp_solve_kernel<<<blocks, kThreads, 0, env.stream>>>(S);
   return cudaGetLastError();

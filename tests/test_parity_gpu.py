@@ -136,6 +136,45 @@ def test_pinv_matches_oracle(ctx, p, seed):
     assert np.linalg.norm(M @ Xg - np.eye(p)) <= 10 * p * kappa * U_RND
 
 
+@pytest.mark.parametrize("p,q,seed", [(60, 45, 7), (45, 60, 8), (24, 24, 9), (256, 256, 10),
+                                      (300, 130, 11), (30, 200, 12), (512, 100, 13),
+                                      (23, 40, 14), (100, 257, 15)])
+def test_pinv_rect_matches_oracle(ctx, p, q, seed):
+    """Rectangular and boundary shapes of the shared-memory QR variants (one
+    CTA below 24 rows, a thread-block cluster up to 512 rows and 16 columns
+    per CTA, the cooperative grid beyond): X against the oracle's within the
+    perturbation bound, and X a one-sided inverse (X M = I for full column
+    rank, M X = I for full row rank)."""
+    rng = np.random.default_rng(seed)
+    M = rng.standard_normal((p, q))
+    Xo, ko, _, _ = oracle.qrcp_pinv(M)
+    Xg, kg = ctx.pinv(dev(M))
+    Xg = Xg.cpu().numpy()
+    k = min(p, q)
+    assert kg == ko == k
+    s = np.linalg.svd(M, compute_uv=False)
+    kappa = s[0] / s[-1]
+    bound = 10 * max(p, q) * kappa * U_RND
+    assert np.linalg.norm(Xg - Xo) / np.linalg.norm(Xo) <= bound
+    E = Xg @ M if p >= q else M @ Xg
+    assert np.linalg.norm(E - np.eye(k)) <= bound
+
+
+@pytest.mark.parametrize("p", [12, 50, 300])
+def test_pinv_nan_column_is_an_error(ctx, p):
+    """A matrix whose every column norm is NaN has no pivot: CUR_EINVAL, and
+    the context still computes the next call correctly."""
+    import paper_2509_21963_gb300 as cur
+    M = np.full((p, p), np.nan)
+    with pytest.raises(cur.CurError) as e:
+        ctx.pinv(dev(M))
+    assert e.value.status == cur.CUR_EINVAL
+    M = np.random.default_rng(p).standard_normal((p, p))
+    Xg, kg = ctx.pinv(dev(M))
+    assert kg == p
+    assert np.linalg.norm(M @ Xg.cpu().numpy() - np.eye(p)) <= 1e-9
+
+
 def test_pinv_team_matches_oracle(ctx):
     """A square core too large for the shared-memory QR kernels (p = 1900)
     runs on the whole-GPU team QR with a panel of 8 right-hand sides: against
