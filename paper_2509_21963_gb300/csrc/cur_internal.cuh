@@ -195,6 +195,12 @@ constexpr int kLuppPanel = 16;
 __host__ __device__ inline int64_t lupp_slot_stride(int64_t nr) {
   return nr + 2 > 2 + 2 * kLuppPanel ? nr + 2 : 2 + 2 * kLuppPanel;
 }
+// The selector's barrier word is followed by its exchange words: 128 bytes
+// from LuppWork::bar, all cleared by launch_lupp.
+constexpr size_t kLuppBarBytes = 128;
+__host__ __device__ inline unsigned long long* lupp_xchg(GridBar* bar) {
+  return reinterpret_cast<unsigned long long*>(bar) + 8;
+}
 int lupp_grid(const LaunchEnv& env, int64_t nr, int64_t ncand);
 cudaError_t launch_lupp(const LaunchEnv& env, const double* X, int64_t ldx, int64_t nr,
                         int64_t ncand, int64_t steps, uint8_t* mask, int64_t* piv,

@@ -68,6 +68,39 @@ __device__ __forceinline__ bool bar_wait(GridBar* bar, unsigned long long target
   return true;
 }
 
+// Release-ordered arrival (fire and forget): this thread's earlier writes, and
+// those of its CTA ordered before it by a __syncthreads, become visible to a
+// thread that later acquires the counter.
+__device__ __forceinline__ void red_release_add_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ void red_max_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("red.relaxed.gpu.global.max.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Spin (acquire loads) until *cnt >= target; the same budget and error rules
+// as bar_wait.  Loads after it see every write released before the arrivals.
+__device__ __forceinline__ bool wait_count_acquire(const unsigned long long* cnt,
+                                                   unsigned long long target, DevStatus* st,
+                                                   long long budget = kBarrierBudget) {
+  const long long t0 = clock64();
+  unsigned spins = 0;
+  while (ld_acquire_u64(cnt) < target) {
+    if ((++spins & 63u) == 0) {
+      if (clock64() - t0 > budget) { dev_set_err(st, kDevTimeout); return false; }
+      if (st && *((volatile int*)&st->err) != 0) return false;
+    }
+  }
+  return true;
+}
+
 // The best (largest value, then smallest index) of G per-CTA records written
 // before a barrier: slot g holds its value at slot[g * stride] and its index
 // (bit pattern of a long long) at slot[g * stride + 1].  Called by a whole

@@ -325,21 +325,27 @@ __global__ void __launch_bounds__(kThreads) lupp_smem_kernel(LuppParams p, int p
   double* Wsh = sh;                                   // nr * per
   double* pvb = Wsh + (size_t)p.nr * per;             // 2 * nr: pivot columns, by step parity
   double* lm = pvb + 2 * p.nr;                        // per multipliers (0: skip)
+  uint8_t* msk = reinterpret_cast<uint8_t*>(lm + per);   // per: not eligible
   __shared__ Best red[kThreads / 32];
   __shared__ Best s_win;
   __shared__ int s_ok;
-  __shared__ unsigned long long s_target;
   const int G = gridDim.x, cta = blockIdx.x, tid = threadIdx.x;
   const int lane = tid & 31, wid = tid >> 5;
   const int64_t lo = (int64_t)cta * per;
   const int own = (int)max((int64_t)0, min((int64_t)per, p.ncand - lo));
   const int stride = (int)lupp_slot_stride(p.nr);
+  unsigned long long* cnt = &p.bar->count;
+  unsigned long long* xF = lupp_xchg(p.bar);          // [4] max key, by step mod 4
+  unsigned long long* xM = xF + 4;                    // [4] max packed (key48, CTA)
 
   for (int e = tid; e < p.nr * own; e += kThreads) {
     int rr = e / own, li = e - rr * own;
     Wsh[rr * per + li] = p.X[rr * p.ldx + lo + li];
   }
-  for (int li = tid; li < per; li += kThreads) lm[li] = 0.0;
+  for (int li = tid; li < per; li += kThreads) {
+    lm[li] = 0.0;
+    msk[li] = li < own ? p.mask[lo + li] : 1;
+  }
   __syncthreads();
 
   bool pending = false;   // pivot t-1 still to be applied to rows > t
@@ -347,14 +353,16 @@ __global__ void __launch_bounds__(kThreads) lupp_smem_kernel(LuppParams p, int p
     double* slot = p.slots + ((size_t)(t & 1) * G) * stride;
     const double* pv = pvb + (size_t)((t + 1) & 1) * p.nr;   // pivot t-1
     double* pvn = pvb + (size_t)(t & 1) * p.nr;              // pivot t (filled below)
-    // row t with pivot t-1 (rows > t follow during the exchange)
-    if (pending)
-      for (int li = tid; li < own; li += kThreads) Wsh[t * per + li] = fma(-lm[li], pv[t], Wsh[t * per + li]);
-    __syncthreads();
+    // row t with pivot t-1 (rows > t follow during the exchange), and the
+    // local argmax over it; thread tid owns the slice entries li = tid (mod
+    // kThreads) in every loop over li, so msk / lm / row t need no barrier
+    const double pvt = pending ? pv[t] : 0.0;
     Best b{-1, LLONG_MAX};
     for (int li = tid; li < own; li += kThreads) {
-      if (p.mask[lo + li]) continue;
-      const long long a = mag_key(Wsh[t * per + li]);
+      double v = Wsh[t * per + li];
+      if (pending) { v = fma(-lm[li], pvt, v); Wsh[t * per + li] = v; }
+      if (msk[li]) continue;
+      const long long a = mag_key(v);
       if (better(a, lo + li, b)) { b.a = a; b.i = lo + li; }
     }
     b = warp_best(b);
@@ -377,18 +385,51 @@ __global__ void __launch_bounds__(kThreads) lupp_smem_kernel(LuppParams p, int p
     }
     __syncthreads();
     if (wid == 0) {
-      // the exchange: arrive, wait, every record, the winner's column
+      // The exchange.  Every CTA folds its candidate into two maxima (the
+      // exact 63-bit key; the key's top 48 bits with the CTA number, smaller
+      // CTA winning ties) and then arrives with release semantics; after the
+      // last arrival one CTA's record is read.  If that record's key is the
+      // exact maximum it is the winner (every CTA with the same top 48 bits
+      // and a smaller number would have won the packed maximum); otherwise
+      // (a tie in the top 48 bits only) every record is read.
+      const int x = t & 3;
       if (lane == 0) {
-        s_target = bar_arrive(p.bar, (unsigned)G);
-        s_ok = bar_wait(p.bar, s_target, p.st) ? 1 : 0;
+        if (mine.i != LLONG_MAX && mine.a >= -2) {
+          const unsigned long long hi =
+              mine.a >= 0 ? (unsigned long long)(mine.a >> 15) + 2ULL : 1ULL;   // NaN: 1
+          if (mine.a >= 0) red_max_u64(xF + x, (unsigned long long)mine.a);
+          red_max_u64(xM + x, (hi << 16) | (unsigned long long)(0xFFFF - cta));
+        }
+        red_release_add_u64(cnt, 1ULL);
       }
       __syncwarp();
-      if (s_ok) {
-        const KeyWin c = warp_slot_best_key(slot, (size_t)stride, G, lane);
-        if (lane == 0) s_win = Best{c.a, c.i};
-        if (c.i != LLONG_MAX) {
-          const double* wcol = slot + (size_t)c.g * stride + 2;
-          for (int rr = t + lane; rr < p.nr; rr += 32) pvn[rr] = __ldcg(wcol + rr);
+      const bool ok = __all_sync(0xffffffffu, wait_count_acquire(cnt, (unsigned long long)(t + 1) * G, p.st));
+      if (lane == 0) s_ok = ok ? 1 : 0;
+      if (ok) {
+        const unsigned long long F = __ldcg(xF + x), M = __ldcg(xM + x);
+        const int gs = 0xFFFF - (int)(M & 0xFFFFu);
+        bool hit = false;
+        if (M != 0ULL && gs >= 0 && gs < G) {
+          const double* rec = slot + (size_t)gs * stride;
+          const long long ka = __double_as_longlong(__ldcg(rec));
+          const long long ki = __double_as_longlong(__ldcg(rec + 1));
+          if (ka >= 0 && (unsigned long long)ka == F) {
+            hit = true;
+            if (lane == 0) s_win = Best{ka, ki};
+            for (int rr = t + lane; rr < p.nr; rr += 32) pvn[rr] = __ldcg(rec + 2 + rr);
+          }
+        }
+        if (!hit) {   // the slow path: every record
+          const KeyWin c = warp_slot_best_key(slot, (size_t)stride, G, lane);
+          if (lane == 0) s_win = Best{c.a, c.i};
+          if (c.i != LLONG_MAX) {
+            const double* wcol = slot + (size_t)c.g * stride + 2;
+            for (int rr = t + lane; rr < p.nr; rr += 32) pvn[rr] = __ldcg(wcol + rr);
+          }
+        }
+        if (cta == 0 && lane == 0) {   // step t + 2's maxima (last read before step t's barrier)
+          xF[(t + 2) & 3] = 0ULL;
+          xM[(t + 2) & 3] = 0ULL;
         }
       }
     } else if (pending && t + 1 < p.nr) {   // rows > t with pivot t-1, meanwhile
@@ -407,13 +448,11 @@ __global__ void __launch_bounds__(kThreads) lupp_smem_kernel(LuppParams p, int p
       return;
     }
     if (cta == 0 && tid == 0) p.piv[t] = w.i;
-    if (tid == 0 && w.i >= lo && w.i < lo + own) p.mask[w.i] = 1;
-    __syncthreads();
     pending = w.a > 0 && t + 1 < p.nr;   // a zero pivot eliminates nothing
-    if (pending) {
-      const double piv = pvn[t];
-      for (int li = tid; li < own; li += kThreads)
-        lm[li] = p.mask[lo + li] ? 0.0 : Wsh[t * per + li] / piv;
+    const double piv = pvn[t];
+    for (int li = tid; li < own; li += kThreads) {
+      if (lo + li == w.i) { msk[li] = 1; p.mask[w.i] = 1; }
+      if (pending) lm[li] = msk[li] ? 0.0 : Wsh[t * per + li] / piv;
     }
   }
 }
@@ -439,13 +478,13 @@ cudaError_t launch_lupp(const LaunchEnv& env, const double* X, int64_t ldx, int6
                         int64_t ncand, int64_t steps, uint8_t* mask, int64_t* piv,
                         const LuppWork& w, int grid, DevStatus* st) {
   if (steps <= 0) return cudaSuccess;
-  cudaError_t e = cudaMemsetAsync(w.bar, 0, sizeof(GridBar), env.stream);
+  cudaError_t e = cudaMemsetAsync(w.bar, 0, kLuppBarBytes, env.stream);
   if (e != cudaSuccess) return e;
   LuppParams p;
   p.X = X; p.ldx = ldx; p.nr = (int)nr; p.ncand = ncand; p.steps = (int)steps;
   p.mask = mask; p.piv = piv; p.W = w.W; p.slots = w.slot_val; p.bar = w.bar; p.st = st;
   const int64_t per = (ncand + grid - 1) / grid;
-  const size_t smem_res = sizeof(double) * ((size_t)nr * per + 2 * nr + per);
+  const size_t smem_res = sizeof(double) * ((size_t)nr * per + 2 * nr + per) + (size_t)per;
   if (smem_res <= kLuppSmemMax) {
     if (smem_res > 0) {  // static shared memory adds to it: always opt in
       e = smem_opt_in((const void*)lupp_smem_kernel, smem_res);
