@@ -62,6 +62,31 @@ int cur_step_sketch_q(cur_ctx *ctx, const double *G, int64_t c, const float *A, 
 int cur_step_sketch_fx(cur_ctx *ctx, const double *G, int64_t c, const double *A, int64_t m,
                        int64_t n, int64_t lda, double *Y, double *sumsq_host);
 
+/* D = alpha op(A) op(B) + beta C in FP64 (op = transpose when trans* != 0):
+ * the products of the residual updates of Algorithm 1 in the Lemma 1 form,
+ * S^row = A(:,J_k) - C U R(:,J_k) and S^col <- S^col - S^col(:,J_k) N^+ R_k
+ * (Sec. 3.2).  D is M x N (stride ldd); op(A) is M x K (A stored K x M when
+ * transA, stride lda); op(B) is K x N (B stored N x K when transB, stride
+ * ldb); C (stride ldc) is read only when beta != 0 and may alias D.  All
+ * pointers are device memory owned by the caller.  sumsq_host (may be NULL)
+ * receives ||D||_F^2, summed in a fixed order (synchronises the stream): the
+ * stopping test's norm.  CUR_EINVAL for negative sizes or short strides. */
+int cur_step_gemm(cur_ctx *ctx, int64_t M, int64_t N, int64_t K, double alpha, const double *A,
+                  int64_t lda, int transA, const double *B, int64_t ldb, int transB, double beta,
+                  const double *C, int64_t ldc, double *D, int64_t ldd, double *sumsq_host);
+
+/* Index gather of Algorithm 1 (C = A(:,J), R = A(I,:), A(I,J), S(:,J_k)):
+ * out[a * ldo + t] = X(r, c) with r = ridx ? ridx[a] : a and
+ * c = cidx ? cidx[t] : t, where X(r, c) = X[r * ldx + c] (trans == 0) or
+ * X[c * ldx + r] (trans != 0, the transposed gather); an index outside
+ * [0, rlim) x [0, clim) writes 0.0 (so a rank that does not own an index
+ * contributes zero to a sum over ranks).  out is rows x cols; X FP64; all
+ * pointers device memory owned by the caller; asynchronous on the context's
+ * stream.  CUR_EINVAL for negative sizes or short strides. */
+int cur_step_gather(cur_ctx *ctx, const double *X, int64_t ldx, int trans, const int64_t *ridx,
+                    const int64_t *cidx, int64_t rows, int64_t cols, int64_t rlim, int64_t clim,
+                    double *out, int64_t ldo);
+
 /* LUPP index selection (Sec. 3.2.1, 3.2.2): the candidates are the ncand
  * columns of X (nr x ncand, stride ldx, FP64; read only).  Step t picks the
  * eligible candidate with the largest |W[t, i]| of the running Schur

@@ -96,6 +96,9 @@ _SIGNATURES = {
     "cur_test_wait_timeout": (_int, [_vp, _int, _int, _dbl]),
     "cur_step_lupp": (_int, [_vp, _vp, _i64, _i64, _i64, _i64, _vp, _vp]),
     "cur_step_pinv": (_int, [_vp, _vp, _i64, _i64, _i64, _dbl, _vp, _vp]),
+    "cur_step_gemm": (_int, [_vp, _i64, _i64, _i64, _dbl, _vp, _i64, _int, _vp, _i64, _int, _dbl,
+                             _vp, _i64, _vp, _i64, _vp]),
+    "cur_step_gather": (_int, [_vp, _vp, _i64, _int, _vp, _vp, _i64, _i64, _i64, _i64, _vp, _i64]),
     "cur_step_lupp_noalloc": (_int, [_int, _vp, _vp, _i64, _i64, _i64, _i64, _vp, _vp,
                                      ctypes.c_char_p, _sz]),
     "cur_batch_create": (_int, [_vp, ctypes.POINTER(cur_batch_job), _i64, _int, ctypes.POINTER(_vp)]),
@@ -341,6 +344,40 @@ class Context:
         _check(self.ptr, lib().cur_step_lupp(self.ptr, _vp(X.data_ptr()), X.stride(0), nr, ncand, steps,
                                              _vp(mask.data_ptr()), _vp(piv.data_ptr())))
         return piv, mask
+
+    def gemm(self, alpha, A, B, beta=0.0, C=None, out=None, trans_a=False, trans_b=False,
+             sumsq=False):
+        """D = alpha op(A) op(B) + beta C (FP64 CUDA tensors, unit column
+        stride); `out` may be C.  Returns D, or (D, ||D||_F^2) with sumsq."""
+        import torch
+        M = A.shape[1] if trans_a else A.shape[0]
+        K = A.shape[0] if trans_a else A.shape[1]
+        N = B.shape[0] if trans_b else B.shape[1]
+        if out is None:
+            out = torch.empty(M, N, dtype=torch.float64, device=A.device)
+        ss = ctypes.c_double()
+        cptr = C.data_ptr() if (C is not None and beta != 0.0) else None
+        ldc = C.stride(0) if (C is not None and beta != 0.0) else 0
+        _check(self.ptr, lib().cur_step_gemm(self.ptr, M, N, K, float(alpha), _vp(A.data_ptr()),
+                                             A.stride(0), int(trans_a), _vp(B.data_ptr()),
+                                             B.stride(0), int(trans_b), float(beta), _vp(cptr),
+                                             ldc, _vp(out.data_ptr()), out.stride(0),
+                                             ctypes.byref(ss) if sumsq else None))
+        return (out, ss.value) if sumsq else out
+
+    def gather(self, X, rows, cols, ridx=None, cidx=None, trans=False, out=None):
+        """out[a, t] = X(ridx[a], cidx[t]) (X^T's entries when trans); indices
+        outside X give 0.0.  ridx / cidx: int64 CUDA tensors or None."""
+        import torch
+        if out is None:
+            out = torch.empty(rows, cols, dtype=torch.float64, device=X.device)
+        rlim, clim = (X.shape[1], X.shape[0]) if trans else (X.shape[0], X.shape[1])
+        _check(self.ptr, lib().cur_step_gather(
+            self.ptr, _vp(X.data_ptr()), X.stride(0), int(trans),
+            _vp(ridx.data_ptr() if ridx is not None else None),
+            _vp(cidx.data_ptr() if cidx is not None else None),
+            rows, cols, rlim, clim, _vp(out.data_ptr()), out.stride(0)))
+        return out
 
     def pinv(self, M, thr: float = -1.0):
         import torch

@@ -798,6 +798,48 @@ int cur_step_sketch(cur_ctx* ctx, const double* G, int64_t c, const void* A, int
   return CUR_OK;
 }
 
+int cur_step_gemm(cur_ctx* ctx, int64_t M, int64_t N, int64_t K, double alpha, const double* A,
+                  int64_t lda, int transA, const double* B, int64_t ldb, int transB, double beta,
+                  const double* C, int64_t ldc, double* D, int64_t ldd, double* sumsq_host) {
+  if (!ctx) return CUR_EINVAL;
+  if (M < 0 || N < 0 || K < 0 || !D || ldd < N || (beta != 0.0 && (!C || ldc < N)) ||
+      (K > 0 && (!A || !B || lda < (transA ? M : K) || ldb < (transB ? K : N))))
+    return fail(ctx, CUR_EINVAL, "bad arguments");
+  CK(cudaSetDevice(ctx->device));
+  TRY(ensure(ctx, B_STATUS, sizeof(DevStatus)));
+  CK(cudaMemsetAsync(ctx->buf[B_STATUS].p, 0, sizeof(DevStatus), ctx->stream));
+  if (M == 0 || N == 0) {
+    if (sumsq_host) *sumsq_host = 0.0;
+    return CUR_OK;
+  }
+  GemmArgs g = gargs(M, N, K, alpha, A, lda, transA != 0, B, ldb, transB != 0, false, beta,
+                     beta != 0.0 ? C : nullptr, beta != 0.0 ? ldc : 0, D, ldd);
+  int64_t np = 0;
+  if (sumsq_host) {
+    np = gemm_num_sumsq_parts(g);
+    TRY(ensure(ctx, B_STEP_PARTS, sizeof(double) * (size_t)(np > 0 ? np : 1)));
+    g.sumsq_part = bp<double>(ctx, B_STEP_PARTS);
+  }
+  TRY(gemm(ctx, g));
+  if (sumsq_host) {
+    TRY(sum_parts(ctx, g.sumsq_part, np, &dstat(ctx)->scalar[0]));
+    TRY(read_status(ctx));
+    *sumsq_host = ctx->st_host->scalar[0];
+  }
+  return CUR_OK;
+}
+
+int cur_step_gather(cur_ctx* ctx, const double* X, int64_t ldx, int trans, const int64_t* ridx,
+                    const int64_t* cidx, int64_t rows, int64_t cols, int64_t rlim, int64_t clim,
+                    double* out, int64_t ldo) {
+  if (!ctx) return CUR_EINVAL;
+  if (rows < 0 || cols < 0 || rlim < 0 || clim < 0 || (rows > 0 && cols > 0 && (!X || !out)) ||
+      ldo < cols || ldx < (trans ? rlim : clim))
+    return fail(ctx, CUR_EINVAL, "bad arguments");
+  CK(cudaSetDevice(ctx->device));
+  return gather(ctx, X, false, ldx, trans != 0, ridx, cidx, rows, cols, rlim, clim, out, ldo);
+}
+
 int cur_step_sketch_q(cur_ctx* ctx, const double* G, int64_t c, const float* A, int64_t m,
                       int64_t n, int64_t lda, int digits, double* Y, double* sumsq_host) {
   if (!ctx) return CUR_EINVAL;
