@@ -616,7 +616,14 @@ int run_device(cur_ctx* ctx, const void* A, int64_t m, int64_t n, int64_t lda, i
     if ((st = ensure(ctx, B_CORE, sizeof(double) * (size_t)(r * r))) != CUR_OK) { cur_result_free(res); return st; }
     double* Mc = bp<double>(ctx, B_CORE);
     tick(ctx, CUR_PHASE_CORE);
-    if ((st = core_solve(ctx, A, f32, lda, m, n, res->I, res->J, r, Mc, res->U)) != CUR_OK) {
+    if (res->iters == 1 && !team_core(env, r, r)) {
+      // One iteration: A(I,J) = A(I_1,J_1) = N_1 entry for entry (S_0 = A), the
+      // core solve would run the same pivoted-QR kernels on it, and its rank
+      // threshold max(p,q) 2^-52 |R_00| equals N_1^+'s (r 2^-52 |R_00(N_1)|), so
+      // U = N_1^+ bit for bit: reuse it.
+      CK(cudaMemcpyAsync(res->U, bp<double>(ctx, B_NP), sizeof(double) * (size_t)(r * r),
+                         cudaMemcpyDeviceToDevice, s));
+    } else if ((st = core_solve(ctx, A, f32, lda, m, n, res->I, res->J, r, Mc, res->U)) != CUR_OK) {
       cur_result_free(res);
       return st;
     }

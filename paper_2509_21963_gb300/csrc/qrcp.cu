@@ -375,6 +375,63 @@ __global__ void __launch_bounds__(kThreads) qrcp_solve_kernel(SolveParams S) {
   }
 }
 
+// Solve for p <= kSolveSmallP: the same arithmetic as qrcp_solve_kernel with
+// the reflectors and R_11 staged in shared memory (shared by the CTA's eight
+// warps, one warp per column l of the identity), the column y in registers
+// (row i = lane + 32 s in y[s]) and R_11's diagonal applied as reciprocals,
+// so a reflector costs one warp reduction and a back-substitution step a
+// multiply and an FMA (GB300 runs a dependent FP64 operation in ~64 cycles, a
+// divide in ~560).
+constexpr int kSolveSmallP = 64;
+
+__global__ void __launch_bounds__(kThreads) qrcp_solve_small_kernel(SolveParams S) {
+  extern __shared__ double ssm[];
+  if (S.st && *((const volatile int*)&S.st->err) != 0) return;
+  const int p = (int)S.p, q = (int)S.q;
+  const int k = (int)*S.rank;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  double* Vs = ssm;                      // k * p: reflector j at Vs[j * p], zero above row j
+  double* Rs = Vs + (size_t)k * p;       // k * k: R(a, i) at Rs[i * k + a], a < i
+  double* tau = Rs + (size_t)k * k;      // k
+  double* rinv = tau + k;                // k
+  int* perm = reinterpret_cast<int*>(rinv + k);   // q
+  for (int e = threadIdx.x; e < k * p; e += kThreads) {
+    const int j = e / p, i = e - j * p;
+    Vs[e] = i >= j ? S.V[(int64_t)j * p + i] : 0.0;
+  }
+  for (int e = threadIdx.x; e < k * k; e += kThreads) {
+    const int i = e / k, a = e - i * k;
+    Rs[e] = a < i ? S.Rc[S.perm[i] * p + a] : 0.0;
+  }
+  for (int j = threadIdx.x; j < k; j += kThreads) { tau[j] = S.tau[j]; rinv[j] = 1.0 / S.rdiag[j]; }
+  for (int i = threadIdx.x; i < q; i += kThreads) perm[i] = (int)S.perm[i];
+  __syncthreads();
+  const int l = blockIdx.x * kWarps + wid;
+  if (l >= p) return;
+  double y0 = lane == l ? 1.0 : 0.0, y1 = lane + 32 == l ? 1.0 : 0.0;   // rows lane, lane + 32
+  const bool r1 = lane + 32 < p;
+  for (int j = 0; j < k; ++j) {   // y = H_{k-1} ... H_0 e_l
+    const double t = tau[j];
+    if (t == 0.0) continue;
+    const double v0 = lane < p ? Vs[j * p + lane] : 0.0;
+    const double v1 = r1 ? Vs[j * p + lane + 32] : 0.0;
+    double d = fma(v1, y1, v0 * y0);
+    d = warp_sum(d) * t;
+    y0 = fma(-d, v0, y0);
+    y1 = fma(-d, v1, y1);
+  }
+  for (int i = k - 1; i >= 0; --i) {   // R_11 z = y(0:k), column oriented
+    const double yi = __shfl_sync(0xffffffffu, i < 32 ? y0 : y1, i & 31);
+    const double zi = yi * rinv[i];
+    if (lane < i) y0 = fma(-zi, Rs[i * k + lane], y0);
+    if (lane + 32 < i) y1 = fma(-zi, Rs[i * k + lane + 32], y1);
+    if (lane == i) y0 = zi;
+    if (lane + 32 == i) y1 = zi;
+  }
+  for (int i = lane; i < q; i += 32)   // row i of z sits in this lane (k <= p <= 64)
+    S.X[(int64_t)perm[i] * S.ldx + l] = i < k ? (i < 32 ? y0 : y1) : 0.0;
+}
+
 // Single-CTA variant for small p, q (every N_k and small cores).  GB300 runs
 // FP64 at ~2 DFMA/clk/SM, so a 50 x 50 problem has too little work for one
 // thread per column to hide FP64 and shared-memory latency.  Here every column
@@ -936,6 +993,15 @@ cudaError_t launch_qrcp_pinv(const LaunchEnv& env, const double* M, int64_t p, i
   S.p = p; S.q = q; S.Rc = w.Rc; S.V = w.V; S.tau = w.tau; S.rdiag = w.rdiag; S.perm = w.perm;
   S.rank = w.rank; S.Ywork = w.Ysolve; S.X = X; S.ldx = ldx; S.st = st;
   unsigned blocks = (unsigned)((p + kWarps - 1) / kWarps);
+  if (p <= kSolveSmallP) {
+    const int64_t kmax = p < q ? p : q;
+    const size_t ssm = sizeof(double) * (size_t)(kmax * p + kmax * kmax + 2 * kmax) +
+                       sizeof(int) * (size_t)q;
+    e = smem_opt_in((const void*)qrcp_solve_small_kernel, ssm);
+    if (e != cudaSuccess) return e;
+    qrcp_solve_small_kernel<<<blocks, kThreads, ssm, env.stream>>>(S);
+    return cudaGetLastError();
+  }
   qrcp_solve_kernel<<<blocks, kThreads, 0, env.stream>>>(S);
   return cudaGetLastError();
 }

@@ -175,6 +175,19 @@ def test_pinv_nan_column_is_an_error(ctx, p):
     assert np.linalg.norm(M @ Xg.cpu().numpy() - np.eye(p)) <= 1e-9
 
 
+@pytest.mark.parametrize("tol,iters", [(1e-3, 1), (1e-7, 2)])
+def test_core_equals_pinv_of_selection(ctx, tol, iters):
+    """U of a run is A(I,J)^+ as cur_step_pinv forms it, bit for bit: after one
+    iteration the run returns N_1^+ (N_1 = A(I_1,J_1), the same kernels and
+    rank threshold), after more it factors A(I,J) at exit."""
+    A = inputs.svd_matrix(600, 500, 0.5 ** np.arange(500), seed=21)
+    got = ctx.run(dev(A), tol, 20, 25, 3)
+    assert got.iterations == iters and got.status == 0
+    M = dev(A)[torch.from_numpy(got.I).cuda()][:, torch.from_numpy(got.J).cuda()].contiguous()
+    X, k = ctx.pinv(M)
+    assert np.array_equal(got.U.reshape(X.shape), X.cpu().numpy())
+
+
 def test_pinv_team_matches_oracle(ctx):
     """A square core too large for the shared-memory QR kernels (p = 1900)
     runs on the whole-GPU team QR with a panel of 8 right-hand sides: against
