@@ -70,6 +70,19 @@ void cur_batch_free(cur_batch *batch);
  * the current value).  Reallocates the team scratch; invalidates the graph. */
 int cur_batch_set_team(cur_batch *batch, int team);
 
+/* Schedule with two team classes: nbig teams of team_big CTAs take the
+ * big_cut largest jobs (by estimated work; the queue is ordered largest
+ * first), then help with the rest; the remaining co-resident CTAs form teams
+ * of `team` CTAs that take only the other jobs.  So a job's team size follows
+ * its size class.  nbig = 0 is cur_batch_set_team(batch, team).  CUR_EINVAL
+ * when the big teams leave no room for one team of `team` CTAs.  Reallocates
+ * the team scratch; invalidates the graph. */
+int cur_batch_set_classes(cur_batch *batch, int team, int team_big, int nbig, int64_t big_cut);
+
+/* The big-team class of the current schedule (team_big = nbig = big_cut = 0
+ * when there is one class). */
+int cur_batch_get_classes(const cur_batch *batch, int *team_big, int *nbig, int64_t *big_cut);
+
 /* Current schedule: team size, CTAs launched, teams, whether launches replay a
  * captured graph (1) or are direct cooperative launches (0). */
 int cur_batch_get_schedule(const cur_batch *batch, int *team, int *grid, int *teams,
@@ -78,7 +91,11 @@ int cur_batch_get_schedule(const cur_batch *batch, int *team, int *grid, int *te
 /* Autotuner: for each candidate team size (candidates: host array of ncand
  * sizes, or NULL for {1, 2, 4, 8, 16}) capture the launch graph first, then
  * run the whole batch twice, timing each run with CUDA events; the faster run
- * is the candidate's time and the fastest candidate is kept.  Every trial is
+ * is the candidate's time.  After the single-class candidates it tries, on
+ * top of the fastest of them, two-class schedules (cur_batch_set_classes):
+ * 1 or 2 big teams of 8 or 16 CTAs (larger than the small teams) serving the
+ * largest jobs up to the big teams' share of the CTAs in estimated work.
+ * The fastest schedule is kept; *best_team receives its small-team size.  Every trial is
  * a complete, valid run, so the results of the last trial are available
  * afterwards.  *best_team and *best_ms (optional) receive the choice and its
  * time. */

@@ -104,6 +104,9 @@ _SIGNATURES = {
     "cur_batch_create": (_int, [_vp, ctypes.POINTER(cur_batch_job), _i64, _int, ctypes.POINTER(_vp)]),
     "cur_batch_free": (None, [_vp]),
     "cur_batch_set_team": (_int, [_vp, _int]),
+    "cur_batch_set_classes": (_int, [_vp, _int, _int, _int, _i64]),
+    "cur_batch_get_classes": (_int, [_vp, ctypes.POINTER(_int), ctypes.POINTER(_int),
+                                     ctypes.POINTER(_i64)]),
     "cur_batch_get_schedule": (_int, [_vp, ctypes.POINTER(_int), ctypes.POINTER(_int),
                                       ctypes.POINTER(_int), ctypes.POINTER(_int)]),
     "cur_batch_tune": (_int, [_vp, ctypes.POINTER(_int), _int, ctypes.POINTER(_int),
@@ -456,6 +459,12 @@ class Batch:
     def set_team(self, team: int):
         _check(self.ctx.ptr, lib().cur_batch_set_team(self.ptr, int(team)))
 
+    def set_classes(self, team: int, team_big: int, nbig: int, big_cut: int):
+        """nbig teams of team_big CTAs take the big_cut largest jobs first; the
+        other CTAs form teams of `team` (include/cur_batch.h)."""
+        _check(self.ctx.ptr, lib().cur_batch_set_classes(self.ptr, int(team), int(team_big),
+                                                         int(nbig), int(big_cut)))
+
     def tune(self, candidates=None):
         best, ms = _int(), _dbl()
         if candidates is None:
@@ -471,7 +480,11 @@ class Batch:
         t, g, n, gr = _int(), _int(), _int(), _int()
         _check(self.ctx.ptr, lib().cur_batch_get_schedule(self.ptr, ctypes.byref(t), ctypes.byref(g),
                                                           ctypes.byref(n), ctypes.byref(gr)))
-        return {"team": t.value, "grid": g.value, "teams": n.value, "graph": bool(gr.value)}
+        tb, nb, cut = _int(), _int(), _i64()
+        _check(self.ctx.ptr, lib().cur_batch_get_classes(self.ptr, ctypes.byref(tb), ctypes.byref(nb),
+                                                         ctypes.byref(cut)))
+        return {"team": t.value, "grid": g.value, "teams": n.value, "graph": bool(gr.value),
+                "team_big": tb.value, "nbig": nb.value, "big_cut": cut.value}
 
     BATCH_PHASES = ("sketch", "lupp_col", "row_res", "lupp_row", "updates", "core_factor",
                     "core_solve", "jobs")

@@ -867,13 +867,21 @@ __device__ void run_job(const BatchParams& P, const Team& tm, const BatchJobDev&
   if (tm.rank == 0 && tid == 0) out->cycles = clock64() - t_job;
 }
 
+// Two team classes: the first nbig teams have team_big CTAs and take the
+// queue positions [0, big_cut) (the largest jobs: the queue is ordered by
+// estimated work), then help with the rest; the other teams have `team` CTAs
+// and take positions [big_cut, njobs) only.  A job's team size is thus set by
+// its class, and the largest jobs no longer hold a small team to the end.
 template <typename AT>
 __global__ void __launch_bounds__(256, 1) batch_kernel(BatchParams P) {
-  const int T = P.team;
-  const int team = blockIdx.x / T;
+  const int bigctas = P.nbig * P.team_big;
+  const bool big = (int)blockIdx.x < bigctas;
+  const int T = big ? P.team_big : P.team;
+  const int local = big ? (int)blockIdx.x : (int)blockIdx.x - bigctas;
+  const int team = big ? local / T : P.nbig + local / T;
   Team tm;
   tm.T = T;
-  tm.rank = blockIdx.x - team * T;
+  tm.rank = local % T;
   tm.st = P.st;
   tm.cluster = false;
   char* tbase = P.team_scratch + (size_t)team * P.team_bytes;
@@ -882,7 +890,11 @@ __global__ void __launch_bounds__(256, 1) batch_kernel(BatchParams P) {
   CtaWs cw = carve_cta(P.cta_scratch + (size_t)blockIdx.x * P.cta_bytes, P.dims);
   __shared__ long long s_job;
   for (;;) {
-    if (tm.rank == 0 && threadIdx.x == 0) *tw.job_slot = (long long)atomicAdd(P.next, 1ULL);
+    if (tm.rank == 0 && threadIdx.x == 0) {
+      long long pos = big ? (long long)atomicAdd(P.next, 1ULL) : P.big_cut;
+      if (pos >= P.big_cut) pos = P.big_cut + (long long)atomicAdd(P.next_small, 1ULL);
+      *tw.job_slot = pos;
+    }
     if (!tm.sync()) return;
     if (threadIdx.x == 0) s_job = __ldcg(tw.job_slot);
     __syncthreads();

@@ -187,7 +187,11 @@ struct BatchParams {
   char* cta_scratch;
   size_t cta_bytes;
   BatchDims dims;
-  int team;                    // CTAs per team
+  int team;                    // CTAs per team (the small teams)
+  int team_big;                // CTAs per big team (used when nbig > 0)
+  int nbig;                    // big teams: CTAs [0, nbig * team_big)
+  long long big_cut;           // queue positions [0, big_cut): the big jobs, served by big teams
+  unsigned long long* next_small;   // head of the queue positions [big_cut, njobs)
   unsigned long long* prof;    // kBatchPhases cycle sums of the team leaders (zeroed per launch)
   size_t panel_bytes;          // dynamic shared memory for the core solve panel (0: none)
 };

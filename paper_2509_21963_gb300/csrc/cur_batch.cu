@@ -35,7 +35,11 @@ struct cur_batch {
   // schedule
   int threads = 256;
   int team = 1;
+  int team_big = 0;          // 0: one team class
+  int nbig = 0;
+  int64_t big_cut = 0;
   int grid = 0;
+  std::vector<double> work;  // estimated work per job, in queue order
   cudaStream_t bstream = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   cudaGraphExec_t gexec = nullptr;
@@ -98,8 +102,10 @@ void drop_graph(cur_batch* b) {
   b->graph_tried = false;
 }
 
-// (Re)size the team and CTA scratch for the current team size.
-int plan_schedule(cur_batch* b, int team) {
+// (Re)size the team and CTA scratch for a schedule: nbig teams of team_big
+// CTAs serving the queue positions [0, big_cut) first (nbig = 0: none), and
+// as many teams of `team` CTAs as the remaining co-resident CTAs allow.
+int plan_schedule(cur_batch* b, int team, int team_big = 0, int nbig = 0, int64_t big_cut = 0) {
   cur_ctx* ctx = b->ctx;
   LaunchEnv env = benv(b);
   const size_t panel = batch_panel_bytes(b->dims.R);
@@ -107,10 +113,22 @@ int plan_schedule(cur_batch* b, int team) {
   if (max_ctas < 1) return bfail(ctx, CUR_ECUDA, "the batch kernel cannot be resident on this GPU");
   if (team < 1 || team > 32 || team > max_ctas)
     return bfail(ctx, CUR_EINVAL, "team size %d outside 1..%d", team, std::min(32, max_ctas));
-  const int teams = max_ctas / team;
-  const int grid = teams * team;
+  if (nbig < 0 || (nbig > 0 && (team_big < 1 || team_big > 32 ||
+                                (int64_t)nbig * team_big + team > max_ctas)))
+    return bfail(ctx, CUR_EINVAL, "%d big teams of %d CTAs leave no room for a team of %d (%d CTAs)",
+                 nbig, team_big, team, max_ctas);
+  if (nbig == 0) { team_big = 0; big_cut = 0; }
+  big_cut = std::max<int64_t>(0, std::min<int64_t>(big_cut, b->njobs));
+  const int bigctas = nbig * team_big;
+  const int teams = nbig + (max_ctas - bigctas) / team;
+  const int grid = bigctas + ((max_ctas - bigctas) / team) * team;
   BatchLayout L = batch_layout_dev(b->dims, team);
-  const size_t tb = al256(L.team_bytes), cb = al256(L.cta_bytes);
+  size_t tb = al256(L.team_bytes), cb = al256(L.cta_bytes);
+  if (nbig > 0) {
+    BatchLayout Lb = batch_layout_dev(b->dims, team_big);
+    tb = std::max(tb, al256(Lb.team_bytes));
+    cb = std::max(cb, al256(Lb.cta_bytes));
+  }
   const size_t need_t = tb * (size_t)teams, need_c = cb * (size_t)grid;
   BCK(cudaStreamSynchronize(b->bstream));
   if (need_t > b->team_alloc) {
@@ -135,8 +153,14 @@ int plan_schedule(cur_batch* b, int team) {
   BCK(cudaMemsetAsync(b->team_scratch, 0, need_t, b->bstream));
   BCK(cudaStreamSynchronize(b->bstream));
   b->team = team;
+  b->team_big = team_big;
+  b->nbig = nbig;
+  b->big_cut = big_cut;
   b->grid = grid;
   b->P.team = team;
+  b->P.team_big = team_big;
+  b->P.nbig = nbig;
+  b->P.big_cut = big_cut;
   b->P.team_scratch = b->team_scratch;
   b->P.team_bytes = tb;
   b->P.cta_scratch = b->cta_scratch;
@@ -149,7 +173,7 @@ int plan_schedule(cur_batch* b, int team) {
 // The launch sequence: queue head and status to zero, the kernel, the
 // per-job records to pinned host memory.
 cudaError_t enqueue(cur_batch* b) {
-  cudaError_t e = cudaMemsetAsync(b->P.next, 0, sizeof(unsigned long long), b->bstream);
+  cudaError_t e = cudaMemsetAsync(b->P.next, 0, 2 * sizeof(unsigned long long), b->bstream);
   if (e == cudaSuccess) e = cudaMemsetAsync(b->P.st, 0, sizeof(DevStatus), b->bstream);
   if (e == cudaSuccess)
     e = cudaMemsetAsync(b->P.prof, 0, sizeof(unsigned long long) * kBatchPhases, b->bstream);
@@ -253,6 +277,8 @@ int cur_batch_create(cur_ctx* ctx, const cur_batch_job* jobs, int64_t njobs, int
   for (int64_t k = 0; k < njobs; ++k) w[(size_t)k] = work_estimate(b->jobs[(size_t)k]);
   std::stable_sort(b->order.begin(), b->order.end(),
                    [&](int x, int y) { return w[(size_t)x] > w[(size_t)y]; });
+  b->work.resize((size_t)njobs);
+  for (int64_t k = 0; k < njobs; ++k) b->work[(size_t)k] = w[(size_t)b->order[(size_t)k]];
 
   // one allocation for everything the size of which depends only on the jobs
   size_t o = 0;
@@ -264,7 +290,7 @@ int cur_batch_create(cur_ctx* ctx, const cur_batch_job* jobs, int64_t njobs, int
   const size_t o_J = put(8 * (size_t)off_ij);
   const size_t o_U = put(8 * (size_t)off_u);
   const size_t o_h = put(8 * (size_t)off_h);
-  const size_t o_next = put(sizeof(unsigned long long));
+  const size_t o_next = put(2 * sizeof(unsigned long long));   // big and small queue heads
   const size_t o_st = put(sizeof(DevStatus));
   const size_t o_prof = put(sizeof(unsigned long long) * kBatchPhases);
   b->outputs_bytes = o;
@@ -291,6 +317,7 @@ int cur_batch_create(cur_ctx* ctx, const cur_batch_job* jobs, int64_t njobs, int
   b->P.rho_hist = reinterpret_cast<double*>(base + o_h);
   b->P.hist_len = off_h;
   b->P.next = reinterpret_cast<unsigned long long*>(base + o_next);
+  b->P.next_small = b->P.next + 1;
   b->P.st = reinterpret_cast<DevStatus*>(base + o_st);
   b->P.prof = reinterpret_cast<unsigned long long*>(base + o_prof);
   b->P.dims = d;
@@ -337,11 +364,24 @@ int cur_batch_set_team(cur_batch* b, int team) {
   return plan_schedule(b, team);
 }
 
+int cur_batch_set_classes(cur_batch* b, int team, int team_big, int nbig, int64_t big_cut) {
+  if (!b) return CUR_EINVAL;
+  return plan_schedule(b, team, team_big, nbig, big_cut);
+}
+
+int cur_batch_get_classes(const cur_batch* b, int* team_big, int* nbig, int64_t* big_cut) {
+  if (!b) return CUR_EINVAL;
+  if (team_big) *team_big = b->team_big;
+  if (nbig) *nbig = b->nbig;
+  if (big_cut) *big_cut = b->big_cut;
+  return CUR_OK;
+}
+
 int cur_batch_get_schedule(const cur_batch* b, int* team, int* grid, int* teams, int* graph) {
   if (!b) return CUR_EINVAL;
   if (team) *team = b->team;
   if (grid) *grid = b->grid;
-  if (teams) *teams = b->grid / b->team;
+  if (teams) *teams = b->nbig + (b->grid - b->nbig * b->team_big) / b->team;
   if (graph) *graph = b->gexec ? 1 : 0;
   return CUR_OK;
 }
@@ -405,15 +445,25 @@ int cur_batch_tune(cur_batch* b, const int* candidates, int ncand, int* best_tea
   cudaEvent_t e0, e1;
   BCK(cudaEventCreate(&e0));
   BCK(cudaEventCreate(&e1));
+  const int max_ctas = batch_max_ctas(benv(b), b->threads, b->a_f32, batch_panel_bytes(b->dims.R));
+  // Candidate schedules: one class of each candidate size, then, on top of the
+  // best of those, big-team classes (team_big in {8, 16} above it, 1 or 2 big
+  // teams) whose queue share is the big teams' share of the CTAs, counted in
+  // estimated work from the largest job down.
+  struct Cand { int team, team_big, nbig; int64_t cut; };
+  std::vector<Cand> cands;
+  for (int k = 0; k < ncand; ++k)
+    if (candidates[k] >= 1 && candidates[k] <= 32 && candidates[k] <= max_ctas)
+      cands.push_back({candidates[k], 0, 0, 0});
+  const size_t nsingle = cands.size();
+  double wsum = 0.0;
+  for (double x : b->work) wsum += x;
   int best = -1;
   float best_t = 0.f;
   int s = CUR_OK;
-  for (int k = 0; k < ncand && s == CUR_OK; ++k) {
-    const int t = candidates[k];
-    const int max_ctas = batch_max_ctas(benv(b), b->threads, b->a_f32,
-                                        batch_panel_bytes(b->dims.R));
-    if (t < 1 || t > 32 || t > max_ctas) continue;
-    s = plan_schedule(b, t);
+  for (size_t k = 0; k < cands.size() && s == CUR_OK; ++k) {
+    const Cand cd = cands[k];
+    s = plan_schedule(b, cd.team, cd.team_big, cd.nbig, cd.cut);
     if (s != CUR_OK) break;
     // capture the candidate's graph before timing (host-side work that would
     // otherwise leave the GPU idle inside the timed interval), then keep the
@@ -433,19 +483,33 @@ int cur_batch_tune(cur_batch* b, const int* candidates, int ncand, int* best_tea
       if (cand < 0.f || ms < cand) cand = ms;
     }
     if (s != CUR_OK) break;
-    if (best < 0 || cand < best_t) { best = t; best_t = cand; }
+    if (best < 0 || cand < best_t) { best = (int)k; best_t = cand; }
+    if (k + 1 == nsingle && best >= 0 && b->njobs > 1) {   // the big-team classes
+      const int ts = cands[(size_t)best].team;
+      for (int tbig : {8, 16})
+        for (int nb : {1, 2}) {
+          if (tbig <= ts || nb * tbig + ts > max_ctas) continue;
+          const double share = wsum * (double)(nb * tbig) / (double)max_ctas;
+          int64_t cut = 0;
+          double acc = 0.0;
+          while (cut < b->njobs && (cut == 0 || acc < share)) acc += b->work[(size_t)cut++];
+          if (cut >= b->njobs) cut = b->njobs - 1;
+          cands.push_back({ts, tbig, nb, cut});
+        }
+    }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (s != CUR_OK) return s;
   if (best < 0) return bfail(ctx, CUR_EINVAL, "no candidate team size fits this GPU");
-  if (best != b->team) {
-    s = plan_schedule(b, best);
+  const Cand bc = cands[(size_t)best];
+  if (best + 1 != (int)cands.size()) {
+    s = plan_schedule(b, bc.team, bc.team_big, bc.nbig, bc.cut);
     if (s != CUR_OK) return s;
     s = cur_batch_run(b);  // results of the chosen schedule
     if (s != CUR_OK) return s;
   }
-  if (best_team) *best_team = best;
+  if (best_team) *best_team = bc.team;
   if (best_ms) *best_ms = best_t;
   return CUR_OK;
 }

@@ -68,7 +68,30 @@ def test_batch_parity(ctx, dtype, team):
         ref = oracle.run(A, 1e-4, 8, 8, seed=s["seed"], mode=1)
         got = B.result(j)
         full += _check_job(A, got, ref, 8, 1e-4)
-    assert full >= len(specs) // 2
+    assert full == len(specs)   # every job's oracle selection is decided: compared in full
+    B.close()
+
+
+@pytest.mark.parametrize("team,team_big,nbig,cut", [(1, 8, 1, 3), (2, 16, 2, 6), (4, 8, 2, 23)])
+def test_batch_team_classes(ctx, team, team_big, nbig, cut):
+    """Two team classes in one launch (big teams take the `cut` largest jobs
+    first, then help with the rest): every job against the oracle over its
+    whole selection, as in test_batch_parity."""
+    import paper_2509_21963_gb300 as cur
+    specs, mats, dev = _jobs(24, seed=7, lo=16, hi=200, dtype=torch.float64)
+    B = cur.Batch(ctx, dev, 1e-4, 8, 8, seed=[s["seed"] for s in specs])
+    B.set_classes(team, team_big, nbig, cut)
+    sch = B.schedule()
+    assert (sch["team"], sch["team_big"], sch["nbig"], sch["big_cut"]) == (team, team_big, nbig, cut)
+    assert sch["teams"] == nbig + (sch["grid"] - nbig * team_big) // team
+    B.run()
+    full = 0
+    for j, (s, A) in enumerate(zip(specs, mats)):
+        ref = oracle.run(A, 1e-4, 8, 8, seed=s["seed"], mode=1)
+        full += _check_job(A, B.result(j), ref, 8, 1e-4)
+    assert full == len(specs)
+    with pytest.raises(cur.CurError):
+        B.set_classes(team, 32, 64, cut)   # no room left for a small team
     B.close()
 
 
