@@ -103,6 +103,13 @@ def parse():
     p.add_argument("--batch-kind", choices=["exp20", "poly1.5", "rank"], default="poly1.5")
     p.add_argument("--serve-requests", type=int, default=300)
     p.add_argument("--serve-rate", type=float, default=200.0, help="Poisson arrival rate (1/s)")
+    p.add_argument("--serve-pool", type=int, default=0,
+                   help="distinct matrices of the stream (0: one per request); request k uses "
+                        "matrix k mod pool, with its own sketch seed and tolerance, so that a "
+                        "stream whose matrices do not fit in HBM together can still be played")
+    p.add_argument("--serve-deadline", type=float, default=0.0,
+                   help="stop submitting after this many seconds of the stream (0: none); the "
+                        "requests not yet submitted are reported as the backlog")
     p.add_argument("--serve-min", type=int, default=512)
     p.add_argument("--serve-max", type=int, default=4096)
     p.add_argument("--serve-team", type=int, default=8)
@@ -548,7 +555,10 @@ def serve_workload_name(a):
     return (f"{a.serve_requests} requests, Poisson {a.serve_rate:g}/s, FP32 A with m, n "
             f"log-uniform in [{a.serve_min}, {a.serve_max}], spectra exp(-i/20) / i^-1.5 / exact "
             f"rank r~U[5,200], tol uniform over {{1e-2, 1e-4, 1e-6}}, b={SERVE_B}, c={SERVE_C}, "
-            f"{a.serve_budget_gb:g} GB admission budget")
+            f"{a.serve_budget_gb:g} GB admission budget"
+            + (f", {a.serve_pool} distinct matrices (request k uses matrix k mod {a.serve_pool} "
+               f"with its own sketch seed and tolerance)"
+               if 0 < getattr(a, "serve_pool", 0) < a.serve_requests else ""))
 
 
 def pct(xs, q):
@@ -613,8 +623,15 @@ def run_serve(a, ws, rank, local):
         dist.init_process_group("nccl")
     dev = f"cuda:{local}"
     arrivals, specs, tols = serve_stream(a, a.seed + 1000 * rank)
-    log("serve: generating matrices")
-    mats = [inputs.batch_matrix_torch(s, device=dev) for s in specs]
+    pool = a.serve_pool if 0 < a.serve_pool < len(specs) else len(specs)
+    if pool < len(specs):   # request k: matrix k mod pool, its own sketch seed and tolerance
+        specs = [dict(specs[k % pool], seed=specs[k % pool]["seed"], sketch_seed=specs[k]["seed"])
+                 for k in range(len(specs))]
+    log(f"serve: generating {pool} matrices")
+    uniq = [inputs.batch_matrix_torch(s, device=dev) for s in specs[:pool]]
+    mats = [uniq[k % pool] for k in range(len(specs))]
+    for s in specs:
+        s.setdefault("sketch_seed", s["seed"])
     torch.cuda.synchronize()
     log("serve: matrices ready")
     ctx = cur.Context(local)
@@ -625,8 +642,8 @@ def run_serve(a, ws, rank, local):
     # warm-up: a few small requests through the server and the plain path
     small = sorted(range(len(specs)), key=lambda j: specs[j]["m"] * specs[j]["n"])[:4]
     for j in small:
-        S.wait(S.submit(mats[j], tols[j], SERVE_B, SERVE_C, seed=specs[j]["seed"]))
-        ctx.run(mats[j], tols[j], SERVE_B, SERVE_C, specs[j]["seed"])
+        S.wait(S.submit(mats[j], tols[j], SERVE_B, SERVE_C, seed=specs[j]["sketch_seed"]))
+        ctx.run(mats[j], tols[j], SERVE_B, SERVE_C, specs[j]["sketch_seed"])
     S.drain()
     for st in list(S._keep):
         S.release(st)
@@ -634,15 +651,22 @@ def run_serve(a, ws, rank, local):
     def play(host):
         """Submit every request at its arrival time; returns per-request
         (latency, queue, rank, status) and the makespan in s."""
-        srcs = [m.cpu().numpy() for m in mats] if host else mats
+        if host:
+            hs = [m.cpu().numpy() for m in uniq]
+            srcs = [hs[k % len(hs)] for k in range(len(mats))]
+        else:
+            srcs = mats
         barrier_sync()
         t0 = time.perf_counter()
         tickets = []
         for k in range(len(specs)):
+            if a.serve_deadline > 0 and time.perf_counter() - t0 > a.serve_deadline:
+                break   # the rest is the backlog at the deadline
             delay = arrivals[k] - (time.perf_counter() - t0)
             if delay > 0:
                 time.sleep(delay)
-            tickets.append(S.submit(srcs[k], tols[k], SERVE_B, SERVE_C, seed=specs[k]["seed"]))
+            tickets.append(S.submit(srcs[k], tols[k], SERVE_B, SERVE_C,
+                                    seed=specs[k]["sketch_seed"]))
         out = []
         for tk in tickets:
             S.wait(tk)
@@ -665,9 +689,12 @@ def run_serve(a, ws, rank, local):
     launches0 = S.stats()["launches"]
     res, makespan = play(False)
     clk = clocks.stop()
+    backlog = len(specs) - len(res)
     lat = [x[0] for x in res]
     stats = S.stats()
     flops = sum(serve_flops(s["m"], s["n"], x[2]) for s, x in zip(specs, res))
+    offered = sum(serve_flops(s["m"], s["n"], serve_rank_model(s, t, SERVE_B))
+                  for s, t in zip(specs, tols))
     statuses = np.bincount([x[3] for x in res], minlength=8).tolist()
     met = sum(1 for x in res if x[3] == cur.CUR_OK)
     log(f"serve: p50 {pct(lat, 50):.1f} ms p99 {pct(lat, 99):.1f} ms makespan {makespan:.2f} s")
@@ -690,16 +717,19 @@ def run_serve(a, ws, rank, local):
         log("serve: plain path, serially")
         end, lat_p = 0.0, []
         for k in range(len(specs)):
+            if a.serve_deadline > 0 and end > a.serve_deadline:
+                break   # the same deadline on the simulated clock
             torch.cuda.synchronize()
             w0 = time.perf_counter()
-            ctx.run(mats[k], tols[k], SERVE_B, SERVE_C, specs[k]["seed"])
+            ctx.run(mats[k], tols[k], SERVE_B, SERVE_C, specs[k]["sketch_seed"])
             torch.cuda.synchronize()
             d = time.perf_counter() - w0
             start = max(arrivals[k], end)
             end = start + d
             lat_p.append((end - arrivals[k]) * 1000.0)
         plain = {"p50_ms": pct(lat_p, 50), "p99_ms": pct(lat_p, 99),
-                 "throughput_rps": len(specs) / end, "busy_s": end}
+                 "throughput_rps": len(lat_p) / end, "busy_s": end, "served": len(lat_p),
+                 "backlog_at_deadline": len(specs) - len(lat_p)}
 
     fp64_meas = ctx.fp64_tflops()
     cpu = None
@@ -721,6 +751,10 @@ def run_serve(a, ws, rank, local):
             "dtype": "f64 (FP32 A)", "data": "synthetic",
             "p99_ms": pct(lat, 99), "throughput_rps": len(res) / makespan,
             "queue_p50_ms": pct([x[1] for x in res], 50), "met_tolerance": met,
+            "served": len(res), "backlog_at_deadline": backlog,
+            "offered_load": {"tflop_model": offered / 1e12,
+                             "arrival_span_s": float(arrivals[-1]),
+                             "tflops_needed_model": offered / 1e12 / float(arrivals[-1])},
             "config": {"workload": serve_workload_name(a), "team": a.serve_team,
                        "streams": a.serve_streams, "big_elements": a.serve_big,
                        "big_lanes": a.serve_lanes,
