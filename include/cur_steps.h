@@ -158,6 +158,16 @@ int cur_test_wait_timeout(cur_ctx *ctx, int which, int nblocks, double budget_ms
  * synchronises the context's stream. */
 int cur_probe_fp64_tflops(cur_ctx *ctx, double *tflops);
 
+/* Latency of dependent operations on the context's device, in SM cycles per
+ * operation (one warp, a chain of 256), into cycles[0 .. n-1] in this order:
+ * FP64 FMA, FP64 FMA with one active lane, FP64 add, FP64 shuffle + add,
+ * FP64 divide, FP64 square root (+ add), FP64 compare-and-select, FP32 FMA,
+ * 64-bit integer shuffle + max, dependent L2 load; entries past the tenth are
+ * 0.  The paper has no counterpart: these figures decide which operations the
+ * latency-bound steps (LUPP, the small QR) keep off their critical paths.
+ * Allocates 33 KB of device memory for the call; synchronises the stream. */
+int cur_probe_latency(cur_ctx *ctx, double *cycles, int n);
+
 #ifdef __cplusplus
 }
 #endif

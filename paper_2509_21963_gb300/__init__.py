@@ -93,6 +93,7 @@ _SIGNATURES = {
     "cur_step_sketch_q": (_int, [_vp, _vp, _i64, _vp, _i64, _i64, _i64, _int, _vp, _vp]),
     "cur_step_sketch_fx": (_int, [_vp, _vp, _i64, _vp, _i64, _i64, _i64, _vp, _vp]),
     "cur_probe_fp64_tflops": (_int, [_vp, ctypes.POINTER(_dbl)]),
+    "cur_probe_latency": (_int, [_vp, ctypes.POINTER(_dbl), _int]),
     "cur_test_wait_timeout": (_int, [_vp, _int, _int, _dbl]),
     "cur_step_lupp": (_int, [_vp, _vp, _i64, _i64, _i64, _i64, _vp, _vp]),
     "cur_step_pinv": (_int, [_vp, _vp, _i64, _i64, _i64, _dbl, _vp, _vp]),
@@ -331,6 +332,15 @@ class Context:
     def wait_timeout_status(self, which: int, nblocks: int = 2, budget_ms: float = 2.0) -> int:
         """Status of cur_test_wait_timeout (CUR_ETIMEOUT when the bounded wait gave up)."""
         return lib().cur_test_wait_timeout(self.ptr, int(which), int(nblocks), float(budget_ms))
+
+    LATENCY_KINDS = ("dfma", "dfma_one_lane", "dadd", "shfl_dadd", "ddiv", "dsqrt_add",
+                     "dsetp_select", "ffma", "shfl_i64_max", "l2_load")
+
+    def latency_cycles(self) -> dict:
+        """Cycles per dependent operation (include/cur_steps.h, cur_probe_latency)."""
+        arr = (_dbl * len(self.LATENCY_KINDS))()
+        _check(self.ptr, lib().cur_probe_latency(self.ptr, arr, len(self.LATENCY_KINDS)))
+        return dict(zip(self.LATENCY_KINDS, list(arr)))
 
     def fp64_tflops(self) -> float:
         """Measured FP64 FMA rate of the device (TFLOP/s)."""

@@ -29,10 +29,106 @@ __global__ void __launch_bounds__(256) fma_probe_kernel(double seed, double* sin
   if (s == 0.1234) sink[0] = s;   // keeps the chains live; never true for these inputs
 }
 
+// Latency probes: one warp runs a chain of kLatN dependent operations of one
+// kind between two clock64 reads; cycles per operation go to cyc[kind].
+constexpr int kLatN = 256;
+enum LatKind {
+  kLatDfma = 0, kLatDfmaOneLane, kLatDadd, kLatShflDadd, kLatDdiv, kLatDsqrt, kLatDsetp,
+  kLatFfma, kLatShflI64Max, kLatL2Load, kLatKinds
+};
+
+__global__ void lat_fp_kernel(int kind, double seed, const long long* chain, double* sink,
+                              long long* cyc) {
+  const int lane = threadIdx.x & 31;
+  double x = seed + lane * 1e-3;
+  const double a = 1.0000001, b = 1e-9;
+  if (kind == kLatDfmaOneLane && lane != 0) return;
+  const long long t0 = clock64();
+  switch (kind) {
+    case kLatDfma: case kLatDfmaOneLane:
+      for (int i = 0; i < kLatN; ++i) x = fma(x, a, b);
+      break;
+    case kLatDadd:
+      for (int i = 0; i < kLatN; ++i) x = x + b;
+      break;
+    case kLatShflDadd:
+      for (int i = 0; i < kLatN; ++i) x = x + __shfl_xor_sync(0xffffffffu, x, 1 + (i & 15)) * 1e-300;
+      break;
+    case kLatDdiv:
+      for (int i = 0; i < kLatN; ++i) x = a / x;
+      break;
+    case kLatDsqrt:
+      for (int i = 0; i < kLatN; ++i) x = sqrt(x) + b;
+      break;
+    case kLatDsetp:
+      for (int i = 0; i < kLatN; ++i) x = x > b ? x * a : x + b;
+      break;
+    case kLatFfma: {
+      float f = (float)seed;
+      for (int i = 0; i < kLatN; ++i) f = fmaf(f, 1.0000001f, 1e-9f);
+      x = f;
+      break;
+    }
+    case kLatShflI64Max: {
+      long long k = __double_as_longlong(x);
+      for (int i = 0; i < kLatN; ++i) {
+        const long long o = __shfl_xor_sync(0xffffffffu, k, 1 + (i & 15));
+        k = o > k ? o : k + 1;
+      }
+      x = (double)k;
+      break;
+    }
+    case kLatL2Load: {   // dependent L2 loads (the chain is a permutation of 0..4095)
+      long long idx = lane;
+      for (int i = 0; i < kLatN; ++i) idx = __ldcg(chain + idx);
+      x = (double)idx;
+      break;
+    }
+  }
+  const long long t1 = clock64();
+  if (lane == 0) cyc[kind] = t1 - t0;
+  if (x == 0.123) sink[0] = x;   // keeps the chain live; never true for these inputs
+}
+
 }  // namespace
 }  // namespace cur
 
 using namespace cur;
+
+extern "C" int cur_probe_latency(cur_ctx* ctx, double* cycles, int n) {
+  if (!ctx || !cycles || n < 1) return CUR_EINVAL;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) { cudaGetLastError(); return CUR_ECUDA; }
+  constexpr int kChain = 4096;
+  long long* dev = nullptr;   // chain[kChain], cyc[kLatKinds], sink
+  int st = CUR_OK;
+  if (cudaMalloc(&dev, sizeof(long long) * (kChain + kLatKinds + 1)) != cudaSuccess) {
+    cudaGetLastError();
+    return CUR_ECUDA;
+  }
+  long long host[kChain];
+  for (int i = 0; i < kChain; ++i) host[i] = (long long)((i * 577 + 1031) % kChain);
+  long long* chain = dev;
+  long long* cyc = dev + kChain;
+  double* sink = reinterpret_cast<double*>(dev + kChain + kLatKinds);
+  if (cudaMemcpyAsync(chain, host, sizeof(host), cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess)
+    st = CUR_ECUDA;
+  for (int k = 0; k < kLatKinds && st == CUR_OK; ++k) {
+    for (int rep = 0; rep < 2; ++rep)   // the second run is the measured one (warm)
+      lat_fp_kernel<<<1, 32, 0, ctx->stream>>>(k, 1.5, chain, sink, cyc);
+  }
+  long long c[kLatKinds];
+  if (st == CUR_OK &&
+      (cudaGetLastError() != cudaSuccess ||
+       cudaMemcpyAsync(c, cyc, sizeof(c), cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess ||
+       cudaStreamSynchronize(ctx->stream) != cudaSuccess)) {
+    cudaGetLastError();
+    st = CUR_ECUDA;
+  }
+  if (st == CUR_OK)
+    for (int k = 0; k < n; ++k) cycles[k] = k < kLatKinds ? (double)c[k] / kLatN : 0.0;
+  cudaFree(dev);
+  return st;
+}
 
 extern "C" int cur_probe_fp64_tflops(cur_ctx* ctx, double* tflops) {
   if (!ctx || !tflops) return CUR_EINVAL;
