@@ -510,6 +510,7 @@ int run_device(cur_ctx* ctx, const void* A, int64_t m, int64_t n, int64_t lda, i
 
   double rho = 1.0;
   int64_t r = 0;
+  int64_t lt_bk = 0;   // rows of L^T still to form from the last iteration's S^row and N^+
   while (rho > tol_eff && r < max_rank) {  // Algorithm 1's loop test
     const int64_t bk = (int64_t)b < max_rank - r ? (int64_t)b : max_rank - r;
     if (r + bk > rcap) {  // grow the Lemma 1 factors, keeping their content
@@ -524,6 +525,15 @@ int run_device(cur_ctx* ctx, const void* A, int64_t m, int64_t n, int64_t lda, i
     double* SrowT = bp<double>(ctx, B_SROWT);
     int64_t* Jk = Jd + r;
     int64_t* Ik = Id + r;
+    if (lt_bk > 0) {   // L_{k-1}^T = N^+^T S^row^T of the last iteration: needed only now that
+                       // the loop goes on (its S^row and N^+ are still in place)
+      tick(ctx, CUR_PHASE_FACTORS);
+      if ((st = gemm(ctx, gargs(lt_bk, m, lt_bk, 1.0, bp<double>(ctx, B_NP), lt_bk, true, SrowT, m,
+                                false, false, 0.0, nullptr, 0, LT + (size_t)(r - lt_bk) * m, m))) !=
+          CUR_OK)
+        return fail_res(st);
+      lt_bk = 0;
+    }
 
     // column selection: J_k = LUPP on S^col (candidates: the n columns)
     tick(ctx, CUR_PHASE_LUPP_COL);
@@ -564,9 +574,9 @@ int run_device(cur_ctx* ctx, const void* A, int64_t m, int64_t n, int64_t lda, i
     // N^+ by pivoted QR; rank threshold |I| 2^-52 |R_00(N_1)|
     if ((st = pinv_call(ctx, B_QRSMALL, Nd, bk, bk, bk, 2, (double)(r + bk),
                         &dstat(ctx)->scalar[2], Np, bk)) != CUR_OK) return fail_res(st);
-    // L_k^T = (S^row N^+)^T = N^+^T S^row^T   (bk x m)
-    if ((st = gemm(ctx, gargs(bk, m, bk, 1.0, Np, bk, true, SrowT, m, false, false, 0.0, nullptr, 0,
-                              LT + (size_t)r * m, m))) != CUR_OK) return fail_res(st);
+    // L_k^T = (S^row N^+)^T = N^+^T S^row^T (bk x m) is formed at the top of
+    // the next iteration, if there is one
+    lt_bk = bk;
     // column residual (Lemma 1): S^col -= (S^col(:,J_k) N^+) Rt_k, fused ||S^col||^2
     tick(ctx, CUR_PHASE_COL_RES);
     double* SJk = bp<double>(ctx, B_SJK);
