@@ -376,15 +376,19 @@ __global__ void __launch_bounds__(kThreads) qrcp_solve_kernel(SolveParams S) {
 }
 
 // Solve for p <= kSolveSmallP: the same arithmetic as qrcp_solve_kernel with
-// the reflectors and R_11 staged in shared memory (shared by the CTA's eight
+// the reflectors and R_11 staged in shared memory (shared by the CTA's
 // warps, one warp per column l of the identity), the column y in registers
 // (row i = lane + 32 s in y[s]) and R_11's diagonal applied as reciprocals,
 // so a reflector costs one warp reduction and a back-substitution step a
 // multiply and an FMA (GB300 runs a dependent FP64 operation in ~64 cycles, a
 // divide in ~560).
 constexpr int kSolveSmallP = 64;
+// Four warps per CTA: one warp per SM sub-partition, so a CTA's FP64 work
+// stays latency bound instead of queueing on the SM's FP64 pipe (eight warps
+// per CTA kept that pipe ~70 % busy on the 7 SMs of a p = 50 solve).
+constexpr int kSolveSmallThreads = 128;
 
-__global__ void __launch_bounds__(kThreads) qrcp_solve_small_kernel(SolveParams S) {
+__global__ void __launch_bounds__(kSolveSmallThreads) qrcp_solve_small_kernel(SolveParams S) {
   extern __shared__ double ssm[];
   if (S.st && *((const volatile int*)&S.st->err) != 0) return;
   const int p = (int)S.p, q = (int)S.q;
@@ -395,18 +399,18 @@ __global__ void __launch_bounds__(kThreads) qrcp_solve_small_kernel(SolveParams 
   double* tau = Rs + (size_t)k * k;      // k
   double* rinv = tau + k;                // k
   int* perm = reinterpret_cast<int*>(rinv + k);   // q
-  for (int e = threadIdx.x; e < k * p; e += kThreads) {
+  for (int e = threadIdx.x; e < k * p; e += kSolveSmallThreads) {
     const int j = e / p, i = e - j * p;
     Vs[e] = i >= j ? S.V[(int64_t)j * p + i] : 0.0;
   }
-  for (int e = threadIdx.x; e < k * k; e += kThreads) {
+  for (int e = threadIdx.x; e < k * k; e += kSolveSmallThreads) {
     const int i = e / k, a = e - i * k;
     Rs[e] = a < i ? S.Rc[S.perm[i] * p + a] : 0.0;
   }
-  for (int j = threadIdx.x; j < k; j += kThreads) { tau[j] = S.tau[j]; rinv[j] = 1.0 / S.rdiag[j]; }
-  for (int i = threadIdx.x; i < q; i += kThreads) perm[i] = (int)S.perm[i];
+  for (int j = threadIdx.x; j < k; j += kSolveSmallThreads) { tau[j] = S.tau[j]; rinv[j] = 1.0 / S.rdiag[j]; }
+  for (int i = threadIdx.x; i < q; i += kSolveSmallThreads) perm[i] = (int)S.perm[i];
   __syncthreads();
-  const int l = blockIdx.x * kWarps + wid;
+  const int l = blockIdx.x * (kSolveSmallThreads / 32) + wid;
   if (l >= p) return;
   double y0 = lane == l ? 1.0 : 0.0, y1 = lane + 32 == l ? 1.0 : 0.0;   // rows lane, lane + 32
   const bool r1 = lane + 32 < p;
@@ -999,7 +1003,8 @@ cudaError_t launch_qrcp_pinv(const LaunchEnv& env, const double* M, int64_t p, i
                        sizeof(int) * (size_t)q;
     e = smem_opt_in((const void*)qrcp_solve_small_kernel, ssm);
     if (e != cudaSuccess) return e;
-    qrcp_solve_small_kernel<<<blocks, kThreads, ssm, env.stream>>>(S);
+    const unsigned wpc = kSolveSmallThreads / 32;
+    qrcp_solve_small_kernel<<<(unsigned)((p + wpc - 1) / wpc), kSolveSmallThreads, ssm, env.stream>>>(S);
     return cudaGetLastError();
   }
   qrcp_solve_kernel<<<blocks, kThreads, 0, env.stream>>>(S);
