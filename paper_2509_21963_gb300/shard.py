@@ -24,7 +24,7 @@ doubles and all-reduces of b m + r b doubles plus one scalar.
 
 The arithmetic of a rank goes through a backend object; CudaBackend runs the
 library's C-ABI step kernels (cur_step_*) on the rank's GPU.  Without an
-initialised process group the driver runs as a single rank.
+initialised process group the run uses a single rank.
 """
 from __future__ import annotations
 
@@ -54,7 +54,7 @@ def column_range(n: int, world: int, rank: int) -> tuple[int, int]:
 
 
 class _Comm:
-    """The collectives the driver uses, on a backend's arrays."""
+    """The collectives of a sharded run, on a backend's arrays."""
 
     def __init__(self, backend, group):
         import torch.distributed as dist

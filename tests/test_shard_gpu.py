@@ -1,4 +1,4 @@
-"""The sharded driver on the GPU step kernels (CudaBackend, one rank): it makes
+"""The sharded run on the GPU step kernels (CudaBackend, one rank): it makes
 the same kernel calls in the same order as cur_run, so I, J, U and rho equal
 cur_run's bit for bit.  Also the two step entry points it adds to the C ABI
 (cur_step_gemm, cur_step_gather) against plain PyTorch FP64 on the CPU."""
