@@ -37,6 +37,10 @@ struct cur_ctx {
   // host-input runs: a copy stream and per-row-block events (created on demand)
   cudaStream_t copy_stream = nullptr;
   std::vector<cudaEvent_t> copy_ev;
+  // a second compute stream: the sketch matrix is generated there while the
+  // column-scale pass of the FP64 tensor-core sketch reads A (created on demand)
+  cudaStream_t side_stream = nullptr;
+  cudaEvent_t side_ev[2] = {nullptr, nullptr};
 };
 
 namespace cur {

@@ -364,6 +364,40 @@ int sketch_fx(cur_ctx* ctx, const double* G, int64_t c, const double* A, int64_t
   return CUR_OK;
 }
 
+// The FP64 tensor-core sketch with G generated from the seed: G and G_q on
+// the side stream while the column-scale pass reads A on the context's stream
+// (independent work: the FP64 Philox / Box-Muller kernel and an HBM-bound read),
+// joined before the tensor-core pass.
+int sketch_fx_seeded(cur_ctx* ctx, uint64_t seed, int64_t c, const double* A, int64_t m,
+                     int64_t n, int64_t lda, double* Y, int slot, BufId parts_id, BufId scratch_id) {
+  LaunchEnv env = env_of(ctx);
+  TRY(ensure(ctx, B_OMEGA, sizeof(double) * (size_t)(c * m)));
+  TRY(ensure(ctx, scratch_id, sketch_fx_scratch_bytes(c, m, n)));
+  TRY(ensure(ctx, parts_id, sizeof(double) * (size_t)sketch_fx_max_parts(c, n)));
+  if (!ctx->side_stream) CK(cudaStreamCreateWithFlags(&ctx->side_stream, cudaStreamNonBlocking));
+  for (auto& ev : ctx->side_ev)
+    if (!ev) CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  LaunchEnv side = env;
+  side.stream = ctx->side_stream;
+  double* G = bp<double>(ctx, B_OMEGA);
+  void* scratch = ctx->buf[scratch_id].p;
+  tick(ctx, CUR_PHASE_SCALES);
+  CK(cudaEventRecord(ctx->side_ev[0], env.stream));
+  CK(cudaStreamWaitEvent(side.stream, ctx->side_ev[0], 0));
+  CK(launch_gaussian(side, seed, c, m, G, m));
+  CK(launch_sketch_fx_q8(side, G, c, m, n, scratch));
+  CK(cudaEventRecord(ctx->side_ev[1], side.stream));
+  CK(launch_sketch_fx_colscales(env, c, A, lda, m, n, scratch));
+  CK(cudaStreamWaitEvent(env.stream, ctx->side_ev[1], 0));
+  tick(ctx, CUR_PHASE_SKETCH);
+  int64_t nparts = 0;
+  CK(launch_sketch_fx_main(env, c, A, lda, m, n, scratch, Y, bp<double>(ctx, parts_id), &nparts,
+                           &dstat(ctx)->err));
+  ctx->launches += 5 + (c + 63) / 64;
+  TRY(sum_parts(ctx, bp<double>(ctx, parts_id), nparts, &dstat(ctx)->scalar[slot]));
+  return CUR_OK;
+}
+
 int check_fx_form(cur_ctx* ctx, const void* A, int64_t lda, int dtype) {
   if (dtype != CUR_F64) return fail(ctx, CUR_EINVAL, "the FP64 tensor-core sketch needs FP64 A");
   if (lda % 2 != 0 || (reinterpret_cast<uintptr_t>(A) & 15) != 0)
@@ -439,7 +473,9 @@ int run_device(cur_ctx* ctx, const void* A, int64_t m, int64_t n, int64_t lda, i
 
   // sketch matrix G; initial sketch S_0 = Y = G A and ||Y||_F (the one full pass over A)
   const double* G = o ? o->omega : nullptr;
-  if (!G) {
+  const int smode0 = o ? o->sketch_mode : CUR_SKETCH_F64;
+  const bool fx_seeded = smode0 == CUR_SKETCH_F64_TC && !G;
+  if (!G && !fx_seeded) {
     TRY(ensure(ctx, B_OMEGA, sizeof(double) * (size_t)(c * m)));
     tick(ctx, CUR_PHASE_GAUSSIAN);
     CK(launch_gaussian(env, seed, c, m, bp<double>(ctx, B_OMEGA), m));
@@ -456,6 +492,9 @@ int run_device(cur_ctx* ctx, const void* A, int64_t m, int64_t n, int64_t lda, i
                              B_PARTS));
   } else if (smode == CUR_SKETCH_F64) {
     TRY(sketch_f64(ctx, G, c, A, f32, m, n, lda, S, 0, B_PARTS));
+  } else if (smode == CUR_SKETCH_F64_TC && fx_seeded) {
+    TRY(sketch_fx_seeded(ctx, seed, c, static_cast<const double*>(A), m, n, lda, S, 0, B_PARTS,
+                         B_FX));
   } else if (smode == CUR_SKETCH_F64_TC) {
     TRY(sketch_fx(ctx, G, c, static_cast<const double*>(A), m, n, lda, S, 0, B_PARTS, B_FX));
   } else {
@@ -687,6 +726,12 @@ void cur_free(cur_ctx* ctx) {
     cudaStreamSynchronize(ctx->copy_stream);
     cudaStreamDestroy(ctx->copy_stream);
   }
+  if (ctx->side_stream) {
+    cudaStreamSynchronize(ctx->side_stream);
+    cudaStreamDestroy(ctx->side_stream);
+  }
+  for (auto e : ctx->side_ev)
+    if (e) cudaEventDestroy(e);
   if (ctx->st_host) cudaFreeHost(ctx->st_host);
   delete ctx;
 }

@@ -158,6 +158,12 @@ int64_t sketch_fx_max_parts(int64_t c, int64_t n);
 cudaError_t launch_sketch_fx_scales(const LaunchEnv& env, const double* G, int64_t c,
                                     const double* A, int64_t lda, int64_t m, int64_t n,
                                     void* scratch);
+// The two halves of launch_sketch_fx_scales, for running them on two streams:
+// G_q from G, and the column exponents of A (with the zeroing of the sums).
+cudaError_t launch_sketch_fx_q8(const LaunchEnv& env, const double* G, int64_t c, int64_t m,
+                                int64_t n, void* scratch);
+cudaError_t launch_sketch_fx_colscales(const LaunchEnv& env, int64_t c, const double* A,
+                                       int64_t lda, int64_t m, int64_t n, void* scratch);
 cudaError_t launch_sketch_fx_main(const LaunchEnv& env, int64_t c, const double* A, int64_t lda,
                                   int64_t m, int64_t n, void* scratch, double* Y,
                                   double* sumsq_part, int64_t* nparts, int* err);

@@ -48,6 +48,24 @@ __device__ __forceinline__ Best warp_best(Best b) {
   return b;
 }
 
+// warp_best with three 32-bit warp reductions (redux.sync) instead of five
+// 64-bit shuffle rounds: the largest key's high word, then its low word among
+// the lanes that hold that high word, then the smallest index among the lanes
+// that hold the whole key.  Keys are >= -3 (shifted to >= 0 here); indices of
+// candidates are below 2^31 (none: LLONG_MAX).  Every lane gets the result.
+__device__ __forceinline__ Best warp_best_redux(const Best& b) {
+  const unsigned long long u = (unsigned long long)(b.a + 3);
+  const unsigned hi = (unsigned)(u >> 32), lo = (unsigned)u;
+  const unsigned mhi = __reduce_max_sync(0xffffffffu, hi);
+  const unsigned mlo = __reduce_max_sync(0xffffffffu, hi == mhi ? lo : 0u);
+  const unsigned idx = (hi == mhi && lo == mlo && b.i != LLONG_MAX) ? (unsigned)b.i : 0xFFFFFFFFu;
+  const unsigned mi = __reduce_min_sync(0xffffffffu, idx);
+  Best r;
+  r.a = (long long)(((unsigned long long)mhi << 32) | mlo) - 3;
+  r.i = mi == 0xFFFFFFFFu ? LLONG_MAX : (long long)mi;
+  return r;
+}
+
 // The winner among G per-CTA records {key, index, ...} (slot g at slot[g *
 // stride]), read by one warp with every lane's loads in flight together; each
 // lane returns the winner and its record number (-1 when no record has a
@@ -365,12 +383,12 @@ __global__ void __launch_bounds__(kThreads) lupp_smem_kernel(LuppParams p, int p
       const long long a = mag_key(v);
       if (better(a, lo + li, b)) { b.a = a; b.i = lo + li; }
     }
-    b = warp_best(b);
+    b = warp_best_redux(b);
     if (lane == 0) red[wid] = b;
     __syncthreads();
     if (wid == 0) {
       Best c = lane < kThreads / 32 ? red[lane] : Best{-1, LLONG_MAX};
-      c = warp_best(c);
+      c = warp_best_redux(c);
       if (lane == 0) s_win = c;
     }
     __syncthreads();

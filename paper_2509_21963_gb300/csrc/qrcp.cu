@@ -748,11 +748,11 @@ __global__ void __launch_bounds__(kClMaxLocal * 32) qrcp_cluster_kernel(QrcpPara
     }
     const int jp = wc;
     const int own = jp % CL, cjp = jp / CL;
-    {   // the pivot column's rows j.. from its owner (frozen from now on)
+    if (tid != 0) {   // the pivot column's rows j.. from its owner (frozen from now on),
+                      // while thread 0 forms the reflector's scalars
       const double* srcc = cl.map_shared_rank(Rl + (size_t)cjp * p, own);
-      for (int i = j + tid; i < p; i += blockDim.x) vcol[i] = srcc[i];
-    }
-    if (tid == 0) {
+      for (int i = j + tid - 1; i < p; i += blockDim.x - 1) vcol[i] = srcc[i];
+    } else {
       const double* rr = rec + (par * CL + wl) * kClRec;
       const double x0 = rr[2], s1 = rr[3];
       const double normx = sqrt(__longlong_as_double(wk));

@@ -602,7 +602,24 @@ cudaError_t launch_sketch_fx_scales(const LaunchEnv& env, const double* G, int64
   long long* acc = f.acc_lo;
 
   cudaError_t e = launch_gaussian_q8(env, G, c, m, ldq, Gq);
-  if (e == cudaSuccess) e = cudaMemsetAsync(cmax, 0, sizeof(unsigned long long) * (size_t)n, env.stream);
+  if (e == cudaSuccess) e = launch_sketch_fx_colscales(env, c, A, lda, m, n, scratch);
+  return e;
+}
+
+cudaError_t launch_sketch_fx_q8(const LaunchEnv& env, const double* G, int64_t c, int64_t m,
+                                int64_t n, void* scratch) {
+  const FxScratch f = carve_fx(scratch, c, m, n);
+  return launch_gaussian_q8(env, G, c, m, ldq_of(m), f.Gq);
+}
+
+cudaError_t launch_sketch_fx_colscales(const LaunchEnv& env, int64_t c, const double* A,
+                                       int64_t lda, int64_t m, int64_t n, void* scratch) {
+  if (!fx_args_ok(c, A, lda, m, n)) return cudaErrorInvalidValue;
+  const FxScratch f = carve_fx(scratch, c, m, n);
+  unsigned long long* cmax = f.cmax;
+  int* cexp = f.cexp;
+  long long* acc = f.acc_lo;
+  cudaError_t e = cudaMemsetAsync(cmax, 0, sizeof(unsigned long long) * (size_t)n, env.stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(acc, 0, 2 * sizeof(long long) * (size_t)(c * n), env.stream);
   if (e != cudaSuccess) return e;
   {
