@@ -782,11 +782,12 @@ def run_serve(a, ws, rank, local):
 # Precision-form workload
 # ---------------------------------------------------------------------------
 PREC_M, PREC_N, PREC_RANK = 65536, 32768, 4096
-PREC_CASES = (  # (tol, b, c, sketch modes, rank cap); mode 0 = FP64 sketch, S = digits
-    (1e-2, 100, 110, (0, 1), 2048),   # one digit: its sketch error (~0.1 here) bounds its reach
-    (1e-3, 100, 110, (0, 2), 4096),
-    (1e-6, 56, 62, (0, 3, 4), 6144),  # CUR needs ~1.4x the SVD rank on this spectrum;
-)                                     # c <= 64 for four digits
+PREC_CASES = (  # (tol, b, c, (sketch mode, residual planes) forms, rank cap); mode 0 = FP64
+    # sketch, S = digits; planes 0 = FP64 residual products, 2 / 3 = BF16 planes on tcgen05
+    (1e-2, 100, 110, ((0, 0), (1, 0), (1, 2)), 2048),   # one digit: its sketch error (~0.1
+    (1e-3, 100, 110, ((0, 0), (2, 0), (2, 2), (2, 3)), 4096),   # here) bounds its reach
+    (1e-6, 56, 62, ((0, 0), (3, 0), (4, 0)), 6144),  # CUR needs ~1.4x the SVD rank here; c <= 64
+)                                                    # for four digits; planes stall near 2e-6
 
 
 def precision_workload_name():
@@ -829,8 +830,8 @@ def run_precision(a, ws, rank, local):
     stream = torch.cuda.current_stream()
     forms = []
     for tol, b, c, modes, cap in PREC_CASES:
-        for mode in modes:
-            kw = dict(sketch_mode=mode, timing=True, max_rank=cap)
+        for mode, planes in modes:
+            kw = dict(sketch_mode=mode, timing=True, max_rank=cap, residual_planes=planes)
             st, out = ctx.run_raw(A, tol, b, c, a.seed, **kw)   # warm
             cur.lib().cur_result_free(out)
             e0 = torch.cuda.Event(enable_timing=True)
@@ -843,7 +844,8 @@ def run_precision(a, ws, rank, local):
             if st not in (cur.CUR_OK, cur.CUR_TOL_UNREACHED) or not out:
                 msg = ctx.last_error()
                 log(f"precision: tol {tol:g} mode {mode}: status {st}: {msg}")
-                forms.append({"tol": tol, "b": b, "c": c, "sketch_mode": mode, "status": int(st),
+                forms.append({"tol": tol, "b": b, "c": c, "sketch_mode": mode,
+                              "residual_planes": planes, "status": int(st),
                               "error": msg, "meets_tol": False})
                 continue
             res = cur._result_from(out)
@@ -852,6 +854,8 @@ def run_precision(a, ws, rank, local):
             sk = max(res.phase_ms["sketch"], 1e-9)
             row = {"tol": tol, "b": b, "c": c,
                    "sketch": "FP64" if mode == 0 else f"tensor-core, {mode} digit(s)",
+                   "residual_products": "FP64" if planes == 0 else
+                                        f"tensor cores, {planes} BF16 planes",
                    "time_to_tolerance_ms": e0.elapsed_time(e1), "rank": res.rank,
                    "iterations": res.iterations, "rho": res.rho, "status": int(st),
                    "true_rel_error": err, "meets_tol": bool(st == cur.CUR_OK and err <= tol),
@@ -861,16 +865,23 @@ def run_precision(a, ws, rank, local):
             else:
                 row["sketch_hbm_gbs_two_passes"] = 2.0 * PREC_M * PREC_N * 4 / (sk * 1e-3) / 1e9
             forms.append(row)
-            log(f"precision: tol {tol:g} mode {mode}: {row['time_to_tolerance_ms']:.1f} ms, "
+            log(f"precision: tol {tol:g} mode {mode} planes {planes}: "
+                f"{row['time_to_tolerance_ms']:.1f} ms, "
                 f"rank {res.rank}, rho {res.rho:.2e}, true error {err:.2e}, status {st}")
     if rank == 0:
-        head = next(f for f in forms if f["tol"] == 1e-3 and f.get("sketch", "").startswith("tensor-core, 2"))
+        cands = [f for f in forms if f["tol"] == 1e-3 and f.get("meets_tol")
+                 and "sketch_hbm_gbs_two_passes" in f]
+        head = min(cands, key=lambda f: f["time_to_tolerance_ms"]) if cands else next(
+            f for f in forms if f["tol"] == 1e-3 and f.get("sketch", "").startswith("tensor-core, 2"))
         line = {"metric": "time-to-tolerance per CUR", "value": head["time_to_tolerance_ms"],
                 "unit": "ms", "n_gpus": ws, "steps": 1, "warmup": 1,
                 "ms_per_step": head["time_to_tolerance_ms"], "higher_is_better": False,
                 "scaling": "weak", "vs_baseline": None,
-                "dtype": "bf16 digit slices (2) in the sketch, f64 loop", "data": "synthetic",
-                "config": {"workload": precision_workload_name(), "headline": "tol 1e-3, 2 digits"},
+                "dtype": f"bf16 digit slices in the sketch ({head.get('sketch')}), residual products "
+                         f"{head.get('residual_products')}, f64 LUPP, core and norms",
+                "data": "synthetic",
+                "config": {"workload": precision_workload_name(),
+                           "headline": "tol 1e-3, the fastest form that meets it"},
                 "forms": forms,
                 "roofline": {"bound": "hbm", "achieved": head["sketch_hbm_gbs_two_passes"],
                              "peak": HBM_GBS, "unit": "GB/s",

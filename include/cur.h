@@ -85,6 +85,17 @@ typedef struct cur_opts {
   double delta;            /* see alpha                                         */
   int timing;              /* non-zero: record CUDA events around each phase
                               (cur_result_phase_ms); adds ~2 events per phase   */
+  int residual_planes;     /* 0: the residual products of the loop (S^row =
+                              A(:,J_k) - L Rt(:,J_k) and R_k = A(I_k,:) -
+                              L(I_k,:) Rt, Sec. 4.2) in FP64.  2 or 3: on the
+                              BF16 tensor cores, the factors L and Rt kept as
+                              2 or 3 BF16 planes (x = x_0 + x_1 (+ x_2) + e),
+                              plane pairs (a, b) with a + b < planes, FP32
+                              accumulation: relative error ~2^-16 / ~2^-24 of
+                              the product plus the FP32 sums; every other step
+                              stays FP64.  Needs block_size <= 128.  Extra
+                              device memory: planes * 2 (m + n) K bytes with
+                              K = max_rank rounded up to 64.                    */
 } cur_opts;
 
 /* Phases of one run, for cur_result_phase_ms (device time, milliseconds). */

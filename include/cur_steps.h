@@ -87,6 +87,17 @@ int cur_step_gather(cur_ctx *ctx, const double *X, int64_t ldx, int trans, const
                     const int64_t *cidx, int64_t rows, int64_t cols, int64_t rlim, int64_t clim,
                     double *out, int64_t ldo);
 
+/* The residual product of cur_opts.residual_planes on its own:
+ * D(n, i) -= sum_{k<K} P(i, k) Q(n, k) for n < N, i < M, with P (M x K, row
+ * pitch ldp) and Q (N x K, pitch ldq) FP64, split into `planes` (2 or 3) BF16
+ * planes and multiplied on the tensor cores with FP32 accumulation (the
+ * products S^row = A(:,J_k) - L Rt(:,J_k) and R_k = A(I_k,:) - L(I_k,:) Rt of
+ * Sec. 4.2 in this form).  D is N x M FP64 with pitch ldd.  All pointers are
+ * device memory owned by the caller.  1 <= N <= 128.  CUR_EINVAL for bad sizes
+ * or strides.  Synchronises the stream. */
+int cur_step_resid_tc(cur_ctx *ctx, const double *P, int64_t ldp, const double *Q, int64_t ldq,
+                      int64_t M, int64_t N, int64_t K, int planes, double *D, int64_t ldd);
+
 /* LUPP index selection (Sec. 3.2.1, 3.2.2): the candidates are the ncand
  * columns of X (nr x ncand, stride ldx, FP64; read only).  Step t picks the
  * eligible candidate with the largest |W[t, i]| of the running Schur

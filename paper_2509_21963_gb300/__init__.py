@@ -43,7 +43,8 @@ class CurError(RuntimeError):
 class cur_opts(ctypes.Structure):
     _fields_ = [("max_rank", ctypes.c_int64), ("omega", ctypes.c_void_p),
                 ("sketch_mode", ctypes.c_int), ("alpha", ctypes.c_double),
-                ("delta", ctypes.c_double), ("timing", ctypes.c_int)]
+                ("delta", ctypes.c_double), ("timing", ctypes.c_int),
+                ("residual_planes", ctypes.c_int)]
 
 
 class cur_batch_job(ctypes.Structure):
@@ -99,6 +100,7 @@ _SIGNATURES = {
     "cur_step_pinv": (_int, [_vp, _vp, _i64, _i64, _i64, _dbl, _vp, _vp]),
     "cur_step_gemm": (_int, [_vp, _i64, _i64, _i64, _dbl, _vp, _i64, _int, _vp, _i64, _int, _dbl,
                              _vp, _i64, _vp, _i64, _vp]),
+    "cur_step_resid_tc": (_int, [_vp, _vp, _i64, _vp, _i64, _i64, _i64, _i64, _int, _vp, _i64]),
     "cur_step_gather": (_int, [_vp, _vp, _i64, _int, _vp, _vp, _i64, _i64, _i64, _i64, _vp, _i64]),
     "cur_step_lupp_noalloc": (_int, [_int, _vp, _vp, _i64, _i64, _i64, _i64, _vp, _vp,
                                      ctypes.c_char_p, _sz]),
@@ -244,8 +246,10 @@ class Context:
         return (lib().cur_last_error(self.ptr) or b"").decode()
 
     @staticmethod
-    def _opts(max_rank=0, omega=None, alpha=0.0, delta=0.0, sketch_mode=CUR_SKETCH_F64, timing=False):
+    def _opts(max_rank=0, omega=None, alpha=0.0, delta=0.0, sketch_mode=CUR_SKETCH_F64, timing=False,
+              residual_planes=0):
         o = cur_opts()
+        o.residual_planes = residual_planes
         o.timing = 1 if timing else 0
         o.max_rank = max_rank
         o.omega = omega.data_ptr() if omega is not None else None
@@ -377,6 +381,16 @@ class Context:
                                              ldc, _vp(out.data_ptr()), out.stride(0),
                                              ctypes.byref(ss) if sumsq else None))
         return (out, ss.value) if sumsq else out
+
+    def resid_tc(self, P, Q, D, planes: int = 2):
+        """D(n, i) -= sum_k P(i, k) Q(n, k) on the tensor cores (FP64 CUDA tensors;
+        P: M x K, Q: N x K, D: N x M), in place; returns D."""
+        M, K = P.shape
+        N = Q.shape[0]
+        _check(self.ptr, lib().cur_step_resid_tc(self.ptr, _vp(P.data_ptr()), P.stride(0),
+                                                 _vp(Q.data_ptr()), Q.stride(0), M, N, K, int(planes),
+                                                 _vp(D.data_ptr()), D.stride(0)))
+        return D
 
     def gather(self, X, rows, cols, ridx=None, cidx=None, trans=False, out=None):
         """out[a, t] = X(ridx[a], cidx[t]) (X^T's entries when trans); indices

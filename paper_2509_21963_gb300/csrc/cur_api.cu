@@ -438,6 +438,10 @@ int validate(cur_ctx* ctx, const void* A, int64_t m, int64_t n, int64_t lda, int
       TRY(check_fx_form(ctx, A, lda, dtype));
     else if (o->sketch_mode != CUR_SKETCH_F64)
       TRY(check_precision_form(ctx, o->sketch_mode, A, lda, dtype, *c));
+    if (o->residual_planes != 0 && o->residual_planes != 2 && o->residual_planes != 3)
+      return fail(ctx, CUR_EINVAL, "residual_planes must be 0, 2 or 3");
+    if (o->residual_planes != 0 && b > 128)
+      return fail(ctx, CUR_EINVAL, "residual_planes needs block_size <= 128");
     if (o->alpha != 0.0) {
       if (!(o->alpha > 0.0 && o->alpha < 1.0) || !(o->delta >= 0.0))
         return fail(ctx, CUR_EINVAL, "alpha must be in (0,1) and delta >= 0");
@@ -546,6 +550,24 @@ int run_device(cur_ctx* ctx, const void* A, int64_t m, int64_t n, int64_t lda, i
   int64_t* Jd = bp<int64_t>(ctx, B_J);
   uint8_t* maskc = bp<uint8_t>(ctx, B_MASKC);
   uint8_t* maskr = bp<uint8_t>(ctx, B_MASKR);
+  // residual products on the tensor cores: L and Rt as BF16 planes, K-major
+  // (PLT: m rows, PRT: n rows, pitch kcap), and the gathered rows of the other
+  // factor (QP: b rows)
+  const int np = o ? o->residual_planes : 0;
+  const int64_t kcap = np ? resid_plane_pitch(max_rank) : 0;
+  __nv_bfloat16 *plt[3] = {nullptr, nullptr, nullptr}, *prt[3] = {nullptr, nullptr, nullptr},
+                *pq[3] = {nullptr, nullptr, nullptr};
+  if (np) {
+    if ((st = ensure(ctx, B_PLT, 2 * (size_t)np * (size_t)(m * kcap))) != CUR_OK) return fail_res(st);
+    if ((st = ensure(ctx, B_PRT, 2 * (size_t)np * (size_t)(n * kcap))) != CUR_OK) return fail_res(st);
+    if ((st = ensure(ctx, B_QP, 2 * (size_t)np * (size_t)(b * kcap))) != CUR_OK) return fail_res(st);
+    for (int q = 0; q < 3; ++q) {
+      const size_t qq = (size_t)(q < np ? q : 0);
+      plt[q] = bp<__nv_bfloat16>(ctx, B_PLT) + qq * (size_t)(m * kcap);
+      prt[q] = bp<__nv_bfloat16>(ctx, B_PRT) + qq * (size_t)(n * kcap);
+      pq[q] = bp<__nv_bfloat16>(ctx, B_QP) + qq * (size_t)(b * kcap);
+    }
+  }
 
   double rho = 1.0;
   int64_t r = 0;
@@ -571,6 +593,12 @@ int run_device(cur_ctx* ctx, const void* A, int64_t m, int64_t n, int64_t lda, i
                                 false, false, 0.0, nullptr, 0, LT + (size_t)(r - lt_bk) * m, m))) !=
           CUR_OK)
         return fail_res(st);
+      if (np) {   // its planes: PLT(i, r - lt_bk + t) from L^T(r - lt_bk + t, i)
+        if (cudaError_t e = launch_split_planes(env, LT + (size_t)(r - lt_bk) * m, m, 1, lt_bk, m,
+                                                plt, np, kcap, r - lt_bk); e != cudaSuccess)
+          return fail_res(fail(ctx, CUR_ECUDA, "split_planes: %s", cudaGetErrorString(e)));
+        ctx->launches += 1;
+      }
       lt_bk = 0;
     }
 
@@ -581,7 +609,14 @@ int run_device(cur_ctx* ctx, const void* A, int64_t m, int64_t n, int64_t lda, i
     tick(ctx, CUR_PHASE_ROW_RES);
     if ((st = gather(ctx, A, f32, lda, true, Jk, nullptr, bk, m, n, m, SrowT, m)) != CUR_OK)
       return fail_res(st);
-    if (r > 0) {
+    if (r > 0 && np) {   // S^row^T(t, i) -= sum_k L(i, k) Rt(k, J_k[t]) on the tensor cores
+      cudaError_t e = launch_gather_plane_rows(env, prt, np, kcap, n, Jk, (int)bk,
+                                               resid_plane_pitch(r), pq, kcap);
+      if (e == cudaSuccess)
+        e = launch_resid_tc(env, np, plt, kcap, m, pq, kcap, (int)bk, r, SrowT, m, &dstat(ctx)->err);
+      if (e != cudaSuccess) return fail_res(fail(ctx, CUR_ECUDA, "resid_tc: %s", cudaGetErrorString(e)));
+      ctx->launches += 2;
+    } else if (r > 0) {
       if ((st = ensure(ctx, B_G1, sizeof(double) * (size_t)(rcap * bk))) != CUR_OK) return fail_res(st);
       double* G1 = bp<double>(ctx, B_G1);
       if ((st = gather(ctx, Rt, false, n, false, nullptr, Jk, r, bk, r, n, G1, bk)) != CUR_OK)
@@ -602,13 +637,25 @@ int run_device(cur_ctx* ctx, const void* A, int64_t m, int64_t n, int64_t lda, i
     double* Rk = Rt + (size_t)r * n;
     if ((st = gather(ctx, A, f32, lda, false, Ik, nullptr, bk, n, m, n, Rk, n)) != CUR_OK)
       return fail_res(st);
-    if (r > 0) {
+    if (r > 0 && np) {   // R_k(t, j) -= sum_k Rt(k, j) L(I_k[t], k) on the tensor cores
+      cudaError_t e = launch_gather_plane_rows(env, plt, np, kcap, m, Ik, (int)bk,
+                                               resid_plane_pitch(r), pq, kcap);
+      if (e == cudaSuccess)
+        e = launch_resid_tc(env, np, prt, kcap, n, pq, kcap, (int)bk, r, Rk, n, &dstat(ctx)->err);
+      if (e != cudaSuccess) return fail_res(fail(ctx, CUR_ECUDA, "resid_tc: %s", cudaGetErrorString(e)));
+      ctx->launches += 2;
+    } else if (r > 0) {
       if ((st = ensure(ctx, B_G2, sizeof(double) * (size_t)(rcap * bk))) != CUR_OK) return fail_res(st);
       double* G2 = bp<double>(ctx, B_G2);
       if ((st = gather(ctx, LT, false, m, false, nullptr, Ik, r, bk, r, m, G2, bk)) != CUR_OK)
         return fail_res(st);
       if ((st = gemm(ctx, gargs(bk, n, r, -1.0, G2, bk, true, Rt, n, false, false, 1.0, Rk, n,
                                 Rk, n))) != CUR_OK) return fail_res(st);
+    }
+    if (np) {   // R_k's planes: PRT(j, r + t) from R_k(t, j)
+      if (cudaError_t e = launch_split_planes(env, Rk, n, 1, bk, n, prt, np, kcap, r); e != cudaSuccess)
+        return fail_res(fail(ctx, CUR_ECUDA, "split_planes: %s", cudaGetErrorString(e)));
+      ctx->launches += 1;
     }
     // N^+ by pivoted QR; rank threshold |I| 2^-52 |R_00(N_1)|
     if ((st = pinv_call(ctx, B_QRSMALL, Nd, bk, bk, bk, 2, (double)(r + bk),
@@ -889,6 +936,33 @@ int cur_step_gemm(cur_ctx* ctx, int64_t M, int64_t N, int64_t K, double alpha, c
     *sumsq_host = ctx->st_host->scalar[0];
   }
   return CUR_OK;
+}
+
+int cur_step_resid_tc(cur_ctx* ctx, const double* P, int64_t ldp, const double* Q, int64_t ldq,
+                      int64_t M, int64_t N, int64_t K, int planes, double* D, int64_t ldd) {
+  if (!ctx) return CUR_EINVAL;
+  if ((planes != 2 && planes != 3) || M < 0 || N < 1 || N > 128 || K < 0 || ldp < K || ldq < K ||
+      ldd < M || !D || (K > 0 && (!P || !Q)))
+    return fail(ctx, CUR_EINVAL, "bad arguments");
+  CK(cudaSetDevice(ctx->device));
+  TRY(ensure(ctx, B_STATUS, sizeof(DevStatus)));
+  CK(cudaMemsetAsync(ctx->buf[B_STATUS].p, 0, sizeof(DevStatus), ctx->stream));
+  if (M == 0 || K == 0) return CUR_OK;
+  LaunchEnv env = env_of(ctx);
+  const int64_t kp = resid_plane_pitch(K);
+  TRY(ensure(ctx, B_STEP_RP, 2 * (size_t)planes * (size_t)(M * kp)));
+  TRY(ensure(ctx, B_STEP_RQ, 2 * (size_t)planes * (size_t)(N * kp)));
+  __nv_bfloat16* pp[3];
+  __nv_bfloat16* qp[3];
+  for (int p = 0; p < 3; ++p) {
+    pp[p] = bp<__nv_bfloat16>(ctx, B_STEP_RP) + (size_t)(p < planes ? p : 0) * (size_t)(M * kp);
+    qp[p] = bp<__nv_bfloat16>(ctx, B_STEP_RQ) + (size_t)(p < planes ? p : 0) * (size_t)(N * kp);
+  }
+  CK(launch_split_planes(env, P, 1, ldp, K, M, pp, planes, kp, 0));
+  CK(launch_split_planes(env, Q, 1, ldq, K, N, qp, planes, kp, 0));
+  CK(launch_resid_tc(env, planes, pp, kp, M, qp, kp, (int)N, K, D, ldd, &dstat(ctx)->err));
+  ctx->launches += 3;
+  return read_status(ctx);
 }
 
 int cur_step_gather(cur_ctx* ctx, const double* X, int64_t ldx, int trans, const int64_t* ridx,

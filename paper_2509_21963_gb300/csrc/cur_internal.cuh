@@ -3,6 +3,8 @@
 // launch functions; the orchestrator (cur_api.cu) chains them on one stream.
 #pragma once
 
+#include <cuda_bf16.h>
+
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -184,6 +186,21 @@ cudaError_t launch_gather2d(const LaunchEnv& env, const void* X, bool x_is_f32, 
                             bool trans, const int64_t* ridx, const int64_t* cidx,
                             int64_t rows, int64_t cols, int64_t rlim, int64_t clim,
                             double* out, int64_t ldo);
+
+// ---- resid_tc.cu ------------------------------------------------------------
+// Residual products on the tensor cores: D(n, i) -= sum_{k<K} P(i, k) Q(n, k)
+// with P (M x K) and Q (N x K, N <= 128) held as np = 2 or 3 BF16 planes,
+// K-major with pitches ldp, ldq (multiples of 64).
+int64_t resid_plane_pitch(int64_t kmax);
+cudaError_t launch_split_planes(const LaunchEnv& env, const double* src, int64_t st, int64_t si,
+                                int64_t nt, int64_t M, __nv_bfloat16* const* planes, int np,
+                                int64_t ldp, int64_t k0);
+cudaError_t launch_gather_plane_rows(const LaunchEnv& env, __nv_bfloat16* const* planes, int np,
+                                     int64_t ldp, int64_t prows, const int64_t* idx, int N,
+                                     int64_t kp, __nv_bfloat16* const* dst, int64_t ldq);
+cudaError_t launch_resid_tc(const LaunchEnv& env, int np, __nv_bfloat16* const* P, int64_t ldp,
+                            int64_t M, __nv_bfloat16* const* Q, int64_t ldq, int N, int64_t K,
+                            double* D, int64_t ldd, int* err);
 
 // ---- lupp.cu --------------------------------------------------------------
 struct LuppWork {
