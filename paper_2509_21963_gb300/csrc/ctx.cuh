@@ -18,7 +18,7 @@ enum BufId {
   B_OMEGA, B_S, B_LUPPW, B_SROWT, B_G1, B_G2, B_N, B_NP, B_SJK, B_T1, B_PARTS, B_SPLITK,
   B_LT, B_RT, B_I, B_J, B_MASKC, B_MASKR, B_QRSMALL, B_QRBIG, B_CORE, B_STATUS, B_AHOST,
   B_STEP_QR, B_STEP_LUPP, B_STEP_PARTS, B_TC, B_STEP_TC, B_TEAMCORE, B_FX, B_STEP_FX,
-  B_PLT, B_PRT, B_QP, B_STEP_RP, B_STEP_RQ, B_COUNT
+  B_PLT, B_PRT, B_QP, B_STEP_RP, B_STEP_RQ, B_PS, B_PNP, B_PRK, B_PT1, B_COUNT
 };
 
 struct cur_ctx {

@@ -561,6 +561,11 @@ int run_device(cur_ctx* ctx, const void* A, int64_t m, int64_t n, int64_t lda, i
     if ((st = ensure(ctx, B_PLT, 2 * (size_t)np * (size_t)(m * kcap))) != CUR_OK) return fail_res(st);
     if ((st = ensure(ctx, B_PRT, 2 * (size_t)np * (size_t)(n * kcap))) != CUR_OK) return fail_res(st);
     if ((st = ensure(ctx, B_QP, 2 * (size_t)np * (size_t)(b * kcap))) != CUR_OK) return fail_res(st);
+    const int64_t kb = resid_plane_pitch(b);   // the planes of S^row and -N^+ for L_k
+    if ((st = ensure(ctx, B_PS, 2 * (size_t)np * (size_t)(m * kb))) != CUR_OK) return fail_res(st);
+    if ((st = ensure(ctx, B_PNP, 2 * (size_t)np * (size_t)(b * kb))) != CUR_OK) return fail_res(st);
+    if ((st = ensure(ctx, B_PRK, 2 * (size_t)np * (size_t)(n * kb))) != CUR_OK) return fail_res(st);
+    if ((st = ensure(ctx, B_PT1, 2 * (size_t)np * (size_t)(c * kb))) != CUR_OK) return fail_res(st);
     for (int q = 0; q < 3; ++q) {
       const size_t qq = (size_t)(q < np ? q : 0);
       plt[q] = bp<__nv_bfloat16>(ctx, B_PLT) + qq * (size_t)(m * kcap);
@@ -589,10 +594,29 @@ int run_device(cur_ctx* ctx, const void* A, int64_t m, int64_t n, int64_t lda, i
     if (lt_bk > 0) {   // L_{k-1}^T = N^+^T S^row^T of the last iteration: needed only now that
                        // the loop goes on (its S^row and N^+ are still in place)
       tick(ctx, CUR_PHASE_FACTORS);
-      if ((st = gemm(ctx, gargs(lt_bk, m, lt_bk, 1.0, bp<double>(ctx, B_NP), lt_bk, true, SrowT, m,
-                                false, false, 0.0, nullptr, 0, LT + (size_t)(r - lt_bk) * m, m))) !=
-          CUR_OK)
+      double* LTk = LT + (size_t)(r - lt_bk) * m;
+      if (np) {   // on the tensor cores: L^T_k(t, i) = 0 - sum_k' S^row(i, k') (-N^+(k', t))
+        const int64_t kb = resid_plane_pitch(lt_bk);
+        __nv_bfloat16 *ps[3], *pn[3];
+        for (int q = 0; q < 3; ++q) {
+          const size_t qq = (size_t)(q < np ? q : 0);
+          ps[q] = bp<__nv_bfloat16>(ctx, B_PS) + qq * (size_t)(m * kb);
+          pn[q] = bp<__nv_bfloat16>(ctx, B_PNP) + qq * (size_t)(lt_bk * kb);
+        }
+        cudaError_t e = launch_split_planes(env, SrowT, m, 1, lt_bk, m, ps, np, kb, 0);
+        if (e == cudaSuccess)
+          e = launch_split_planes(env, bp<double>(ctx, B_NP), lt_bk, 1, lt_bk, lt_bk, pn, np, kb, 0,
+                                  true);
+        if (e == cudaSuccess)
+          e = cudaMemsetAsync(LTk, 0, sizeof(double) * (size_t)(lt_bk * m), s);
+        if (e == cudaSuccess)
+          e = launch_resid_tc(env, np, ps, kb, m, pn, kb, (int)lt_bk, lt_bk, LTk, m, &dstat(ctx)->err);
+        if (e != cudaSuccess) return fail_res(fail(ctx, CUR_ECUDA, "L_k: %s", cudaGetErrorString(e)));
+        ctx->launches += 3;
+      } else if ((st = gemm(ctx, gargs(lt_bk, m, lt_bk, 1.0, bp<double>(ctx, B_NP), lt_bk, true, SrowT,
+                                       m, false, false, 0.0, nullptr, 0, LTk, m))) != CUR_OK) {
         return fail_res(st);
+      }
       if (np) {   // its planes: PLT(i, r - lt_bk + t) from L^T(r - lt_bk + t, i)
         if (cudaError_t e = launch_split_planes(env, LT + (size_t)(r - lt_bk) * m, m, 1, lt_bk, m,
                                                 plt, np, kcap, r - lt_bk); e != cudaSuccess)
@@ -671,7 +695,27 @@ int run_device(cur_ctx* ctx, const void* A, int64_t m, int64_t n, int64_t lda, i
       return fail_res(st);
     if ((st = gemm(ctx, gargs(c, bk, bk, 1.0, SJk, bk, false, Np, bk, false, false, 0.0, nullptr, 0,
                               T1, bk))) != CUR_OK) return fail_res(st);
-    {
+    if (np && c <= 128) {   // S^col(i, j) -= sum_t T1(i, t) R_k(t, j) on the tensor cores,
+                            // then ||S^col||_F^2 in FP64
+      const int64_t kb = resid_plane_pitch(bk);
+      __nv_bfloat16 *pr[3], *pt[3];
+      for (int q = 0; q < 3; ++q) {
+        const size_t qq = (size_t)(q < np ? q : 0);
+        pr[q] = bp<__nv_bfloat16>(ctx, B_PRK) + qq * (size_t)(n * kb);
+        pt[q] = bp<__nv_bfloat16>(ctx, B_PT1) + qq * (size_t)(c * kb);
+      }
+      const int64_t nparts = resid_sumsq_parts();
+      if ((st = ensure(ctx, B_PARTS, sizeof(double) * (size_t)nparts)) != CUR_OK) return fail_res(st);
+      cudaError_t e = launch_split_planes(env, Rk, n, 1, bk, n, pr, np, kb, 0);
+      if (e == cudaSuccess) e = launch_split_planes(env, T1, 1, bk, bk, c, pt, np, kb, 0);
+      if (e == cudaSuccess)
+        e = launch_resid_tc(env, np, pr, kb, n, pt, kb, (int)c, bk, S, n, &dstat(ctx)->err);
+      if (e == cudaSuccess) e = launch_sumsq_parts(env, S, c, n, n, bp<double>(ctx, B_PARTS));
+      if (e != cudaSuccess) return fail_res(fail(ctx, CUR_ECUDA, "S^col: %s", cudaGetErrorString(e)));
+      ctx->launches += 4;
+      if ((st = sum_parts(ctx, bp<double>(ctx, B_PARTS), nparts, &dstat(ctx)->scalar[1])) != CUR_OK)
+        return fail_res(st);
+    } else {
       GemmArgs g = gargs(c, n, bk, -1.0, T1, bk, false, Rk, n, false, false, 1.0, S, n, S, n);
       int64_t np = gemm_num_sumsq_parts(g);
       if ((st = ensure(ctx, B_PARTS, sizeof(double) * (size_t)np)) != CUR_OK) return fail_res(st);

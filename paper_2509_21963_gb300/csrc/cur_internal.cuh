@@ -192,9 +192,14 @@ cudaError_t launch_gather2d(const LaunchEnv& env, const void* X, bool x_is_f32, 
 // with P (M x K) and Q (N x K, N <= 128) held as np = 2 or 3 BF16 planes,
 // K-major with pitches ldp, ldq (multiples of 64).
 int64_t resid_plane_pitch(int64_t kmax);
+// ||X||_F^2 of a rows x cols FP64 matrix as resid_sumsq_parts() per-CTA partial
+// sums (fixed order; reduce with launch_sum_parts).
+int64_t resid_sumsq_parts();
+cudaError_t launch_sumsq_parts(const LaunchEnv& env, const double* X, int64_t rows, int64_t cols,
+                               int64_t ld, double* parts);
 cudaError_t launch_split_planes(const LaunchEnv& env, const double* src, int64_t st, int64_t si,
                                 int64_t nt, int64_t M, __nv_bfloat16* const* planes, int np,
-                                int64_t ldp, int64_t k0);
+                                int64_t ldp, int64_t k0, bool negate = false);
 cudaError_t launch_gather_plane_rows(const LaunchEnv& env, __nv_bfloat16* const* planes, int np,
                                      int64_t ldp, int64_t prows, const int64_t* idx, int N,
                                      int64_t kp, __nv_bfloat16* const* dst, int64_t ldq);

@@ -177,11 +177,12 @@ __global__ void __launch_bounds__(kRThreads, 1)
 // nearest), each from the FP64 remainder of the previous ones.
 __global__ void split_planes_kernel(const double* __restrict__ src, int64_t st, int64_t si, int64_t nt,
                                     int64_t M, __nv_bfloat16* p0, __nv_bfloat16* p1,
-                                    __nv_bfloat16* p2, int64_t ldp, int64_t k0) {
+                                    __nv_bfloat16* p2, int64_t ldp, int64_t k0, bool negate) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= M) return;
   for (int64_t t = 0; t < nt; ++t) {
     double x = src[t * st + i * si];
+    if (negate) x = -x;
     const __nv_bfloat16 h0 = __double2bfloat16(x);
     x -= (double)__bfloat162float(h0);
     const __nv_bfloat16 h1 = __double2bfloat16(x);
@@ -216,6 +217,29 @@ __global__ void gather_plane_rows_kernel(const __nv_bfloat16* __restrict__ p0,
   }
 }
 
+// Per-CTA sums of squares of X (rows x cols, pitch ld), in a fixed order:
+// parts[blockIdx.x] (summed by launch_sum_parts).
+__global__ void sumsq_parts_kernel(const double* __restrict__ X, int64_t rows, int64_t cols,
+                                   int64_t ld, double* parts) {
+  __shared__ double red[8];
+  double s = 0.0;
+  const int64_t total = rows * cols;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t rr = e / cols, cc = e - rr * cols;
+    const double x = X[rr * ld + cc];
+    s = fma(x, x, s);
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    parts[blockIdx.x] = t;
+  }
+}
+
 bool make_plane_map(CUtensorMap* map, const __nv_bfloat16* base, int64_t K, int64_t rows,
                     int64_t ld, int box_rows) {
   EncodeTiledFn enc = encode_fn();
@@ -233,12 +257,21 @@ bool make_plane_map(CUtensorMap* map, const __nv_bfloat16* base, int64_t K, int6
 
 int64_t resid_plane_pitch(int64_t kmax) { return (kmax + 63) / 64 * 64; }
 
+constexpr int kSumsqBlocks = 304;
+int64_t resid_sumsq_parts() { return kSumsqBlocks; }
+
+cudaError_t launch_sumsq_parts(const LaunchEnv& env, const double* X, int64_t rows, int64_t cols,
+                               int64_t ld, double* parts) {
+  sumsq_parts_kernel<<<kSumsqBlocks, 256, 0, env.stream>>>(X, rows, cols, ld, parts);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_split_planes(const LaunchEnv& env, const double* src, int64_t st, int64_t si,
                                 int64_t nt, int64_t M, __nv_bfloat16* const* planes, int np,
-                                int64_t ldp, int64_t k0) {
+                                int64_t ldp, int64_t k0, bool negate) {
   if (nt <= 0 || M <= 0) return cudaSuccess;
   split_planes_kernel<<<(unsigned)((M + 255) / 256), 256, 0, env.stream>>>(
-      src, st, si, nt, M, planes[0], planes[1], np > 2 ? planes[2] : nullptr, ldp, k0);
+      src, st, si, nt, M, planes[0], planes[1], np > 2 ? planes[2] : nullptr, ldp, k0, negate);
   return cudaGetLastError();
 }
 
