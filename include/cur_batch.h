@@ -83,6 +83,15 @@ int cur_batch_set_classes(cur_batch *batch, int team, int team_big, int nbig, in
  * when there is one class). */
 int cur_batch_get_classes(const cur_batch *batch, int *team_big, int *nbig, int64_t *big_cut);
 
+/* Tile of the residual products inside the batch kernel (the Lemma 1
+ * products S^row = A(:,J_k) - L Rt(:,J_k) and the factor/sketch updates of
+ * Sec. 4.2): each thread forms tile_n (4 or 8) outputs per pass over the
+ * staged inner dimension.  The same arithmetic either way (each output is one
+ * FP64 dot product in the same order); only registers and shared-memory
+ * reuse differ.  Invalidates the graph.  CUR_EINVAL for other values. */
+int cur_batch_set_tile(cur_batch *batch, int tile_n);
+int cur_batch_get_tile(const cur_batch *batch, int *tile_n);
+
 /* Current schedule: team size, CTAs launched, teams, whether launches replay a
  * captured graph (1) or are direct cooperative launches (0). */
 int cur_batch_get_schedule(const cur_batch *batch, int *team, int *grid, int *teams,
@@ -94,7 +103,8 @@ int cur_batch_get_schedule(const cur_batch *batch, int *team, int *grid, int *te
  * is the candidate's time.  After the single-class candidates it tries, on
  * top of the fastest of them, two-class schedules (cur_batch_set_classes):
  * 1 or 2 big teams of 8 or 16 CTAs (larger than the small teams) serving the
- * largest jobs up to the big teams' share of the CTAs in estimated work.
+ * largest jobs up to the big teams' share of the CTAs in estimated work,
+ * then the other product tile (cur_batch_set_tile) on the fastest schedule.
  * The fastest schedule is kept; *best_team receives its small-team size.  Every trial is
  * a complete, valid run, so the results of the last trial are available
  * afterwards.  *best_team and *best_ms (optional) receive the choice and its

@@ -108,6 +108,8 @@ _SIGNATURES = {
     "cur_batch_free": (None, [_vp]),
     "cur_batch_set_team": (_int, [_vp, _int]),
     "cur_batch_set_classes": (_int, [_vp, _int, _int, _int, _i64]),
+    "cur_batch_set_tile": (_int, [_vp, _int]),
+    "cur_batch_get_tile": (_int, [_vp, ctypes.POINTER(_int)]),
     "cur_batch_get_classes": (_int, [_vp, ctypes.POINTER(_int), ctypes.POINTER(_int),
                                      ctypes.POINTER(_i64)]),
     "cur_batch_get_schedule": (_int, [_vp, ctypes.POINTER(_int), ctypes.POINTER(_int),
@@ -489,6 +491,9 @@ class Batch:
         _check(self.ctx.ptr, lib().cur_batch_set_classes(self.ptr, int(team), int(team_big),
                                                          int(nbig), int(big_cut)))
 
+    def set_tile(self, tile_n: int):
+        _check(self.ctx.ptr, lib().cur_batch_set_tile(self.ptr, int(tile_n)))
+
     def tune(self, candidates=None):
         best, ms = _int(), _dbl()
         if candidates is None:
@@ -507,8 +512,10 @@ class Batch:
         tb, nb, cut = _int(), _int(), _i64()
         _check(self.ctx.ptr, lib().cur_batch_get_classes(self.ptr, ctypes.byref(tb), ctypes.byref(nb),
                                                          ctypes.byref(cut)))
+        tile = _int()
+        _check(self.ctx.ptr, lib().cur_batch_get_tile(self.ptr, ctypes.byref(tile)))
         return {"team": t.value, "grid": g.value, "teams": n.value, "graph": bool(gr.value),
-                "team_big": tb.value, "nbig": nb.value, "big_cut": cut.value}
+                "team_big": tb.value, "nbig": nb.value, "big_cut": cut.value, "tile_n": tile.value}
 
     BATCH_PHASES = ("sketch", "lupp_col", "row_res", "lupp_row", "updates", "core_factor",
                     "core_solve", "jobs")

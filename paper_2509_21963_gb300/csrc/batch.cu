@@ -35,7 +35,8 @@
 namespace cur {
 namespace {
 
-constexpr int kTB = 8;     // outputs per thread and pass in the residual products
+constexpr int kTB = 8;     // outputs per thread and pass in the residual products (the
+                           // serving kernel's; the batch kernel takes 4 or 8, tuned per batch)
 constexpr int kLch = 128;  // rows of L^T / Rt staged per shared-memory chunk
 constexpr int kIch = 256;  // rows of A per sketch staging chunk
 constexpr int kMaxWarps = 32;
@@ -614,10 +615,10 @@ __device__ void team_qr_solve_best(const Team& tm, const QrWs& w, int64_t p, int
 // ---------------------------------------------------------------------------
 // One job.
 // ---------------------------------------------------------------------------
-template <typename AT>
+template <typename AT, int TB>
 __device__ void run_job(const BatchParams& P, const Team& tm, const BatchJobDev& jb,
                         BatchOutDev* out, const TeamWs& tw, const CtaWs& cw) {
-  __shared__ double s_stage[kLch * kTB > 8 * kIch ? kLch * kTB : 8 * kIch];
+  __shared__ double s_stage[kLch * TB > 8 * kIch ? kLch * TB : 8 * kIch];
   __shared__ double s_prow[kBatchMaxB > kBatchMaxC ? kBatchMaxB : kBatchMaxC];
   __shared__ int64_t s_Jk[kBatchMaxB], s_Ik[kBatchMaxB];
   const int tid = threadIdx.x, NT = blockDim.x;
@@ -717,16 +718,16 @@ __device__ void run_job(const BatchParams& P, const Team& tm, const BatchJobDev&
     // row residual: S^row = A(:,J_k) - L Rt(:,J_k), rows over the team
     for (int64_t i0 = (int64_t)tm.rank * NT; i0 < m; i0 += tm.gsize()) {
       const int64_t i = i0 + tid;
-      for (int t0 = 0; t0 < bk; t0 += kTB) {
-        const int nt = min(kTB, bk - t0);
-        double acc[kTB];
+      for (int t0 = 0; t0 < bk; t0 += TB) {
+        const int nt = min(TB, bk - t0);
+        double acc[TB];
 #pragma unroll
-        for (int t = 0; t < kTB; ++t) acc[t] = 0.0;
+        for (int t = 0; t < TB; ++t) acc[t] = 0.0;
         for (int64_t l0 = 0; l0 < r; l0 += kLch) {
           const int nl = (int)min((int64_t)kLch, r - l0);
           __syncthreads();
-          for (int e = tid; e < kLch * kTB; e += NT) {
-            const int ll = e / kTB, t = e - ll * kTB;
+          for (int e = tid; e < kLch * TB; e += NT) {
+            const int ll = e / TB, t = e - ll * TB;
             s_stage[e] = (ll < nl && t < nt) ? __ldcg(Rt + (l0 + ll) * n + s_Jk[t0 + t]) : 0.0;
           }
           __syncthreads();
@@ -734,7 +735,7 @@ __device__ void run_job(const BatchParams& P, const Team& tm, const BatchJobDev&
             for (int ll = 0; ll < nl; ++ll) {
               const double a = __ldcg(Lt + (l0 + ll) * m + i);
 #pragma unroll
-              for (int t = 0; t < kTB; ++t) acc[t] += a * s_stage[ll * kTB + t];
+              for (int t = 0; t < TB; ++t) acc[t] += a * s_stage[ll * TB + t];
             }
           }
         }
@@ -789,16 +790,16 @@ __device__ void run_job(const BatchParams& P, const Team& tm, const BatchJobDev&
     double ssum = 0.0;
     for (int64_t j0 = (int64_t)tm.rank * NT; j0 < n; j0 += tm.gsize()) {
       const int64_t j = j0 + tid;
-      for (int a0 = 0; a0 < bk; a0 += kTB) {
-        const int na = min(kTB, bk - a0);
-        double acc[kTB];
+      for (int a0 = 0; a0 < bk; a0 += TB) {
+        const int na = min(TB, bk - a0);
+        double acc[TB];
 #pragma unroll
-        for (int a = 0; a < kTB; ++a) acc[a] = 0.0;
+        for (int a = 0; a < TB; ++a) acc[a] = 0.0;
         for (int64_t l0 = 0; l0 < r; l0 += kLch) {
           const int nl = (int)min((int64_t)kLch, r - l0);
           __syncthreads();
-          for (int e = tid; e < kLch * kTB; e += NT) {
-            const int ll = e / kTB, a = e - ll * kTB;
+          for (int e = tid; e < kLch * TB; e += NT) {
+            const int ll = e / TB, a = e - ll * TB;
             s_stage[e] = (ll < nl && a < na) ? __ldcg(Lt + (l0 + ll) * m + s_Ik[a0 + a]) : 0.0;
           }
           __syncthreads();
@@ -806,7 +807,7 @@ __device__ void run_job(const BatchParams& P, const Team& tm, const BatchJobDev&
             for (int ll = 0; ll < nl; ++ll) {
               const double rv = __ldcg(Rt + (l0 + ll) * n + j);
 #pragma unroll
-              for (int a = 0; a < kTB; ++a) acc[a] += s_stage[ll * kTB + a] * rv;
+              for (int a = 0; a < TB; ++a) acc[a] += s_stage[ll * TB + a] * rv;
             }
           }
         }
@@ -872,7 +873,7 @@ __device__ void run_job(const BatchParams& P, const Team& tm, const BatchJobDev&
 // estimated work), then help with the rest; the other teams have `team` CTAs
 // and take positions [big_cut, njobs) only.  A job's team size is thus set by
 // its class, and the largest jobs no longer hold a small team to the end.
-template <typename AT>
+template <typename AT, int TB>
 __global__ void __launch_bounds__(256, 1) batch_kernel(BatchParams P) {
   const int bigctas = P.nbig * P.team_big;
   const bool big = (int)blockIdx.x < bigctas;
@@ -902,7 +903,7 @@ __global__ void __launch_bounds__(256, 1) batch_kernel(BatchParams P) {
     if (pos >= P.njobs) return;
     const int jid = P.order[pos];
     BatchJobDev jb = P.jobs[jid];
-    run_job<AT>(P, tm, jb, P.out + jid, tw, cw);
+    run_job<AT, TB>(P, tm, jb, P.out + jid, tw, cw);
     if (*((volatile int*)&P.st->err) != 0) return;
   }
 }
@@ -943,7 +944,7 @@ __global__ void __launch_bounds__(256, 1) serve_kernel(BatchParams P) {
   const size_t tb = (L.team_bytes + 255) & ~(size_t)255, cb = (L.cta_bytes + 255) & ~(size_t)255;
   TeamWs tw = carve_team(jb.ws, d, tm.T);
   CtaWs cw = carve_cta(jb.ws + tb + (size_t)tm.rank * cb, d);
-  run_job<AT>(P, tm, jb, P.out + jid, tw, cw);
+  run_job<AT, kTB>(P, tm, jb, P.out + jid, tw, cw);
 }
 
 }  // namespace
@@ -951,20 +952,28 @@ __global__ void __launch_bounds__(256, 1) serve_kernel(BatchParams P) {
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
-template <typename AT>
-static int max_ctas_t(const LaunchEnv& env, int threads, size_t dyn_smem) {
-  if (cudaFuncSetAttribute(batch_kernel<AT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+template <typename AT, int TB>
+static int max_ctas_tb(const LaunchEnv& env, int threads, size_t dyn_smem) {
+  if (cudaFuncSetAttribute(batch_kernel<AT, TB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)kBatchMaxPanelBytes) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<AT>, threads,
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<AT, TB>, threads,
                                                     dyn_smem) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
   return per_sm * env.num_sms;
+}
+
+// CTAs every tile variant of the batch kernel can keep co-resident.
+template <typename AT>
+static int max_ctas_t(const LaunchEnv& env, int threads, size_t dyn_smem) {
+  const int a = max_ctas_tb<AT, 4>(env, threads, dyn_smem);
+  const int b = max_ctas_tb<AT, 8>(env, threads, dyn_smem);
+  return a < b ? a : b;
 }
 
 int batch_max_ctas(const LaunchEnv& env, int threads, bool a_f32, size_t dyn_smem) {
@@ -989,8 +998,11 @@ cudaError_t launch_batch(const LaunchEnv& env, const BatchParams& P, int grid, i
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  if (a_f32) return cudaLaunchKernelEx(&cfg, batch_kernel<float>, P);
-  return cudaLaunchKernelEx(&cfg, batch_kernel<double>, P);
+  if (P.tile_n == 4)
+    return a_f32 ? cudaLaunchKernelEx(&cfg, batch_kernel<float, 4>, P)
+                 : cudaLaunchKernelEx(&cfg, batch_kernel<double, 4>, P);
+  return a_f32 ? cudaLaunchKernelEx(&cfg, batch_kernel<float, 8>, P)
+               : cudaLaunchKernelEx(&cfg, batch_kernel<double, 8>, P);
 }
 
 }  // namespace cur

@@ -192,6 +192,7 @@ struct BatchParams {
   int nbig;                    // big teams: CTAs [0, nbig * team_big)
   long long big_cut;           // queue positions [0, big_cut): the big jobs, served by big teams
   unsigned long long* next_small;   // head of the queue positions [big_cut, njobs)
+  int tile_n;                  // outputs per thread and pass of the residual products (4 or 8)
   unsigned long long* prof;    // kBatchPhases cycle sums of the team leaders (zeroed per launch)
   size_t panel_bytes;          // dynamic shared memory for the core solve panel (0: none)
 };

@@ -35,6 +35,7 @@ struct cur_batch {
   // schedule
   int threads = 256;
   int team = 1;
+  int tile_n = 8;            // outputs per thread and pass of the residual products (4 or 8)
   int team_big = 0;          // 0: one team class
   int nbig = 0;
   int64_t big_cut = 0;
@@ -158,6 +159,7 @@ int plan_schedule(cur_batch* b, int team, int team_big = 0, int nbig = 0, int64_
   b->big_cut = big_cut;
   b->grid = grid;
   b->P.team = team;
+  b->P.tile_n = b->tile_n;
   b->P.team_big = team_big;
   b->P.nbig = nbig;
   b->P.big_cut = big_cut;
@@ -369,6 +371,23 @@ int cur_batch_set_classes(cur_batch* b, int team, int team_big, int nbig, int64_
   return plan_schedule(b, team, team_big, nbig, big_cut);
 }
 
+int cur_batch_set_tile(cur_batch* b, int tile_n) {
+  if (!b) return CUR_EINVAL;
+  if (tile_n != 4 && tile_n != 8) return bfail(b->ctx, CUR_EINVAL, "tile_n must be 4 or 8");
+  if (tile_n != b->tile_n) {
+    b->tile_n = tile_n;
+    b->P.tile_n = tile_n;
+    drop_graph(b);
+  }
+  return CUR_OK;
+}
+
+int cur_batch_get_tile(const cur_batch* b, int* tile_n) {
+  if (!b || !tile_n) return CUR_EINVAL;
+  *tile_n = b->tile_n;
+  return CUR_OK;
+}
+
 int cur_batch_get_classes(const cur_batch* b, int* team_big, int* nbig, int64_t* big_cut) {
   if (!b) return CUR_EINVAL;
   if (team_big) *team_big = b->team_big;
@@ -450,12 +469,13 @@ int cur_batch_tune(cur_batch* b, const int* candidates, int ncand, int* best_tea
   // best of those, big-team classes (team_big in {8, 16} above it, 1 or 2 big
   // teams) whose queue share is the big teams' share of the CTAs, counted in
   // estimated work from the largest job down.
-  struct Cand { int team, team_big, nbig; int64_t cut; };
+  struct Cand { int team, team_big, nbig; int64_t cut; int tile; };
   std::vector<Cand> cands;
   for (int k = 0; k < ncand; ++k)
     if (candidates[k] >= 1 && candidates[k] <= 32 && candidates[k] <= max_ctas)
-      cands.push_back({candidates[k], 0, 0, 0});
+      cands.push_back({candidates[k], 0, 0, 0, 8});
   const size_t nsingle = cands.size();
+  size_t tile_from = (size_t)-1;   // index after the last schedule candidate (set below)
   double wsum = 0.0;
   for (double x : b->work) wsum += x;
   int best = -1;
@@ -463,6 +483,7 @@ int cur_batch_tune(cur_batch* b, const int* candidates, int ncand, int* best_tea
   int s = CUR_OK;
   for (size_t k = 0; k < cands.size() && s == CUR_OK; ++k) {
     const Cand cd = cands[k];
+    b->tile_n = cd.tile;
     s = plan_schedule(b, cd.team, cd.team_big, cd.nbig, cd.cut);
     if (s != CUR_OK) break;
     // capture the candidate's graph before timing (host-side work that would
@@ -484,18 +505,24 @@ int cur_batch_tune(cur_batch* b, const int* candidates, int ncand, int* best_tea
     }
     if (s != CUR_OK) break;
     if (best < 0 || cand < best_t) { best = (int)k; best_t = cand; }
-    if (k + 1 == nsingle && best >= 0 && b->njobs > 1) {   // the big-team classes
+    if (k + 1 == nsingle && best >= 0) {   // the big-team classes
       const int ts = cands[(size_t)best].team;
       for (int tbig : {8, 16})
         for (int nb : {1, 2}) {
-          if (tbig <= ts || nb * tbig + ts > max_ctas) continue;
+          if (b->njobs < 2 || tbig <= ts || nb * tbig + ts > max_ctas) continue;
           const double share = wsum * (double)(nb * tbig) / (double)max_ctas;
           int64_t cut = 0;
           double acc = 0.0;
           while (cut < b->njobs && (cut == 0 || acc < share)) acc += b->work[(size_t)cut++];
           if (cut >= b->njobs) cut = b->njobs - 1;
-          cands.push_back({ts, tbig, nb, cut});
+          cands.push_back({ts, tbig, nb, cut, 8});
         }
+      tile_from = cands.size();
+    }
+    if (k + 1 == tile_from && best >= 0) {   // the other product tile on the best schedule
+      Cand c4 = cands[(size_t)best];
+      c4.tile = 4;
+      cands.push_back(c4);
     }
   }
   cudaEventDestroy(e0);
@@ -504,6 +531,7 @@ int cur_batch_tune(cur_batch* b, const int* candidates, int ncand, int* best_tea
   if (best < 0) return bfail(ctx, CUR_EINVAL, "no candidate team size fits this GPU");
   const Cand bc = cands[(size_t)best];
   if (best + 1 != (int)cands.size()) {
+    b->tile_n = bc.tile;
     s = plan_schedule(b, bc.team, bc.team_big, bc.nbig, bc.cut);
     if (s != CUR_OK) return s;
     s = cur_batch_run(b);  // results of the chosen schedule

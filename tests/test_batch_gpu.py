@@ -72,6 +72,27 @@ def test_batch_parity(ctx, dtype, team):
     B.close()
 
 
+def test_batch_tile_4_equals_tile_8(ctx):
+    """The product tile changes registers and reuse, not the arithmetic: the
+    batch gives the same I, J, U and rho bit for bit with tiles of 4 and 8."""
+    import paper_2509_21963_gb300 as cur
+    specs, mats, dev = _jobs(12, seed=19, lo=30, hi=220, dtype=torch.float64)
+    B = cur.Batch(ctx, dev, 1e-4, 8, 8, seed=[s["seed"] for s in specs])
+    B.set_team(2)
+    B.run()
+    r8 = [B.result(j) for j in range(len(specs))]
+    B.set_tile(4)
+    assert B.schedule()["tile_n"] == 4
+    B.run()
+    for j in range(len(specs)):
+        a, b = r8[j], B.result(j)
+        assert np.array_equal(a.I, b.I) and np.array_equal(a.J, b.J)
+        assert np.array_equal(a.U, b.U) and a.rho == b.rho
+    with pytest.raises(cur.CurError):
+        B.set_tile(6)
+    B.close()
+
+
 @pytest.mark.parametrize("team,team_big,nbig,cut", [(1, 8, 1, 3), (2, 16, 2, 6), (4, 8, 2, 23)])
 def test_batch_team_classes(ctx, team, team_big, nbig, cut):
     """Two team classes in one launch (big teams take the `cut` largest jobs
