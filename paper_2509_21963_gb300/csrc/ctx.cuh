@@ -4,6 +4,7 @@
 #pragma once
 
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/cur.h"
@@ -42,6 +43,8 @@ struct cur_ctx {
   // column-scale pass of the FP64 tensor-core sketch reads A (created on demand)
   cudaStream_t side_stream = nullptr;
   cudaEvent_t side_ev[2] = {nullptr, nullptr};
+  // device blocks of freed results (U, I, J), reused by later runs
+  std::vector<std::pair<void*, size_t>> result_pool;
 };
 
 namespace cur {

@@ -38,6 +38,8 @@ struct cur_result {
   int64_t* I = nullptr;
   int64_t* J = nullptr;
   double* U = nullptr;
+  void* block = nullptr;      // one device allocation holding U, I and J
+  size_t block_bytes = 0;
   std::vector<double> rho_hist;
   double phase_ms[CUR_PHASE_COUNT] = {0};
   int64_t launches = 0;
@@ -505,21 +507,19 @@ int run_device(cur_ctx* ctx, const void* A, int64_t m, int64_t n, int64_t lda, i
     TRY(sketch_q(ctx, smode, G, c, static_cast<const float*>(A), m, n, lda, S, 0, B_PARTS, B_TC));
   }
   tick(ctx, -1);
-  TRY(read_status(ctx));
-  const double nY2 = ctx->st_host->scalar[0];
-  if (!std::isfinite(nY2)) return fail(ctx, CUR_ENONFINITE, "A contains Inf or NaN");
-  const double nY = std::sqrt(nY2);
-
+  // ||G A||_F^2 comes back with the first iteration's rho (one host round trip
+  // less per run); a non-finite or zero sketch is handled there, before that
+  // iteration's results are used.
+  double nY = -1.0;
   cur_result* res = new cur_result();
   res->ctx = ctx;
-  res->normY = nY;
-  if (nY == 0.0) {  // G A = 0: nothing to approximate
-    res->rho = 0.0;
-    collect_phases(ctx, res);
-    res->launches = ctx->launches;
-    *out = res;
+  auto take_norm = [&]() -> int {   // after a read_status: ||G A||_F from the status block
+    const double nY2 = ctx->st_host->scalar[0];
+    if (!std::isfinite(nY2)) return fail(ctx, CUR_ENONFINITE, "A contains Inf or NaN");
+    nY = std::sqrt(nY2);
+    res->normY = nY;
     return CUR_OK;
-  }
+  };
 
   // index arrays and masks
   int64_t rcap = max_rank < 256 ? max_rank : 256;
@@ -726,10 +726,23 @@ int run_device(cur_ctx* ctx, const void* A, int64_t m, int64_t n, int64_t lda, i
     }
     // rho_k (the host needs it for the loop test)
     tick(ctx, -1);
-    if ((st = read_status(ctx)) != CUR_OK) return fail_res(st);
+    const int st_iter = read_status(ctx);
+    if (nY < 0.0) {
+      if ((st = take_norm()) != CUR_OK) return fail_res(st);
+      if (nY == 0.0) {  // G A = 0: nothing to approximate (this iteration is discarded)
+        rho = 0.0;
+        break;
+      }
+    }
+    if (st_iter != CUR_OK) return fail_res(st_iter);
     r += bk;
     rho = std::sqrt(ctx->st_host->scalar[1]) / nY;
     res->rho_hist.push_back(rho);
+  }
+  if (nY < 0.0) {   // the loop did not run (tol >= 1): read the norm now
+    if ((st = read_status(ctx)) != CUR_OK) return fail_res(st);
+    if ((st = take_norm()) != CUR_OK) return fail_res(st);
+    if (nY == 0.0) rho = 0.0;
   }
 
   // core of the returned CUR: U = A(I,J)^+ by pivoted QR
@@ -738,19 +751,32 @@ int run_device(cur_ctx* ctx, const void* A, int64_t m, int64_t n, int64_t lda, i
   res->rho = rho;
   res->status = rho > tol_eff ? CUR_TOL_UNREACHED : CUR_OK;
   if (r > 0) {
-    int64_t *Ires = nullptr, *Jres = nullptr;
-    double* Ures = nullptr;
-    cudaError_t e = cudaMalloc((void**)&Ires, sizeof(int64_t) * (size_t)r);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&Jres, sizeof(int64_t) * (size_t)r);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&Ures, sizeof(double) * (size_t)(r * r));
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      cudaFree(Ires); cudaFree(Jres); cudaFree(Ures);
-      return fail_res(fail(ctx, CUR_ENOMEM, "result allocation failed"));
+    // U, I and J in one block, reused from the context's pool of freed result
+    // blocks when one is large enough (no allocation on the repeated-run path)
+    const size_t ub = (sizeof(double) * (size_t)(r * r) + 255) / 256 * 256;
+    const size_t need = ub + 2 * ((sizeof(int64_t) * (size_t)r + 255) / 256 * 256);
+    void* blk = nullptr;
+    size_t blk_bytes = 0;
+    for (size_t k = 0; k < ctx->result_pool.size(); ++k)
+      if (ctx->result_pool[k].second >= need) {
+        blk = ctx->result_pool[k].first;
+        blk_bytes = ctx->result_pool[k].second;
+        ctx->result_pool.erase(ctx->result_pool.begin() + (std::ptrdiff_t)k);
+        break;
+      }
+    if (!blk) {
+      if (cudaMalloc(&blk, need) != cudaSuccess) {
+        cudaGetLastError();
+        return fail_res(fail(ctx, CUR_ENOMEM, "result allocation failed"));
+      }
+      blk_bytes = need;
     }
-    res->I = Ires;
-    res->J = Jres;
-    res->U = Ures;
+    res->block = blk;
+    res->block_bytes = blk_bytes;
+    res->U = static_cast<double*>(blk);
+    res->I = reinterpret_cast<int64_t*>(static_cast<char*>(blk) + ub);
+    res->J = reinterpret_cast<int64_t*>(static_cast<char*>(blk) + ub +
+                                        (sizeof(int64_t) * (size_t)r + 255) / 256 * 256);
     CK(cudaMemcpyAsync(res->I, Id, sizeof(int64_t) * (size_t)r, cudaMemcpyDeviceToDevice, s));
     CK(cudaMemcpyAsync(res->J, Jd, sizeof(int64_t) * (size_t)r, cudaMemcpyDeviceToDevice, s));
     if ((st = ensure(ctx, B_CORE, sizeof(double) * (size_t)(r * r))) != CUR_OK) { cur_result_free(res); return st; }
@@ -821,6 +847,7 @@ void cur_free(cur_ctx* ctx) {
     cudaStreamSynchronize(ctx->side_stream);
     cudaStreamDestroy(ctx->side_stream);
   }
+  for (auto& pb : ctx->result_pool) cudaFree(pb.first);
   for (auto e : ctx->side_ev)
     if (e) cudaEventDestroy(e);
   if (ctx->st_host) cudaFreeHost(ctx->st_host);
@@ -919,9 +946,12 @@ int cur_result_copy_to_host(const cur_result* r, int64_t* I, int64_t* J, double*
 void cur_result_free(cur_result* r) {
   if (!r) return;
   if (r->ctx) cudaStreamSynchronize(r->ctx->stream);
-  cudaFree(r->I);
-  cudaFree(r->J);
-  cudaFree(r->U);
+  if (r->block) {   // back to the context's pool (a few blocks), else freed
+    if (r->ctx && r->ctx->result_pool.size() < 4)
+      r->ctx->result_pool.emplace_back(r->block, r->block_bytes);
+    else
+      cudaFree(r->block);
+  }
   delete r;
 }
 
