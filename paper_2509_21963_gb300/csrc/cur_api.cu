@@ -392,6 +392,9 @@ int sketch_fx_seeded(cur_ctx* ctx, uint64_t seed, int64_t c, const double* A, in
   CK(launch_sketch_fx_colscales(env, c, A, lda, m, n, scratch));
   CK(cudaStreamWaitEvent(env.stream, ctx->side_ev[1], 0));
   tick(ctx, CUR_PHASE_SKETCH);
+  // (a column-blocked form that read the scales of block k + 1 on the side
+  // stream during the tensor-core pass over block k was slower: 1.78 against
+  // 1.63 ms at 20000^2, the pass slowing down next to the concurrent read)
   int64_t nparts = 0;
   CK(launch_sketch_fx_main(env, c, A, lda, m, n, scratch, Y, bp<double>(ctx, parts_id), &nparts,
                            &dstat(ctx)->err));

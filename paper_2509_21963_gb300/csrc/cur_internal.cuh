@@ -166,6 +166,20 @@ cudaError_t launch_sketch_fx_q8(const LaunchEnv& env, const double* G, int64_t c
                                 int64_t n, void* scratch);
 cudaError_t launch_sketch_fx_colscales(const LaunchEnv& env, int64_t c, const double* A,
                                        int64_t lda, int64_t m, int64_t n, void* scratch);
+// The FP64 tensor-core sketch in pieces: zero the column maxima and the sums;
+// column scales of columns [c0, c1); the tensor-core pass over those columns
+// (c0 even); the final reduction.
+cudaError_t launch_sketch_fx_zero(const LaunchEnv& env, int64_t c, const double* A, int64_t lda,
+                                  int64_t m, int64_t n, void* scratch);
+cudaError_t launch_sketch_fx_colscales_range(const LaunchEnv& env, int64_t c, const double* A,
+                                             int64_t lda, int64_t m, int64_t n, void* scratch,
+                                             int64_t c0, int64_t c1);
+cudaError_t launch_sketch_fx_main_range(const LaunchEnv& env, int64_t c, const double* A,
+                                        int64_t lda, int64_t m, int64_t n, void* scratch,
+                                        int64_t c0, int64_t c1, int* err);
+cudaError_t launch_sketch_fx_reduce(const LaunchEnv& env, int64_t c, const double* A, int64_t lda,
+                                    int64_t m, int64_t n, void* scratch, double* Y,
+                                    double* sumsq_part, int64_t* nparts);
 cudaError_t launch_sketch_fx_main(const LaunchEnv& env, int64_t c, const double* A, int64_t lda,
                                   int64_t m, int64_t n, void* scratch, double* Y,
                                   double* sumsq_part, int64_t* nparts, int* err);

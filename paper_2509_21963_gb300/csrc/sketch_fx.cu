@@ -596,12 +596,7 @@ cudaError_t launch_sketch_fx_scales(const LaunchEnv& env, const double* G, int64
   if (!fx_args_ok(c, A, lda, m, n)) return cudaErrorInvalidValue;
   const int64_t ldq = ldq_of(m);
   const FxScratch f = carve_fx(scratch, c, m, n);
-  uint16_t* Gq = f.Gq;
-  unsigned long long* cmax = f.cmax;
-  int* cexp = f.cexp;
-  long long* acc = f.acc_lo;
-
-  cudaError_t e = launch_gaussian_q8(env, G, c, m, ldq, Gq);
+  cudaError_t e = launch_gaussian_q8(env, G, c, m, ldq, f.Gq);
   if (e == cudaSuccess) e = launch_sketch_fx_colscales(env, c, A, lda, m, n, scratch);
   return e;
 }
@@ -614,57 +609,75 @@ cudaError_t launch_sketch_fx_q8(const LaunchEnv& env, const double* G, int64_t c
 
 cudaError_t launch_sketch_fx_colscales(const LaunchEnv& env, int64_t c, const double* A,
                                        int64_t lda, int64_t m, int64_t n, void* scratch) {
+  cudaError_t e = launch_sketch_fx_zero(env, c, A, lda, m, n, scratch);
+  if (e == cudaSuccess) e = launch_sketch_fx_colscales_range(env, c, A, lda, m, n, scratch, 0, n);
+  return e;
+}
+
+cudaError_t launch_sketch_fx_zero(const LaunchEnv& env, int64_t c, const double* A, int64_t lda,
+                                  int64_t m, int64_t n, void* scratch) {
   if (!fx_args_ok(c, A, lda, m, n)) return cudaErrorInvalidValue;
   const FxScratch f = carve_fx(scratch, c, m, n);
-  unsigned long long* cmax = f.cmax;
-  int* cexp = f.cexp;
-  long long* acc = f.acc_lo;
-  cudaError_t e = cudaMemsetAsync(cmax, 0, sizeof(unsigned long long) * (size_t)n, env.stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(acc, 0, 2 * sizeof(long long) * (size_t)(c * n), env.stream);
-  if (e != cudaSuccess) return e;
-  {
-    const int64_t rows_per = 512;
-    dim3 grid((unsigned)((n + 255) / 256), (unsigned)((m + rows_per - 1) / rows_per));
-    colmax_f64_kernel<<<grid, 256, 0, env.stream>>>(A, lda, m, n, rows_per, cmax);
-    colexp_f64_kernel<<<(unsigned)((n + 255) / 256), 256, 0, env.stream>>>(cmax, n, cexp);
-  }
+  cudaError_t e = cudaMemsetAsync(f.cmax, 0, sizeof(unsigned long long) * (size_t)n, env.stream);
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync(f.acc_lo, 0, 2 * sizeof(long long) * (size_t)(c * n), env.stream);
+  return e;
+}
+
+cudaError_t launch_sketch_fx_colscales_range(const LaunchEnv& env, int64_t c, const double* A,
+                                             int64_t lda, int64_t m, int64_t n, void* scratch,
+                                             int64_t c0, int64_t c1) {
+  if (!fx_args_ok(c, A, lda, m, n) || c0 < 0 || c1 > n || c0 >= c1) return cudaErrorInvalidValue;
+  const FxScratch f = carve_fx(scratch, c, m, n);
+  const int64_t nb = c1 - c0;
+  const int64_t rows_per = 512;
+  dim3 grid((unsigned)((nb + 255) / 256), (unsigned)((m + rows_per - 1) / rows_per));
+  colmax_f64_kernel<<<grid, 256, 0, env.stream>>>(A + c0, lda, m, nb, rows_per, f.cmax + c0);
+  colexp_f64_kernel<<<(unsigned)((nb + 255) / 256), 256, 0, env.stream>>>(f.cmax + c0, nb,
+                                                                         f.cexp + c0);
   return cudaGetLastError();
 }
 
 cudaError_t launch_sketch_fx_main(const LaunchEnv& env, int64_t c, const double* A, int64_t lda,
                                   int64_t m, int64_t n, void* scratch, double* Y,
                                   double* sumsq_part, int64_t* nparts, int* err) {
-  if (!fx_args_ok(c, A, lda, m, n)) return cudaErrorInvalidValue;
+  cudaError_t e = launch_sketch_fx_main_range(env, c, A, lda, m, n, scratch, 0, n, err);
+  if (e == cudaSuccess) e = launch_sketch_fx_reduce(env, c, A, lda, m, n, scratch, Y, sumsq_part, nparts);
+  return e;
+}
+
+cudaError_t launch_sketch_fx_main_range(const LaunchEnv& env, int64_t c, const double* A,
+                                        int64_t lda, int64_t m, int64_t n, void* scratch,
+                                        int64_t c0, int64_t c1, int* err) {
+  if (!fx_args_ok(c, A, lda, m, n) || c0 < 0 || c1 > n || c0 >= c1 || (c0 & 1))
+    return cudaErrorInvalidValue;
   const int64_t ldq = ldq_of(m);
   const FxScratch f = carve_fx(scratch, c, m, n);
-  const uint16_t* Gq = f.Gq;
-  int* cexp = f.cexp;
-  long long* acc_lo = f.acc_lo;
-  long long* acc_hi = f.acc_hi;
+  const int64_t nb = c1 - c0;
   cudaError_t e = cudaSuccess;
   EncodeTiledFn enc = encode_fn();
   if (!enc) return cudaErrorNotSupported;
   CUtensorMap mA;
   {
-    cuuint64_t gdim[2] = {(cuuint64_t)n, (cuuint64_t)m};
+    cuuint64_t gdim[2] = {(cuuint64_t)nb, (cuuint64_t)m};
     cuuint64_t gstride[1] = {(cuuint64_t)lda * 8};
     cuuint32_t box[2] = {kCols, kRows};
     cuuint32_t es[2] = {1, 1};
-    if (enc(&mA, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, (void*)A, gdim, gstride, box, es,
+    if (enc(&mA, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, (void*)(A + c0), gdim, gstride, box, es,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
       return cudaErrorInvalidValue;
   }
   FxArgs a;
-  a.m = m; a.n = n; a.ldy = n; a.colexp = cexp;
-  a.acc_lo = reinterpret_cast<unsigned long long*>(acc_lo);
-  a.acc_hi = reinterpret_cast<unsigned long long*>(acc_hi);
-  a.nstrips = (n + kCols - 1) / kCols;
+  a.m = m; a.n = nb; a.ldy = n; a.colexp = f.cexp + c0;   // the block's columns, the full sums' pitch
+  a.acc_lo = reinterpret_cast<unsigned long long*>(f.acc_lo + c0);
+  a.acc_hi = reinterpret_cast<unsigned long long*>(f.acc_hi + c0);
+  a.nstrips = (nb + kCols - 1) / kCols;
   a.nchunks = (m + kChunkRows - 1) / kChunkRows;
   a.err = err;
   const int64_t units = a.nstrips * a.nchunks;
   const int grid = (int)(units < env.num_sms ? units : env.num_sms);
-  // row groups of at most 64 rows of G_q: one pass of A each
+  // row groups of at most 64 rows of G_q: one pass of the block's columns each
   for (int64_t g0 = 0; g0 < c; g0 += 64) {
     const int64_t cg = c - g0 < 64 ? c - g0 : 64;
     const int CP = (int)((cg + 15) / 16 * 16);
@@ -673,7 +686,7 @@ cudaError_t launch_sketch_fx_main(const LaunchEnv& env, int64_t c, const double*
     cuuint64_t gstride[1] = {(cuuint64_t)ldq * 2};
     cuuint32_t box[2] = {kGRows, (cuuint32_t)CP};
     cuuint32_t es[2] = {1, 1};
-    if (enc(&mG, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)(Gq + g0 * ldq), gdim, gstride, box,
+    if (enc(&mG, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)(f.Gq + g0 * ldq), gdim, gstride, box,
             es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
       return cudaErrorInvalidValue;
@@ -687,8 +700,16 @@ cudaError_t launch_sketch_fx_main(const LaunchEnv& env, int64_t c, const double*
     }
     if (e != cudaSuccess) return e;
   }
+  return cudaSuccess;
+}
+
+cudaError_t launch_sketch_fx_reduce(const LaunchEnv& env, int64_t c, const double* A, int64_t lda,
+                                    int64_t m, int64_t n, void* scratch, double* Y,
+                                    double* sumsq_part, int64_t* nparts) {
+  if (!fx_args_ok(c, A, lda, m, n)) return cudaErrorInvalidValue;
+  const FxScratch f = carve_fx(scratch, c, m, n);
   const dim3 rgrid((unsigned)((n + 255) / 256), (unsigned)((c + kReduceRows - 1) / kReduceRows));
-  fx_reduce_kernel<<<rgrid, 256, 0, env.stream>>>(acc_lo, acc_hi, c, n, cexp, Y, sumsq_part);
+  fx_reduce_kernel<<<rgrid, 256, 0, env.stream>>>(f.acc_lo, f.acc_hi, c, n, f.cexp, Y, sumsq_part);
   *nparts = (int64_t)rgrid.x * rgrid.y;
   return cudaGetLastError();
 }
