@@ -100,36 +100,44 @@ __device__ double cta_sum(double v) {
   return total;
 }
 
-// (value, index) maximum: larger value wins, equal values -> smaller index;
-// index < 0 means "none".
-__device__ __forceinline__ bool better(double v1, int64_t i1, double v2, int64_t i2) {
-  if (i2 < 0) return i1 >= 0;
-  if (i1 < 0) return false;
-  return v1 > v2 || (v1 == v2 && i1 < i2);
+// Magnitude keys: the bit pattern of |x| orders like |x| for every non-NaN
+// double, so pivot searches compare integers (an FP64 compare-and-select takes
+// ~230 cycles on GB300, an integer one a few); NaN gets -2, below every number.
+__device__ __forceinline__ long long mkey(double x) {
+  const long long k = __double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFLL;
+  return k > 0x7FF0000000000000LL ? -2 : k;
 }
 
-__device__ void cta_argmax(double& v, int64_t& idx) {
-  __shared__ double rv[kMaxWarps];
+// (key, index) maximum: larger key wins, equal keys -> smaller index;
+// index < 0 means "none".
+__device__ __forceinline__ bool better(long long k1, int64_t i1, long long k2, int64_t i2) {
+  if (i2 < 0) return i1 >= 0;
+  if (i1 < 0) return false;
+  return k1 > k2 || (k1 == k2 && i1 < i2);
+}
+
+__device__ void cta_argmax(long long& k, int64_t& idx) {
+  __shared__ long long rk[kMaxWarps];
   __shared__ long long ri[kMaxWarps];
   for (int o = 16; o > 0; o >>= 1) {
-    double ov = __shfl_down_sync(0xffffffffu, v, o);
-    long long oi = __shfl_down_sync(0xffffffffu, (long long)idx, o);
-    if (better(ov, oi, v, idx)) { v = ov; idx = oi; }
+    const long long ok = __shfl_down_sync(0xffffffffu, k, o);
+    const long long oi = __shfl_down_sync(0xffffffffu, (long long)idx, o);
+    if (better(ok, oi, k, idx)) { k = ok; idx = oi; }
   }
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   __syncthreads();
-  if (lane == 0) { rv[wid] = v; ri[wid] = idx; }
+  if (lane == 0) { rk[wid] = k; ri[wid] = idx; }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double bv = rv[0];
+    long long bk = rk[0];
     int64_t bi = ri[0];
     for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
-      if (better(rv[w], ri[w], bv, bi)) { bv = rv[w]; bi = ri[w]; }
-    rv[0] = bv;
+      if (better(rk[w], ri[w], bk, bi)) { bk = rk[w]; bi = ri[w]; }
+    rk[0] = bk;
     ri[0] = bi;
   }
   __syncthreads();
-  v = rv[0];
+  k = rk[0];
   idx = ri[0];
   __syncthreads();
 }
@@ -165,17 +173,17 @@ struct PhaseClock {
 __device__ bool cta_lupp(double* W, int64_t ldw, int nf, int64_t ncand, int steps, uint8_t* mask,
                          int64_t* piv, double* prow) {
   for (int t = 0; t < steps; ++t) {
-    double bv = -1.0;
+    long long bk = -1;
     int64_t bi = -1;
     for (int64_t i = threadIdx.x; i < ncand; i += blockDim.x) {
       if (mask[i]) continue;
-      double a = fabs(W[t * ldw + i]);
-      if (a > bv) { bv = a; bi = i; }  // NaN never wins
+      const long long a = mkey(W[t * ldw + i]);
+      if (a > bk) { bk = a; bi = i; }  // NaN (-2) never wins
     }
-    cta_argmax(bv, bi);
+    cta_argmax(bk, bi);
     if (bi < 0) return false;
     if (threadIdx.x == 0) { piv[t] = bi; mask[bi] = 1; }
-    if (bv > 0.0 && t + 1 < nf) {
+    if (bk > 0 && t + 1 < nf) {
       for (int u = t + 1 + threadIdx.x; u < nf; u += blockDim.x) prow[u] = W[u * ldw + bi];
       __syncthreads();
       const double pivv = W[t * ldw + bi];
@@ -204,16 +212,16 @@ __device__ bool cta_lupp(double* W, int64_t ldw, int nf, int64_t ncand, int step
 
 __device__ void qr_local_best(const Team& tm, const QrWs& w, int64_t q, double* slot) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  double bv = -1.0;
+  long long bk = -1;
   int64_t bi = -1;
   for (int64_t col = tm.rank + (int64_t)tm.T * wid; col < q; col += (int64_t)tm.T * nw) {
     if (lane == 0 && !w.used[col]) {
-      double v = w.norm2[col];
-      if (better(v, col, bv, bi)) { bv = v; bi = col; }
+      const long long k = mkey(w.norm2[col]);
+      if (better(k, col, bk, bi)) { bk = k; bi = col; }
     }
   }
-  cta_argmax(bv, bi);
-  if (threadIdx.x == 0) { slot[0] = bv; slot[1] = (double)bi; }
+  cta_argmax(bk, bi);
+  if (threadIdx.x == 0) { slot[0] = __longlong_as_double(bk); slot[1] = (double)bi; }
 }
 
 // Apply H_j = I - tau v v^T (v = vloc, rows j..p-1) to one column x of the
@@ -331,28 +339,29 @@ __device__ bool team_qr_factor(const Team& tm, const QrWs& w, int64_t p, int64_t
   for (int64_t j = 0; j < kmax; ++j) {
     const double* slot = w.slots + (j & 1) * 2 * tm.T;
     if (threadIdx.x < 32) {  // warp 0 reads the T candidates, all loads in flight together
-      double bv = -1.0;
+      long long bk = -1;
       int64_t bi = -1;
       constexpr int kR = 8;
-      double cv[kR], ci[kR];
+      long long cv[kR];
+      double ci[kR];
 #pragma unroll
       for (int u = 0; u < kR; ++u) {
         const int r = threadIdx.x + 32 * u;
-        cv[u] = r < tm.T ? __ldcg(slot + 2 * r) : -1.0;
+        cv[u] = r < tm.T ? __double_as_longlong(__ldcg(slot + 2 * r)) : -1;
         ci[u] = r < tm.T ? __ldcg(slot + 2 * r + 1) : -1.0;
       }
 #pragma unroll
       for (int u = 0; u < kR; ++u)
-        if (better(cv[u], (int64_t)ci[u], bv, bi)) { bv = cv[u]; bi = (int64_t)ci[u]; }
+        if (better(cv[u], (int64_t)ci[u], bk, bi)) { bk = cv[u]; bi = (int64_t)ci[u]; }
       for (int r = threadIdx.x + 32 * kR; r < tm.T; r += 32) {  // teams above 256 CTAs
-        double v = __ldcg(slot + 2 * r);
-        int64_t i = (int64_t)__ldcg(slot + 2 * r + 1);
-        if (better(v, i, bv, bi)) { bv = v; bi = i; }
+        const long long k = __double_as_longlong(__ldcg(slot + 2 * r));
+        const int64_t i = (int64_t)__ldcg(slot + 2 * r + 1);
+        if (better(k, i, bk, bi)) { bk = k; bi = i; }
       }
-      for (int o = 16; o > 0; o >>= 1) {  // (value, index) max is order independent
-        double ov = __shfl_xor_sync(0xffffffffu, bv, o);
-        long long oi = __shfl_xor_sync(0xffffffffu, (long long)bi, o);
-        if (better(ov, oi, bv, bi)) { bv = ov; bi = oi; }
+      for (int o = 16; o > 0; o >>= 1) {  // (key, index) max is order independent
+        const long long ok = __shfl_xor_sync(0xffffffffu, bk, o);
+        const long long oi = __shfl_xor_sync(0xffffffffu, (long long)bi, o);
+        if (better(ok, oi, bk, bi)) { bk = ok; bi = oi; }
       }
       if (threadIdx.x == 0) s_pc = bi;
     }
