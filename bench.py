@@ -66,7 +66,7 @@ HBM_GBS, HBM_SRC = hbm_peak()
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--m", type=int, default=20000)
@@ -976,6 +976,7 @@ def main():
         return run_reference(a, ws, rank)
 
     import copy
+    import numpy as np
     import torch
     import paper_2509_21963_gb300 as cur
 
@@ -1041,19 +1042,39 @@ def main():
     t0.record(stream)
     infos = []
     phases = []
-    for _ in range(a.steps):
+    ev_step = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(a.steps)]
+    for k in range(a.steps):
+        ev_step[k][0].record(stream)
         infos.append(one_step(True))
+        ev_step[k][1].record(stream)
         phases.append(last_phases[0])
     t1.record(stream)
     barrier()
     clk = clocks.stop()
     elapsed_ms = t0.elapsed_time(t1)
+    per_step = [e0.elapsed_time(e1) for e0, e1 in ev_step]
+    step_ms = {"median": float(np.median(per_step)), "p10": float(np.percentile(per_step, 10)),
+               "p90": float(np.percentile(per_step, 90)), "n": len(per_step)}
     log(f"timed {a.steps} steps: {elapsed_ms:.2f} ms")
     elapsed_ms, value = aggregate(elapsed_ms, a.steps, ws, device=f"cuda:{local}")
     rank_r, iters, rho, _, launches, status = infos[-1]
     phase_ms = {p: sum(ph[p] for ph in phases) / len(phases) for p in cur.PHASES}
     sketch_ms = phase_ms["sketch"]
     ms_per_step = elapsed_ms / a.steps
+
+    # accuracy of the timed configuration: ||A - C U R||_F / ||A||_F in FP64 on
+    # the device (outside the timed region), C = A(:, J), R = A(I, :)
+    res = ctx.run(A, a.tol, a.block, a.sketch, a.seed, sketch_mode=a.sketch_mode)
+    A64 = A if A.dtype == torch.float64 else A.to(torch.float64)
+    Jt = torch.from_numpy(res.J).to(A.device)
+    It = torch.from_numpy(res.I).to(A.device)
+    Ut = torch.from_numpy(res.U.reshape(res.rank, res.rank)).to(A.device)
+    E = A64 - (A64[:, Jt] @ Ut) @ A64[It, :]
+    true_err = float(torch.linalg.norm(E) / torch.linalg.norm(A64))
+    del E, A64
+    torch.cuda.empty_cache()
+    log(f"true relative error {true_err:.3e} (rho {res.rho:.3e})")
 
     # end-to-end: the host-buffer C ABI call, H2D of A and D2H of I, J, U inside
     e2e = None
@@ -1074,6 +1095,23 @@ def main():
         es = A_host.itemsize
         e2e = {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": a.m * a.n * es,
                "d2h_bytes_per_step": 16 * r.rank + 8 * r.rank * r.rank + 8 * (r.iterations + 8)}
+        # the copy floor on this machine: the same bytes, one plain pinned copy
+        # into a device buffer (the host link's rate varies between machines)
+        Ad = torch.empty_like(A)
+        cms = []
+        for _ in range(3):
+            c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            c0.record()
+            Ad.copy_(Ah, non_blocking=True)
+            c1.record()
+            c1.synchronize()
+            cms.append(c0.elapsed_time(c1))
+        del Ad
+        copy_ms = sorted(cms)[1]
+        e2e["h2d_copy_ms"] = copy_ms
+        e2e["h2d_gbs"] = a.m * a.n * es / (copy_ms * 1e-3) / 1e9
+        e2e["after_copy_ms"] = e2e_ms - copy_ms
+        log(f"plain H2D copy of A: {copy_ms:.2f} ms ({e2e['h2d_gbs']:.1f} GB/s)")
 
     # roofline of the dominant kernel: the sketch of A (the one full pass)
     fp64_meas = ctx.fp64_tflops()
@@ -1123,7 +1161,8 @@ def main():
                          f"{a.m}x{a.n} matrix with {cores} threads; one_core_ms: the same run "
                          "on one thread",
                "oracle_rank": ro.rank, "oracle_rho": ro.rho,
-               "same_indices_as_gpu": bool(ro.rank == rank_r)}
+               "same_indices_as_gpu": bool(np.array_equal(np.asarray(ro.I), res.I) and
+                                           np.array_equal(np.asarray(ro.J), res.J))}
     del A_host
 
     extra = {}
@@ -1206,6 +1245,7 @@ def main():
         line = {
             "metric": "time-to-tolerance per CUR", "value": value, "unit": "ms", "n_gpus": ws,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms_per_step,
+            "step_ms": step_ms,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
             "dtype": {0: "f64", 5: "f64 loop; sketch on bf16 tensor cores, exact 52-bit fixed point"}.get(
                 a.sketch_mode, f"bf16x{a.sketch_mode} sketch, f64 loop"),
@@ -1214,6 +1254,7 @@ def main():
                        "block_size": a.block, "sketch_size": a.sketch, "a_dtype": a.dtype,
                        "sketch_mode": a.sketch_mode,
                        "rank": rank_r, "iterations": iters, "rho": rho, "status": status,
+                       "true_rel_error": true_err,
                        "l2": "inputs larger than L2 (A is resident in HBM)",
                        "parallelism": f"replicas x{ws}"},
             "gpu_launches": launches * a.steps,

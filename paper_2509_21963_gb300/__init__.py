@@ -280,12 +280,15 @@ class Context:
             lib().cur_result_free(out)
 
     def run_host(self, A: np.ndarray, tol, block_size, sketch_size=0, seed=0, **kw) -> Result:
-        """End-to-end form: A is a host array (C-contiguous float64/float32)."""
-        assert A.ndim == 2 and A.flags.c_contiguous
+        """End-to-end form: A is a host array (float64/float32, rows contiguous,
+        row stride a whole number of elements >= n)."""
+        assert A.ndim == 2 and A.strides[1] == A.itemsize and A.strides[0] % A.itemsize == 0
+        lda = A.strides[0] // A.itemsize
+        assert lda >= A.shape[1]
         dt = {np.dtype(np.float64): CUR_F64, np.dtype(np.float32): CUR_F32}[A.dtype]
         out = _vp()
         o = self._opts(**kw)
-        st = lib().cur_run_host(self.ptr, _vp(A.ctypes.data), A.shape[0], A.shape[1], A.shape[1], dt,
+        st = lib().cur_run_host(self.ptr, _vp(A.ctypes.data), A.shape[0], A.shape[1], lda, dt,
                                 float(tol), int(block_size), int(sketch_size), int(seed),
                                 ctypes.byref(o), ctypes.byref(out))
         _check(self.ptr, st, ok=(CUR_OK, CUR_TOL_UNREACHED))

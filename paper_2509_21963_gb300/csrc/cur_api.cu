@@ -403,6 +403,97 @@ int sketch_fx_seeded(cur_ctx* ctx, uint64_t seed, int64_t c, const double* A, in
   return CUR_OK;
 }
 
+// The FP64 tensor-core sketch with A arriving from host memory.  A is copied
+// into A_dev on the context's copy stream in column groups at least 8192
+// columns wide (pitched copies with shorter rows run well below the host
+// link's rate), each group in row blocks.  The column maxima of a row block
+// are taken as soon as it lands; once a group is complete its exponents and
+// its tensor-core pass follow, under the copy of the next group, so only the
+// last group's pass is left when the copy ends.  G (given, or drawn from the
+// seed) and G_q are formed on the side stream meanwhile.  Every group adds
+// exact integer sums into its own columns, so Y equals the device-resident
+// form's bit for bit.
+int sketch_fx_from_host(cur_ctx* ctx, const double* G, uint64_t seed, int64_t c,
+                        const void* A_host, int64_t lda_host, double* A_dev, int64_t m, int64_t n,
+                        double* Y, int slot, BufId parts_id, BufId scratch_id) {
+  LaunchEnv env = env_of(ctx);
+  const int64_t ng = std::max<int64_t>(1, n / 8192);
+  const int64_t w = ((n + ng - 1) / ng + 127) / 128 * 128;
+  const int64_t nr = m >= 1024 ? std::min<int64_t>(8, m / 512) : 1;
+  const int64_t rows = (m + nr - 1) / nr;
+  const int nev = (int)(ng * nr);
+  if (!G) TRY(ensure(ctx, B_OMEGA, sizeof(double) * (size_t)(c * m)));
+  TRY(ensure(ctx, scratch_id, sketch_fx_scratch_bytes(c, m, n)));
+  TRY(ensure(ctx, parts_id, sizeof(double) * (size_t)sketch_fx_max_parts(c, n)));
+  if (!ctx->copy_stream) CK(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
+  if (!ctx->side_stream) CK(cudaStreamCreateWithFlags(&ctx->side_stream, cudaStreamNonBlocking));
+  for (auto& ev : ctx->side_ev)
+    if (!ev) CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  while ((int)ctx->copy_ev.size() < nev + 1) {
+    cudaEvent_t e;
+    CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    ctx->copy_ev.push_back(e);
+  }
+  LaunchEnv side = env;
+  side.stream = ctx->side_stream;
+  void* scratch = ctx->buf[scratch_id].p;
+  const size_t es = sizeof(double);
+  const char* src = static_cast<const char*>(A_host);
+  tick(ctx, CUR_PHASE_SCALES);
+  // the copies and the side stream may only start once earlier work on the
+  // context's stream (a previous run reading A_dev, G or the scratch) is done
+  CK(cudaEventRecord(ctx->copy_ev[nev], env.stream));
+  CK(cudaStreamWaitEvent(ctx->copy_stream, ctx->copy_ev[nev], 0));
+  CK(cudaStreamWaitEvent(side.stream, ctx->copy_ev[nev], 0));
+  for (int64_t g = 0; g < ng; ++g) {
+    const int64_t c0 = g * w, wg = std::min(w, n - c0);
+    for (int64_t k = 0; k < nr; ++k) {
+      const int64_t r0 = k * rows, rk = std::min(rows, m - r0);
+      if (wg > 0 && rk > 0)
+        CK(cudaMemcpy2DAsync(A_dev + r0 * n + c0, (size_t)n * es,
+                             src + ((size_t)r0 * (size_t)lda_host + (size_t)c0) * es,
+                             (size_t)lda_host * es, (size_t)wg * es, (size_t)rk,
+                             cudaMemcpyHostToDevice, ctx->copy_stream));
+      CK(cudaEventRecord(ctx->copy_ev[g * nr + k], ctx->copy_stream));
+    }
+  }
+  if (!G) {
+    G = bp<double>(ctx, B_OMEGA);
+    CK(launch_gaussian(side, seed, c, m, const_cast<double*>(G), m));
+    ctx->launches += 1;
+  }
+  CK(launch_sketch_fx_q8(side, G, c, m, n, scratch));
+  CK(cudaEventRecord(ctx->side_ev[1], side.stream));
+  CK(launch_sketch_fx_zero(env, c, A_dev, n, m, n, scratch));
+  bool joined = false;
+  for (int64_t g = 0; g < ng; ++g) {
+    const int64_t c0 = g * w, c1 = std::min(n, c0 + w);
+    if (c0 >= c1) break;
+    for (int64_t k = 0; k < nr; ++k) {
+      const int64_t r0 = k * rows, r1 = std::min(m, r0 + rows);
+      CK(cudaStreamWaitEvent(env.stream, ctx->copy_ev[g * nr + k], 0));
+      if (r0 < r1) {
+        CK(launch_sketch_fx_colmax_block(env, c, A_dev, n, m, n, scratch, r0, r1, c0, c1));
+        ctx->launches += 1;
+      }
+    }
+    CK(launch_sketch_fx_colexp_range(env, c, A_dev, n, m, n, scratch, c0, c1));
+    if (!joined) {
+      CK(cudaStreamWaitEvent(env.stream, ctx->side_ev[1], 0));
+      tick(ctx, CUR_PHASE_SKETCH);
+      joined = true;
+    }
+    CK(launch_sketch_fx_main_range(env, c, A_dev, n, m, n, scratch, c0, c1, &dstat(ctx)->err));
+    ctx->launches += 1 + (c + 63) / 64;
+  }
+  int64_t nparts = 0;
+  CK(launch_sketch_fx_reduce(env, c, A_dev, n, m, n, scratch, Y, bp<double>(ctx, parts_id),
+                             &nparts));
+  ctx->launches += 2;
+  TRY(sum_parts(ctx, bp<double>(ctx, parts_id), nparts, &dstat(ctx)->scalar[slot]));
+  return CUR_OK;
+}
+
 int check_fx_form(cur_ctx* ctx, const void* A, int64_t lda, int dtype) {
   if (dtype != CUR_F64) return fail(ctx, CUR_EINVAL, "the FP64 tensor-core sketch needs FP64 A");
   if (lda % 2 != 0 || (reinterpret_cast<uintptr_t>(A) & 15) != 0)
@@ -501,6 +592,9 @@ int run_device(cur_ctx* ctx, const void* A, int64_t m, int64_t n, int64_t lda, i
                              B_PARTS));
   } else if (smode == CUR_SKETCH_F64) {
     TRY(sketch_f64(ctx, G, c, A, f32, m, n, lda, S, 0, B_PARTS));
+  } else if (smode == CUR_SKETCH_F64_TC && A_host) {
+    TRY(sketch_fx_from_host(ctx, fx_seeded ? nullptr : G, seed, c, A_host, lda_host,
+                            static_cast<double*>(const_cast<void*>(A)), m, n, S, 0, B_PARTS, B_FX));
   } else if (smode == CUR_SKETCH_F64_TC && fx_seeded) {
     TRY(sketch_fx_seeded(ctx, seed, c, static_cast<const double*>(A), m, n, lda, S, 0, B_PARTS,
                          B_FX));
@@ -887,8 +981,11 @@ int cur_run_host(cur_ctx* ctx, const void* A_host, int64_t m, int64_t n, int64_t
   size_t bytes = es * (size_t)(m * n);
   CK(cudaSetDevice(ctx->device));
   TRY(ensure(ctx, B_AHOST, bytes));
-  const bool overlap = !opts || opts->sketch_mode == CUR_SKETCH_F64;
-  if (!overlap)  // the precision forms read A twice (column scales first): copy it whole
+  // the FP64 forms overlap the copy of A with the sketch; the precision forms
+  // read A twice (column scales first): copy it whole
+  const bool overlap = !opts || opts->sketch_mode == CUR_SKETCH_F64 ||
+                       (opts->sketch_mode == CUR_SKETCH_F64_TC && dtype == CUR_F64);
+  if (!overlap)
     CK(cudaMemcpy2DAsync(ctx->buf[B_AHOST].p, es * (size_t)n, A_host, es * (size_t)lda,
                          es * (size_t)n, (size_t)m, cudaMemcpyHostToDevice, ctx->stream));
   int st = run_device(ctx, ctx->buf[B_AHOST].p, m, n, n, dtype, tol, block_size, sketch_size, seed,

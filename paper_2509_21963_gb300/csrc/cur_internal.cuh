@@ -174,6 +174,15 @@ cudaError_t launch_sketch_fx_zero(const LaunchEnv& env, int64_t c, const double*
 cudaError_t launch_sketch_fx_colscales_range(const LaunchEnv& env, int64_t c, const double* A,
                                              int64_t lda, int64_t m, int64_t n, void* scratch,
                                              int64_t c0, int64_t c1);
+// The column scales in finer pieces: the maxima of rows [r0, r1) of columns
+// [c0, c1) (atomic maxima into the zeroed column maxima), then E_j of columns
+// [c0, c1) once all their rows are in.
+cudaError_t launch_sketch_fx_colmax_block(const LaunchEnv& env, int64_t c, const double* A,
+                                          int64_t lda, int64_t m, int64_t n, void* scratch,
+                                          int64_t r0, int64_t r1, int64_t c0, int64_t c1);
+cudaError_t launch_sketch_fx_colexp_range(const LaunchEnv& env, int64_t c, const double* A,
+                                          int64_t lda, int64_t m, int64_t n, void* scratch,
+                                          int64_t c0, int64_t c1);
 cudaError_t launch_sketch_fx_main_range(const LaunchEnv& env, int64_t c, const double* A,
                                         int64_t lda, int64_t m, int64_t n, void* scratch,
                                         int64_t c0, int64_t c1, int* err);

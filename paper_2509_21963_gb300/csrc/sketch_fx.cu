@@ -627,12 +627,32 @@ cudaError_t launch_sketch_fx_zero(const LaunchEnv& env, int64_t c, const double*
 cudaError_t launch_sketch_fx_colscales_range(const LaunchEnv& env, int64_t c, const double* A,
                                              int64_t lda, int64_t m, int64_t n, void* scratch,
                                              int64_t c0, int64_t c1) {
+  cudaError_t e = launch_sketch_fx_colmax_block(env, c, A, lda, m, n, scratch, 0, m, c0, c1);
+  if (e == cudaSuccess) e = launch_sketch_fx_colexp_range(env, c, A, lda, m, n, scratch, c0, c1);
+  return e;
+}
+
+cudaError_t launch_sketch_fx_colmax_block(const LaunchEnv& env, int64_t c, const double* A,
+                                          int64_t lda, int64_t m, int64_t n, void* scratch,
+                                          int64_t r0, int64_t r1, int64_t c0, int64_t c1) {
+  if (!fx_args_ok(c, A, lda, m, n) || c0 < 0 || c1 > n || c0 >= c1 || r0 < 0 || r1 > m ||
+      r0 >= r1)
+    return cudaErrorInvalidValue;
+  const FxScratch f = carve_fx(scratch, c, m, n);
+  const int64_t nb = c1 - c0, mb = r1 - r0;
+  const int64_t rows_per = 512;
+  dim3 grid((unsigned)((nb + 255) / 256), (unsigned)((mb + rows_per - 1) / rows_per));
+  colmax_f64_kernel<<<grid, 256, 0, env.stream>>>(A + r0 * lda + c0, lda, mb, nb, rows_per,
+                                                  f.cmax + c0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sketch_fx_colexp_range(const LaunchEnv& env, int64_t c, const double* A,
+                                          int64_t lda, int64_t m, int64_t n, void* scratch,
+                                          int64_t c0, int64_t c1) {
   if (!fx_args_ok(c, A, lda, m, n) || c0 < 0 || c1 > n || c0 >= c1) return cudaErrorInvalidValue;
   const FxScratch f = carve_fx(scratch, c, m, n);
   const int64_t nb = c1 - c0;
-  const int64_t rows_per = 512;
-  dim3 grid((unsigned)((nb + 255) / 256), (unsigned)((m + rows_per - 1) / rows_per));
-  colmax_f64_kernel<<<grid, 256, 0, env.stream>>>(A + c0, lda, m, nb, rows_per, f.cmax + c0);
   colexp_f64_kernel<<<(unsigned)((nb + 255) / 256), 256, 0, env.stream>>>(f.cmax + c0, nb,
                                                                          f.cexp + c0);
   return cudaGetLastError();

@@ -477,6 +477,31 @@ def test_host_entry_point_row_blocks(ctx):
     _check_parity(A, h, ref, 20, require_full=False)
 
 
+@pytest.mark.parametrize("m,n,strided", [(700, 1500, False), (600, 2176, True), (300, 128, False),
+                                         (1100, 16500, True)])
+def test_host_entry_point_fx_column_blocks(ctx, m, n, strided):
+    """FP64 tensor-core sketch with A in host memory: A is copied in column
+    groups of at least 8192 columns (16500 gives 8320 + 8180), each in row
+    blocks of at least 512 rows (1100 gives two); the column maxima of a row
+    block are taken when it lands and a group's tensor-core pass runs while
+    the next group is copied.  The sketch sums are exact integers added into
+    each group's own columns, so the run equals the device-input run bit for
+    bit (strided host rows too)."""
+    k = min(m, n)
+    A = inputs.svd_matrix(m, n, 10.0 ** (-np.arange(1, k + 1) / 40.0), seed=m + n)
+    if strided:
+        Aw = np.zeros((m, n + 10))
+        Aw[:, :n] = A
+        Ah = Aw[:, :n]
+    else:
+        Ah = A
+    a = ctx.run(dev(A), 1e-6, 20, 30, 3, sketch_mode=5)
+    h = ctx.run_host(Ah, 1e-6, 20, 30, 3, sketch_mode=5)
+    assert np.array_equal(a.I, h.I) and np.array_equal(a.J, h.J) and a.rank == h.rank
+    assert a.rho == h.rho and np.array_equal(a.U, h.U)
+    assert a.status == h.status
+
+
 def test_deterministic_repeat(ctx):
     A = dev(inputs.cfg_small(2))
     a = ctx.run(A, 1e-6, 10, 30, 4)
