@@ -121,7 +121,7 @@ __device__ __forceinline__ void fx_digits(uint64_t bits, int rshift_base, float 
 
 // The same digits for columns with E >= kFastMinExp, branch-free: the implicit
 // bit is always set (an exponent field of 0 gives a shift >= 53, X = 0), the
-// 64-bit shift is done with clamped funnel shifts, and each 9-bit field goes
+// 64-bit shift is one clamped shr.b64, and each 9-bit field goes
 // straight into an FP32 mantissa whose exponent gives that field weight one
 // (2^23 + f for bits 0-8, 2^14 + f for bits 9-17 left in place), so one
 // subtraction yields the digit.  f[0..5] hold FP32 bit patterns.
@@ -129,8 +129,9 @@ __device__ __forceinline__ void fx_digits_fast(uint32_t lo, uint32_t hi, int rsh
                                                uint32_t (&f)[kDigits]) {
   const uint32_t r = (uint32_t)(rshift_base - (int)((hi >> 20) & 0x7FFu));   // >= 1
   const uint32_t mh = (hi & 0x000FFFFFu) | 0x00100000u;
-  const uint32_t th = __funnelshift_rc(mh, 0u, r);             // 0 for r >= 32
-  const uint32_t tl = r < 32u ? __funnelshift_rc(lo, mh, r) : __funnelshift_rc(mh, 0u, r - 32u);
+  uint64_t T64;   // PTX clamps the shift at 64: X = 0 for r >= 64
+  asm("shr.b64 %0, %1, %2;" : "=l"(T64) : "l"(((uint64_t)mh << 32) | lo), "r"(r));
+  const uint32_t th = (uint32_t)(T64 >> 32), tl = (uint32_t)T64;
   const uint32_t sm = (uint32_t)((int32_t)hi >> 31);           // all ones for x < 0
   uint32_t yl, yh;                                             // X + K, X = -T for x < 0
   asm("add.cc.u32 %0, %2, %3;\n\taddc.u32 %1, %4, %5;"
@@ -316,7 +317,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             fx_digits_fast(x1.x, x1.y, base, f1);
 #pragma unroll
             for (int d = 0; d < kDigits; ++d)   // two BF16 digits (rows 2p, 2p+1) per column
-              w[d][p] = __byte_perm(f0[d], f1[d], 0x7632);
+              asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(w[d][p])
+                  : "f"(__uint_as_float(f1[d])), "f"(__uint_as_float(f0[d])));
           }
         } else {
 #pragma unroll
