@@ -44,9 +44,9 @@ sys.path.insert(0, ROOT)
 # host-side row-block launchers were appended to the file (the kernel unchanged).
 TRAFFIC = {"sketch_simt.cu": {"sha1": "31824a3eff0a3f330025c2a908a52893a001d576",
                               "bytes_per_launch_full": 3.323e9},
-           # profiles/sketch_fx_8192x4096_c55.md: 277.5 MB read + 4.6 MB written at 8192 x 4096;
-           # at 20000^2 reads scale with m*n (3309 MB) and the int64 sum writes with c*n (22 MB)
-           "sketch_fx.cu": {"sha1": "5e52123f26ca125fceed9cf4e9921cca4b9cb91d", "bytes_per_launch_full": 3.331e9}}
+           # profiles/sketch_fx_8192x4096_c55.md: 277.4 MB read + 4.1 MB written at 8192 x 4096;
+           # at 20000^2 reads scale with m*n (3307 MB) and the int64 sum writes with c*n (20 MB)
+           "sketch_fx.cu": {"sha1": "340702b5a6bcfaeedd52420c55205b9dc38e1f06", "bytes_per_launch_full": 3.327e9}}
 FP64_PEAK_TFLOPS = 1.25  # GB300 nominal FP64 rate; the line reports the measured one beside it
 
 
