@@ -51,8 +51,8 @@ FP64_PEAK_TFLOPS = 1.25  # GB300 nominal FP64 rate; the line reports the measure
 
 
 def hbm_peak():
-    """Measured copy bandwidth of the GB300s (MEASURED_PEAKS.json, written
-    by the driver), else the profiling recipe's fallback."""
+    """Measured copy bandwidth of the GB300s this runs on (MEASURED_PEAKS.json),
+    else 6800 GB/s, an earlier copy measurement on a GB300."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             return float(json.load(f)["hbm_gbs"]), "measured"

@@ -281,7 +281,7 @@ int64_t cur_oracle_qrcp_pinv(const double *M, int64_t p, int64_t q,
 }
 
 /* ------------------------------------------------------------------------ */
-/* Helpers of the driver loop (plain loops).                                */
+/* Helpers of the main loop (plain loops).                                  */
 /* ------------------------------------------------------------------------ */
 static double frob(const double *X, int64_t len) {
   double s = 0.0;
