@@ -25,6 +25,11 @@ doubles and all-reduces of b m + r b doubles plus one scalar.
 The arithmetic of a rank goes through a backend object; CudaBackend runs the
 library's C-ABI step kernels (cur_step_*) on the rank's GPU.  Without an
 initialised process group the run uses a single rank.
+
+With the FP64 tensor-core sketch (CudaBackend(sketch_mode=5)) every column of
+Y = RN(G_q trunc(A 2^(52 - E_j))) 2^(E_j - 52) depends only on that column of
+A (its own exponent E_j, an exact integer sum rounded once), so each rank's
+block of S^col equals the same columns of the unsharded sketch bit for bit.
 """
 from __future__ import annotations
 
@@ -174,19 +179,30 @@ def run(backend, A_local, n: int, col0: int, tol: float, b: int, c: int, seed: i
 class CudaBackend:
     """One rank's arithmetic on its GPU through the library's step kernels
     (Context.gaussian / sketch / lupp / gather / gemm / pinv).  Arrays are
-    FP64 CUDA tensors; the process group is NCCL (or gloo, via host copies)."""
+    FP64 CUDA tensors; the process group is NCCL (or gloo, via host copies).
+    sketch_mode 0: the FP64-pipe sketch; 5: the FP64 tensor-core sketch."""
 
-    def __init__(self, ctx, nccl: bool = True):
+    def __init__(self, ctx, nccl: bool = True, sketch_mode: int = 0):
         import torch
+        if sketch_mode not in (0, 5):
+            raise ValueError("sketch_mode must be 0 or 5")
         self.ctx = ctx
         self.torch = torch
         self.dev = torch.device("cuda", torch.cuda.current_device())
         self.nccl = nccl
+        self.sketch_mode = sketch_mode
 
     def gaussian(self, seed, c, m):
         return self.ctx.gaussian(seed, c, m)
 
     def sketch(self, G, A):
+        if self.sketch_mode == 5:
+            if A.stride(0) % 2 or A.data_ptr() % 16:   # the tensor maps need an even pitch
+                m, n = A.shape
+                buf = self.torch.empty((m, n + 1), dtype=A.dtype, device=A.device)[:, :n]
+                buf.copy_(A)
+                A = buf
+            return self.ctx.sketch_fx(G, A)
         return self.ctx.sketch(G, A)
 
     def zeros(self, shape):

@@ -19,13 +19,20 @@ torch = pytest.importorskip("torch")
 
 
 class OracleBackend:
-    """Test stand-in for a rank's device: numpy arrays, oracle arithmetic."""
+    """Test stand-in for a rank's device: numpy arrays, oracle arithmetic.
+    fx: the sketch is the oracle's exact 52-bit fixed-point form (G_q from G)."""
+
+    def __init__(self, fx=False):
+        self.fx = fx
 
     def gaussian(self, seed, c, m):
         return oracle.gaussian_sketch(seed, c, m)
 
     def sketch(self, G, A):
-        Y = oracle.sketch(G, np.ascontiguousarray(A))
+        if self.fx:
+            Y = oracle.sketch_fx(oracle.quantize_q8(G), np.ascontiguousarray(A))
+        else:
+            Y = oracle.sketch(G, np.ascontiguousarray(A))
         return Y, float((Y * Y).sum())
 
     def zeros(self, shape):
@@ -100,6 +107,7 @@ class OracleBackend:
 CASES = {
     "small": (lambda: inputs.cfg_small(0), 1e-6, 10, 30, 0),
     "odd": (lambda: inputs.svd_matrix(300, 257, 0.9 ** np.arange(257), seed=3), 1e-8, 7, 12, 4),
+    "fx": (lambda: inputs.svd_matrix(400, 301, 0.85 ** np.arange(301), seed=6), 1e-8, 9, 14, 2),
 }
 
 
@@ -108,15 +116,30 @@ def _run(case, world=1, rank=0, group=None):
     A = make()
     n = A.shape[1]
     c0, c1 = shard.column_range(n, world, rank)
-    return shard.run(OracleBackend(), np.ascontiguousarray(A[:, c0:c1]), n, c0, tol, b, c, seed,
-                     group=group)
+    return shard.run(OracleBackend(fx=case == "fx"), np.ascontiguousarray(A[:, c0:c1]), n, c0,
+                     tol, b, c, seed, group=group)
+
+
+def test_fx_sketch_blocks_equal_columns():
+    """The exact fixed-point sketch of a column block is the same columns of
+    the whole matrix's sketch, bit for bit, and the seeded 8-bit sketch is the
+    rounding of the seeded Gaussian."""
+    A = CASES["fx"][0]()
+    Gq = oracle.quantize_q8(oracle.gaussian_sketch(2, 14, A.shape[0]))
+    assert np.array_equal(Gq, oracle.gaussian_sketch_q8(2, 14, A.shape[0]))
+    Y = oracle.sketch_fx(Gq, A)
+    for c0, c1 in [(0, 150), (150, 301), (7, 8)]:
+        assert np.array_equal(oracle.sketch_fx(Gq, np.ascontiguousarray(A[:, c0:c1])), Y[:, c0:c1])
 
 
 @pytest.mark.parametrize("case", list(CASES))
 def test_single_rank_equals_oracle(case):
     make, tol, b, c, seed = CASES[case]
     A = make()
-    ref = oracle.run(A, tol, b, c, seed=seed, mode=1)
+    if case == "fx":
+        ref = oracle.run_fx(A, tol, b, c, seed=seed, mode=1)
+    else:
+        ref = oracle.run(A, tol, b, c, seed=seed, mode=1)
     got = _run(case)
     assert got.rank == ref.rank and got.status == ref.status
     assert np.array_equal(got.I, ref.I) and np.array_equal(got.J, ref.J)

@@ -77,3 +77,43 @@ def test_single_rank_shard_equals_cur_run(ctx, case):
     assert np.array_equal(got.U, ref.U.reshape(got.U.shape))
     assert got.rho == ref.rho
     assert oracle.true_error(A, got.I, got.J, got.U) <= 10 * tol
+
+
+@pytest.mark.parametrize("case", ["small", "exact_rank"])
+def test_single_rank_shard_fx_equals_cur_run(ctx, case):
+    """With the FP64 tensor-core sketch (CudaBackend(sketch_mode=5)) the
+    sharded run makes cur_run's calls with sketch_mode 5 (G from the seed, the
+    exact fixed-point sketch, then the FP64 loop): the same I, J, U and rho."""
+    from paper_2509_21963_gb300 import shard
+    if case == "small":
+        A, tol, b, c, seed = inputs.cfg_small(0), 1e-6, 10, 30, 0
+    else:
+        A, tol, b, c, seed = inputs.exact_rank(500, 400, 37, seed=4), 1e-10, 10, 30, 2
+    Ad = torch.from_numpy(A).cuda()
+    ref = ctx.run(Ad, tol, b, c, seed, sketch_mode=5)
+    got = shard.run(shard.CudaBackend(ctx, sketch_mode=5), Ad, A.shape[1], 0, tol, b, c, seed)
+    assert got.rank == ref.rank and got.status == ref.status
+    assert np.array_equal(got.I, ref.I) and np.array_equal(got.J, ref.J)
+    assert np.array_equal(got.U, ref.U.reshape(got.U.shape))
+    assert got.rho == ref.rho
+
+
+def test_shard_fx_odd_width_block(ctx):
+    """An odd-width column block (odd row pitch) is copied to an even pitch for
+    the tensor maps; the run then selects the oracle's indices (exact sketch,
+    FP64 loop) wherever the oracle's LUPP gaps are above rounding, and its CUR
+    is as accurate as the oracle's (the 135 x 135 core has entries ~1e9, so U
+    itself agrees only to its conditioning; the true error, ~3.4e-7, is well
+    above tol: rho is the sketched estimate)."""
+    from paper_2509_21963_gb300 import shard
+    from test_parity_gpu import _decided_prefix
+    A = inputs.svd_matrix(400, 301, 0.85 ** np.arange(301), seed=6)
+    tol, b, c, seed = 1e-8, 9, 14, 2
+    got = shard.run(shard.CudaBackend(ctx, sketch_mode=5), torch.from_numpy(A).cuda(), 301, 0,
+                    tol, b, c, seed)
+    ref = oracle.run_fx(A, tol, b, c, seed=seed, mode=1)
+    n_dec = _decided_prefix(ref, b, ref.maxabsY)
+    assert n_dec >= b
+    assert np.array_equal(got.I[:n_dec], ref.I[:n_dec]) and np.array_equal(got.J[:n_dec], ref.J[:n_dec])
+    err_ref = oracle.true_error(A, ref.I, ref.J, ref.U)
+    assert oracle.true_error(A, got.I, got.J, got.U) <= 2 * err_ref
