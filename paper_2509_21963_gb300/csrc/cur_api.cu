@@ -113,7 +113,12 @@ int ensure(cur_ctx* ctx, BufId id, size_t bytes, size_t keep = 0) {
                         ctx->stream);
     if (e != cudaSuccess) { cudaFree(p); return fail(ctx, CUR_ECUDA, "workspace copy failed"); }
   }
-  if (b.p) { cudaStreamSynchronize(ctx->stream); cudaFree(b.p); }
+  if (b.p) {   // nothing on the context's streams may still use the old buffer
+    cudaStreamSynchronize(ctx->stream);
+    if (ctx->copy_stream) cudaStreamSynchronize(ctx->copy_stream);
+    if (ctx->side_stream) cudaStreamSynchronize(ctx->side_stream);
+    cudaFree(b.p);
+  }
   ctx->held = ctx->held - b.bytes + bytes;
   b.p = p;
   b.bytes = bytes;
@@ -931,19 +936,17 @@ int cur_create(cur_ctx** out, int device, void* cuda_stream, size_t hbm_budget_b
 void cur_free(cur_ctx* ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->device);
+  // every stream that may still write a context buffer (a run that failed
+  // after enqueueing its copies or side work) finishes before the frees
   cudaStreamSynchronize(ctx->stream);
+  if (ctx->copy_stream) cudaStreamSynchronize(ctx->copy_stream);
+  if (ctx->side_stream) cudaStreamSynchronize(ctx->side_stream);
   for (auto& b : ctx->buf)
     if (b.p) cudaFree(b.p);
   for (auto e : ctx->ev_pool) cudaEventDestroy(e);
   for (auto e : ctx->copy_ev) cudaEventDestroy(e);
-  if (ctx->copy_stream) {
-    cudaStreamSynchronize(ctx->copy_stream);
-    cudaStreamDestroy(ctx->copy_stream);
-  }
-  if (ctx->side_stream) {
-    cudaStreamSynchronize(ctx->side_stream);
-    cudaStreamDestroy(ctx->side_stream);
-  }
+  if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
+  if (ctx->side_stream) cudaStreamDestroy(ctx->side_stream);
   for (auto& pb : ctx->result_pool) cudaFree(pb.first);
   for (auto e : ctx->side_ev)
     if (e) cudaEventDestroy(e);
