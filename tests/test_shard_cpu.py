@@ -173,15 +173,12 @@ def _worker(rank, world, port, case, q):
         dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("case", list(CASES))
-def test_two_ranks_equal_one(case):
-    """World size 2 (gloo): both ranks return the single-rank I, J and U bit
-    for bit; the column blocks are [0, n/2) and [n/2, n) (uneven for n odd)."""
+def _spawn_ranks(case, world):
     import torch.multiprocessing as mp
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
-    procs = [ctx.Process(target=_worker, args=(r, 2, port, case, q)) for r in range(2)]
+    procs = [ctx.Process(target=_worker, args=(r, world, port, case, q)) for r in range(world)]
     for p in procs:
         p.start()
     out = {}
@@ -191,6 +188,28 @@ def test_two_ranks_equal_one(case):
     for p in procs:
         p.join(timeout=60)
         assert p.exitcode == 0
+    return out
+
+
+@pytest.mark.parametrize("case", ["odd", "fx"])
+def test_three_ranks_equal_one(case):
+    """World size 3 (gloo): blocks of 85/86/86 (n = 257) and 100/100/101
+    (n = 301) columns; every rank returns the single-rank I, J and U."""
+    out = _spawn_ranks(case, 3)
+    one = _run(case)
+    for rank in range(3):
+        I, J, U, hist, status = out[rank]
+        assert np.array_equal(I, one.I) and np.array_equal(J, one.J)
+        assert np.array_equal(U, one.U)
+        assert status == one.status
+        np.testing.assert_allclose(hist, one.rho_history, rtol=1e-12)
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_two_ranks_equal_one(case):
+    """World size 2 (gloo): both ranks return the single-rank I, J and U bit
+    for bit; the column blocks are [0, n/2) and [n/2, n) (uneven for n odd)."""
+    out = _spawn_ranks(case, 2)
     one = _run(case)
     for rank in (0, 1):
         I, J, U, hist, status = out[rank]
